@@ -1,0 +1,307 @@
+"""ctypes binding of the FP64 oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline / reference arm. The CUDA product path never imports
+it. Function names follow oracle.h; arrays are numpy, poses are (..., 12)
+row-major [R | t].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int)
+_u32p = C.POINTER(C.c_uint32)
+
+
+class Grid(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("h", C.c_double), ("n", C.c_int * 3)]
+
+
+class EvalParams(C.Structure):
+    _fields_ = [("eps", C.c_double), ("face_delta", C.c_double)]
+
+
+class MoveParams(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("lambda_", C.c_double), ("theta_max", C.c_double),
+                ("t_max", C.c_double), ("w_min", C.c_double)]
+
+
+class StepParams(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("eps", C.c_double), ("lambda_", C.c_double),
+                ("theta_max", C.c_double), ("t_max", C.c_double), ("w_min", C.c_double),
+                ("face_delta", C.c_double), ("k_nb", C.c_int), ("steps", C.c_int),
+                ("resample", C.c_int), ("seed", C.c_uint64)]
+
+
+class StepOut(C.Structure):
+    _fields_ = [("estimate", C.c_double * 12), ("ess", C.c_double), ("max_w", C.c_double),
+                ("argmax", C.c_int), ("resampled", C.c_int)]
+
+
+DEFAULTS = dict(sigma=0.2, eps=1e-3, lambda_=1e-3, theta_max=np.deg2rad(2.0), t_max=0.1,
+                w_min=1e-6, face_delta=1e-3, k_nb=3, steps=3, resample=0, seed=0)
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.ora_systematic_u.restype = C.c_double
+        L.ora_cell_eval.restype = C.c_int
+        _LIB = L
+    return _LIB
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _f(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_fp)
+
+
+def make_grid(g):
+    gr = Grid()
+    for a in range(3):
+        gr.origin[a] = float(g["origin"][a])
+        gr.n[a] = int(g["dims"][a])
+    gr.h = float(g["h"])
+    return gr
+
+
+# ---------------------------------------------------------------- SE(3)
+def pose_mul(A, B):
+    A, pa = _d(A); B, pb = _d(B)
+    out = np.zeros(12)
+    lib().ora_pose_mul(pa, pb, out.ctypes.data_as(_dp))
+    return out
+
+
+def pose_inv(A):
+    A, pa = _d(A)
+    out = np.zeros(12)
+    lib().ora_pose_inv(pa, out.ctypes.data_as(_dp))
+    return out
+
+
+def se3_exp(xi):
+    xi, px = _d(xi)
+    out = np.zeros(12)
+    lib().ora_se3_exp(px, out.ctypes.data_as(_dp))
+    return out
+
+
+def se3_log(T):
+    T, pt = _d(T)
+    out = np.zeros(6)
+    lib().ora_se3_log(pt, out.ctypes.data_as(_dp))
+    return out
+
+
+# ---------------------------------------------------------------- random draws
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().ora_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def normal6(seed, i, t):
+    z = np.zeros(6)
+    lib().ora_normal6(C.c_uint64(seed), C.c_uint32(i), C.c_uint32(t), z.ctypes.data_as(_dp))
+    return z
+
+
+def systematic_u(seed, t):
+    return float(lib().ora_systematic_u(C.c_uint64(seed), C.c_uint32(t)))
+
+
+# ---------------------------------------------------------------- tables
+def build_table(pts, grid, sigma=0.2, r_t=1.0, brute=False):
+    pts, pp = _f(pts)
+    gr = make_grid(grid)
+    nx, ny, nz = grid["dims"]
+    vals = np.zeros((nz, ny, nx))
+    fn = lib().ora_build_table_brute if brute else lib().ora_build_table
+    fn(pp, C.c_int(pts.shape[0]), C.byref(gr), C.c_double(sigma), C.c_double(r_t), vals.ctypes.data_as(_dp))
+    return vals
+
+
+def quantize(vals, dtype):
+    """dtype 1 = bfloat16, 2 = float16, both round-to-nearest-even."""
+    v, pv = _d(vals)
+    out = np.zeros_like(v)
+    lib().ora_quantize(pv, C.c_size_t(v.size), C.c_int(dtype), out.ctypes.data_as(_dp))
+    return out
+
+
+def cell_eval(vals, grid, c, u):
+    v, pv = _d(vals)
+    gr = make_grid(grid)
+    ci = (C.c_int * 3)(*[int(x) for x in c])
+    uu = (C.c_double * 3)(*[float(x) for x in u])
+    L = C.c_double()
+    d = (C.c_double * 3)()
+    ok = lib().ora_cell_eval(pv, C.byref(gr), ci, uu, C.byref(L), d)
+    return ok, L.value, np.array(list(d))
+
+
+# ---------------------------------------------------------------- evaluation
+def eval_particle(Tt, Tk, tables, grids, scan, eps=1e-3, face_delta=1e-3, cells=None, frozen=False,
+                  want_cells=False):
+    """Tk: (n_nb, 12); tables: list of (nz, ny, nx) arrays; grids: list of dicts."""
+    Tt, pt = _d(Tt)
+    Tk = np.ascontiguousarray(np.asarray(Tk, np.float64).reshape(-1, 12))
+    n_nb = Tk.shape[0]
+    tabs = [np.ascontiguousarray(t, np.float64) for t in tables]
+    tab_ptrs = (_dp * max(n_nb, 1))(*[t.ctypes.data_as(_dp) for t in tabs])
+    grs = (Grid * max(n_nb, 1))(*[make_grid(g) for g in grids])
+    scan, ps = _f(scan)
+    N = scan.shape[0]
+    prm = EvalParams(eps, face_delta)
+    ll = C.c_double()
+    g = np.zeros(6)
+    mom = np.zeros(10)
+    slack = C.c_double()
+    if cells is None and (want_cells or frozen):
+        cells = np.zeros((n_nb, N, 3), np.int32)
+    cp = None
+    if cells is not None:
+        cells = np.ascontiguousarray(cells, np.int32)
+        cp = cells.ctypes.data_as(_ip)
+    lib().ora_eval_particle(pt, C.c_int(n_nb), Tk.ctypes.data_as(_dp), tab_ptrs, grs, ps, C.c_int(N),
+                            C.byref(prm), C.byref(ll), g.ctypes.data_as(_dp), mom.ctypes.data_as(_dp),
+                            C.byref(slack), cp, C.c_int(1 if frozen else 0))
+    out = {"ll": ll.value, "g": g, "mom": mom, "slack": slack.value}
+    if cells is not None:
+        out["cells"] = cells
+    return out
+
+
+def eval_batch(poses, nbr, kf_poses, tables, grids, scan, eps=1e-3, face_delta=1e-3, idx=None):
+    """Per-particle evaluation over a set. kf_poses: (K, P, 12); nbr: (P, n_nb).
+    idx restricts to a subset of particle indices."""
+    poses = np.asarray(poses, np.float64).reshape(-1, 12)
+    P = poses.shape[0]
+    idx = np.arange(P) if idx is None else np.asarray(idx)
+    res = {"ll": np.zeros(len(idx)), "g": np.zeros((len(idx), 6)), "mom": np.zeros((len(idx), 10)),
+           "slack": np.zeros(len(idx))}
+    for r, i in enumerate(idx):
+        ks = [int(k) for k in nbr[i] if k >= 0]
+        o = eval_particle(poses[i], [kf_poses[k][i] for k in ks], [tables[k] for k in ks],
+                          [grids[k] for k in ks], scan, eps, face_delta)
+        res["ll"][r] = o["ll"]; res["g"][r] = o["g"]; res["mom"][r] = o["mom"]; res["slack"][r] = o["slack"]
+    return res
+
+
+def h_from_moments(mom, sigma=0.2):
+    m, pm = _d(mom)
+    H = np.zeros(36)
+    lib().ora_h_from_moments(pm, C.c_double(sigma), H.ctypes.data_as(_dp))
+    return H.reshape(6, 6)
+
+
+def h_explicit(scan, w, sigma=0.2):
+    s, ps = _f(scan)
+    w, pw = _d(w)
+    H = np.zeros(36)
+    lib().ora_h_explicit(ps, C.c_int(s.shape[0]), pw, C.c_double(sigma), H.ctypes.data_as(_dp))
+    return H.reshape(6, 6)
+
+
+def move(Tt, g, mom, sigma=0.2, lambda_=1e-3, theta_max=np.deg2rad(2.0), t_max=0.1, w_min=1e-6):
+    Tt, pt = _d(Tt); g, pg = _d(g); mom, pm = _d(mom)
+    mp = MoveParams(sigma, lambda_, theta_max, t_max, w_min)
+    Tout = np.zeros(12)
+    psi = np.zeros(6)
+    lib().ora_move(pt, pg, pm, C.byref(mp), Tout.ctypes.data_as(_dp), psi.ctypes.data_as(_dp))
+    return Tout, psi
+
+
+def select_nbrs(Tt, kf_t, k_nb=3):
+    Tt, pt = _d(Tt)
+    kf_t, pk = _d(np.asarray(kf_t).reshape(-1, 3))
+    idx = np.full(k_nb, -1, np.int32)
+    lib().ora_select_nbrs(pt, pk, C.c_int(kf_t.shape[0]), C.c_int(k_nb), idx.ctypes.data_as(_ip))
+    return idx
+
+
+def predict(T, dT, cov, z):
+    T, pt = _d(T); dT, pd = _d(dT); cov, pc = _d(np.asarray(cov).reshape(36)); z, pz = _d(z)
+    out = np.zeros(12)
+    lib().ora_predict(pt, pd, pc, pz, out.ctypes.data_as(_dp))
+    return out
+
+
+def lse(logw, ll):
+    logw, pl = _d(logw); ll, pll = _d(ll)
+    P = logw.shape[0]
+    lo = np.zeros(P); w = np.zeros(P)
+    M = C.c_double(); lS = C.c_double(); am = C.c_int(); ess = C.c_double()
+    lib().ora_lse(pl, pll, C.c_int(P), lo.ctypes.data_as(_dp), w.ctypes.data_as(_dp), C.byref(M), C.byref(lS),
+                  C.byref(am), C.byref(ess))
+    return {"logw": lo, "w": w, "M": M.value, "logS": lS.value, "argmax": am.value, "ess": ess.value}
+
+
+def resample(w, u):
+    w, pw = _d(w)
+    P = w.shape[0]
+    anc = np.zeros(P, np.int32)
+    lib().ora_resample(pw, C.c_int(P), C.c_double(u), anc.ctypes.data_as(_ip))
+    return anc
+
+
+class State:
+    """Particle set held by the oracle in FP64: poses (P, 12), keyframe poses
+    (K, P, 12), log-weights (P,), plus the shared keyframe tables."""
+
+    def __init__(self, poses, kf_poses, tables, grids, logw=None):
+        self.poses = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 12))
+        self.kf_poses = np.ascontiguousarray(np.asarray(kf_poses, np.float64))
+        P = self.poses.shape[0]
+        self.logw = np.full(P, -np.log(P)) if logw is None else np.ascontiguousarray(logw, np.float64)
+        self.tables = [np.ascontiguousarray(t, np.float64) for t in tables]
+        self.grids = list(grids)
+
+    def step(self, scan, dT, cov, frame, z=None, u=None, **params):
+        prm = dict(DEFAULTS)
+        prm.update(params)
+        sp = StepParams(prm["sigma"], prm["eps"], prm["lambda_"], prm["theta_max"], prm["t_max"], prm["w_min"],
+                        prm["face_delta"], prm["k_nb"], prm["steps"], prm["resample"], prm["seed"])
+        P = self.poses.shape[0]
+        K = len(self.tables)
+        tab_ptrs = (_dp * max(K, 1))(*[t.ctypes.data_as(_dp) for t in self.tables])
+        grs = (Grid * max(K, 1))(*[make_grid(g) for g in self.grids])
+        scan, ps = _f(scan)
+        dT, pd = _d(dT)
+        cov, pc = _d(np.asarray(cov).reshape(36))
+        zp = None
+        if z is not None:
+            z, zp = _d(z)
+        up = None
+        if u is not None:
+            uu = C.c_double(u)
+            up = C.byref(uu)
+        out = StepOut()
+        k_nb = min(prm["k_nb"], K)
+        ll = np.zeros(P); w = np.zeros(P); anc = np.zeros(P, np.int32); nbr = np.zeros((P, max(k_nb, 1)), np.int32)
+        lib().ora_step(C.c_int(P), C.c_int(K), self.poses.ctypes.data_as(_dp), self.kf_poses.ctypes.data_as(_dp),
+                       self.logw.ctypes.data_as(_dp), tab_ptrs, grs, ps, C.c_int(scan.shape[0]), pd, pc,
+                       C.c_uint32(frame), zp, up, C.byref(sp), C.byref(out), ll.ctypes.data_as(_dp),
+                       w.ctypes.data_as(_dp), anc.ctypes.data_as(_ip), nbr.ctypes.data_as(_ip))
+        return {"estimate": np.array(list(out.estimate)), "ess": out.ess, "max_w": out.max_w,
+                "argmax": out.argmax, "resampled": bool(out.resampled), "ll": ll, "w": w, "anc": anc,
+                "nbr": nbr[:, :k_nb]}

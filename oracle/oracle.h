@@ -1,0 +1,153 @@
+/*
+ * oracle.h -- plain, slow FP64 reference of the per-frame particle update of
+ * "Range-based 6-DoF Monte Carlo SLAM with Gradient-guided Particle Filter on
+ * GPU" (Nakao et al., arXiv 2504.18056).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline / reference arm may load this library. The CUDA product path
+ * shares no code with it and never calls it.
+ *
+ * Conventions
+ *   pose    12 doubles, row-major 3x4 [R | t]; x_world = R p + t.
+ *   xi      se(3) tangent vector [omega(3); v(3)], rotation first; a pose is
+ *           perturbed on the right, T exp(xi), as in Eq. 1, Eq. 7 and Eq. 10.
+ *   grid    lattice vertices at origin + h*(ix, iy, iz), 0 <= i? < n?, values
+ *           stored [iz][iy][ix] (x fastest).
+ *   scan    float triples (the sensor's own precision) widened to double.
+ *
+ * Parity status of each function is stated beside it; the pins live in the
+ * test-suite (tests/test_oracle_*.py).
+ */
+#ifndef GMCS_ORACLE_H
+#define GMCS_ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double origin[3];
+    double h;
+    int n[3];
+} ora_grid;
+
+/* ---- SE(3) (closed forms: Rodrigues + left Jacobian; Taylor below 1e-4 rad) */
+void ora_pose_mul(const double A[12], const double B[12], double C[12]);
+void ora_pose_inv(const double A[12], double B[12]);
+void ora_se3_exp(const double xi[6], double T[12]);
+void ora_se3_log(const double T[12], double xi[6]);
+
+/* ---- Philox4x32-10 (Salmon et al., SC'11) and the draws built on it */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Six standard normals for particle i at frame t (Box-Muller on 24-bit uniforms). */
+void ora_normal6(uint64_t seed, uint32_t i, uint32_t t, double z[6]);
+/* Systematic-resampling offset u in [0,1) for frame t (53-bit uniform). */
+double ora_systematic_u(uint64_t seed, uint32_t t);
+
+/* ---- likelihood tables (Sec. III-C1 replaced by a voxel likelihood field) */
+/* vals[v] = exp(-d^2 / 2 sigma^2) if d <= r_t else 0, d = distance from vertex v
+ * to the nearest point. Points are visited one by one and every vertex within
+ * r_t of the point is relaxed. */
+void ora_build_table(const float* pts, int n, const ora_grid* g, double sigma, double r_t, double* vals);
+/* Same value, with the minimum taken over all points for every vertex. */
+void ora_build_table_brute(const float* pts, int n, const ora_grid* g, double sigma, double r_t, double* vals);
+/* Round to bfloat16 (dtype 1) or IEEE half (dtype 2), nearest-even, widened back. */
+void ora_quantize(const double* in, size_t n, int dtype, double* out);
+
+/* Trilinear value and gradient (w.r.t. lattice coordinate u) of cell c at u.
+ * Returns 1 if c is inside the table, else 0 (value and gradient set to 0). */
+int ora_cell_eval(const double* vals, const ora_grid* g, const int c[3], const double u[3],
+                  double* L, double dLdu[3]);
+
+/* ---- per-particle evaluation (form of Eq. 2-3 and Eq. 6 on the voxel field) */
+typedef struct {
+    double eps;          /* likelihood floor: l = log(L + eps) */
+    double face_delta;   /* cells; lookups closer than this to a cell face add slack */
+} ora_eval_params;
+
+/*
+ * One particle: current pose Tt, n_nb neighbour keyframes with this particle's
+ * keyframe poses Tk[s] (12 each), their tables and grids, N scan points.
+ * Outputs (any may be NULL):
+ *   ll      sum over points and neighbours of log(L + eps)
+ *   g       d ll / d xi at xi = 0 for Tt exp(xi)  (6)
+ *   mom     [W, Sx, Sy, Sz, Qxx, Qxy, Qxz, Qyy, Qyz, Qzz] with weight w = L/(L+eps):
+ *           W = sum w, S = sum w p, Q = sum w p p^T (p in the sensor frame)
+ *   slack   sum over lookups within face_delta of a face of the norm of the
+ *           change in that lookup's d l / d xi when the neighbouring cell is used
+ *   cells   if frozen == 0 and cells != NULL: the cell used per (s, j) is written
+ *           (3 ints, -1 -1 -1 when outside); if frozen == 1 those cells are used
+ *           instead of floor(u), their polynomial extended past the faces.
+ */
+void ora_eval_particle(const double Tt[12], int n_nb, const double* Tk, const double* const* tables,
+                       const ora_grid* grids, const float* scan, int N, const ora_eval_params* prm,
+                       double* ll, double g[6], double mom[10], double* slack, int* cells, int frozen);
+
+/* Gauss-Newton matrix from the moments (Eq. 6 on the field, sigma^-2 sum w B^T B). */
+void ora_h_from_moments(const double mom[10], double sigma, double H[36]);
+/* Same matrix, summed explicitly from points and weights. */
+void ora_h_explicit(const float* scan, int N, const double* w, double sigma, double H[36]);
+
+typedef struct {
+    double sigma;       /* field width (m) */
+    double lambda;      /* Levenberg-Marquardt factor on diag(H) */
+    double theta_max;   /* rad, clamp on |psi_omega| */
+    double t_max;       /* m, clamp on |psi_v| */
+    double w_min;       /* no move when W < w_min */
+} ora_move_params;
+
+/* Eq. 5-7: psi = (H + lambda diag H)^-1 g, clamped, Tout = Tt exp(psi). */
+void ora_move(const double Tt[12], const double g[6], const double mom[10], const ora_move_params* mp,
+              double Tout[12], double psi[6]);
+
+/* ---- neighbour keyframes: the k_nb smallest |t_k - t_t| (ties -> lower k).
+ * The squared distances are formed in float with a fixed order of operations,
+ * the precision the GPU takes this decision in. */
+void ora_select_nbrs(const double Tt[12], const double* kf_t /* K x 3 */, int K, int k_nb, int* idx);
+
+/* ---- prediction, Eq. 1: Tout = T dT exp(L z), L = chol(cov) (lower). */
+void ora_predict(const double T[12], const double dT[12], const double cov[36], const double z[6],
+                 double Tout[12]);
+
+/* ---- importance weighting, Eq. 11, normalised by log-sum-exp. */
+void ora_lse(const double* logw, const double* ll, int P, double* logw_out, double* w,
+             double* M, double* logS, int* argmax, double* ess);
+
+/* ---- systematic resampling on weights quantised to the 2^-52 grid. */
+void ora_resample(const double* w, int P, double u, int* anc);
+
+/* ---- whole frame over a particle set (the hot path, all steps in order). */
+typedef struct {
+    double sigma, eps, lambda, theta_max, t_max, w_min, face_delta;
+    int k_nb, steps;
+    int resample;        /* 0 always, 1 when ESS < P/2, 2 never */
+    uint64_t seed;
+} ora_step_params;
+
+typedef struct {
+    double estimate[12];
+    double ess, max_w;
+    int argmax, resampled;
+} ora_step_out;
+
+/*
+ * poses     P x 12 current poses (in/out)
+ * kf_poses  K x P x 12 per-particle keyframe poses (in/out; gathered on resample)
+ * logw      P log-weights (in/out)
+ * frame     frame counter for the counter-based draws
+ * z         optional P x 6 standard normals (NULL -> Philox draws)
+ * u         optional systematic offset (NULL -> Philox draw)
+ * ll_out, w_out, anc_out, nbr_out   optional diagnostics (P, P, P, P x k_nb)
+ */
+void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
+              const double* const* tables, const ora_grid* grids,
+              const float* scan, int N, const double dT[12], const double cov[36],
+              uint32_t frame, const double* z, const double* u, const ora_step_params* sp,
+              ora_step_out* out, double* ll_out, double* w_out, int* anc_out, int* nbr_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
