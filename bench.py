@@ -1,0 +1,377 @@
+"""Benchmark of the per-frame particle update (gradient-guided Monte Carlo SLAM).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+One step = one frame of the whole hot path on the paper-scale session:
+100,000 particles, 2,048-point scans, 20 keyframes of 8,192 points (0.2 m
+lattice), 3 neighbour keyframes, 3 gradient-guided moves, the value pass,
+log-sum-exp weighting and systematic resampling. Inputs are synthetic (a
+procedural corridor-and-trunk scene ray-cast by a 64 x 1024 lidar), resident
+in HBM before the timed region. L2 is flushed (a 256 MB write) before every
+timed step, outside its events.
+
+Metric: particle x point likelihood+gradient evaluations per second, i.e.
+P * N * steps per frame (each evaluation covers the 3 neighbour keyframes);
+the frame time p50/p99 and lookups/s are reported beside it.
+
+Under torchrun (N > 1) every rank runs an independent session (replicas: the
+filter has no data-path exchange); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle×point lik+grad evals/s; frame update ms @100k particles; p50/p99"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--particles", type=int, default=100_000)
+    ap.add_argument("--points", type=int, default=2048)
+    ap.add_argument("--keyframes", type=int, default=20)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-particles", type=int, default=1024, help="oracle sample for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--out", default=None, help="also write the JSON line to this file")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return dist
+
+
+def reduce_max(value, world, device=None):
+    """Max of a float over ranks (identity at world size 1)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, world, device=None):
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock, max clock and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_prepare(w, n_particles):
+    """FP64 oracle state for the first n_particles of the workload, with tables
+    for every keyframe a sampled particle can select (an empty 2x2x2 lattice far
+    away, which every lookup misses, stands in for the others)."""
+    import oracle
+    P = n_particles
+    K = len(w["keyframes"])
+    poses = w["particles"][:P].astype(np.float64)
+    kfp = np.stack([p[:P] for p in w["kf_particle_poses"]]).astype(np.float64)
+    t = poses[:, [3, 7, 11]]
+    dist = np.stack([np.linalg.norm(kfp[k][:, [3, 7, 11]] - t, axis=1) for k in range(K)], 1)
+    third = np.sort(dist, axis=1)[:, min(2, K - 1)]
+    need = set(np.nonzero((dist <= third[:, None] + 3.0).any(axis=0))[0].tolist())
+    tables, grids = [], []
+    for k, kf in enumerate(w["keyframes"]):
+        if k in need:
+            tables.append(oracle.build_table(kf["points"], kf["grid"], 0.2, 1.0))
+            grids.append(kf["grid"])
+        else:
+            tables.append(np.zeros((2, 2, 2)))
+            grids.append({"origin": np.array([1e6, 1e6, 1e6]), "h": 1.0, "dims": (2, 2, 2)})
+    return oracle.State(poses, kfp, tables, grids)
+
+
+def oracle_frames(st, w, frames, first=0):
+    """Seconds of each whole oracle frame (single thread) on the prepared sample."""
+    out = []
+    for fr in range(first, first + frames):
+        t0 = time.perf_counter()
+        st.step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=fr)
+        out.append(time.perf_counter() - t0)
+    return np.array(out)
+
+
+def oracle_sample(w, n_particles, frames=1):
+    """Evals per second of the oracle's whole frame on a particle sample."""
+    st = oracle_prepare(w, n_particles)
+    dt = oracle_frames(st, w, frames).sum()
+    N = w["scans"][0].shape[0]
+    evals = n_particles * N * 3 * frames
+    desc = (f"FP64 oracle, whole frame on the first {n_particles} particles of the same session "
+            f"({N} points, {len(w['keyframes'])} keyframes, 3 moves), {frames} frame(s), single thread")
+    return evals / dt, dt, desc
+
+
+# ----------------------------------------------------------------------------- native arm
+def run_native(a, world, rank, local):
+    import torch
+    import paper_2504_18056_b300 as g
+    import synth
+
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    frames = a.warmup + a.steps + a.e2e_steps
+    w = synth.forest_workload(seed=rank, n_particles=a.particles, n_points=a.points, n_keyframes=a.keyframes,
+                              n_frames=frames)
+    P, N, K = a.particles, a.points, a.keyframes
+    dtype = {"f32": 0, "bf16": 1, "f16": 2}[a.dtype]
+    stream = torch.cuda.current_stream(dev)
+    f = g.Filter(P, K, N, stream=stream.cuda_stream, table_dtype=dtype, seed=rank)
+    f.init_particles(w["particles"])
+    for k, kf in enumerate(w["keyframes"]):
+        f.add_keyframe(kf["points"], kf["grid"], w["kf_particle_poses"][k])
+    scans_d = [torch.from_numpy(s).to(dev) for s in w["scans"]]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
+    torch.cuda.synchronize()
+
+    for fr in range(a.warmup):
+        f.step(scans_d[fr], w["odometry"][fr], w["cov"], sync=False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    f.set_profiling(True)
+    f.reset_stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in range(a.steps):
+        fr = a.warmup + s
+        if not a.no_flush:
+            flush.fill_(float(s))
+        ev[s][0].record(stream)
+        f.step(scans_d[fr], w["odometry"][fr], w["cov"], sync=False)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+    stats = f.stats()
+    f.set_profiling(False)
+    res = f.last_result()
+
+    # end to end through the public call: pinned host scan in, result struct out
+    pinned = [torch.from_numpy(w["scans"][a.warmup + a.steps + s]).pin_memory() for s in range(a.e2e_steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(a.e2e_steps):
+        fr = a.warmup + a.steps + s
+        out = f.step(pinned[s], w["odometry"][fr], w["cov"])      # synchronises, fills the host struct
+    e2e_s = time.perf_counter() - t0
+    assert out["status"] == 0
+    dev_bytes = f.device_bytes()
+    f.close()
+
+    total_ms = float(step_ms.sum())
+    max_ms = reduce_max(total_ms, world, dev)
+    evals_rank = float(P) * N * 3 * a.steps
+    evals_all = reduce_sum(evals_rank, world, dev)
+    value = evals_all / (max_ms / 1e3)
+    e2e_max = reduce_max(e2e_s, world, dev)
+    e2e_value = reduce_sum(float(P) * N * 3 * a.e2e_steps, world, dev) / e2e_max
+
+    kinds = stats["kinds"]
+    pg = kinds["pass_grad"]
+    lookups_per_launch = float(P) * N * 3
+    rec_bytes = 32 if dtype == 0 else 16
+    avg_ms = pg["ms"] / max(pg["launches"], 1)
+    achieved_gbs = lookups_per_launch * rec_bytes / (avg_ms / 1e3) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak, peak_src = 6400.0, "fallback"
+    if os.path.exists(peaks_path):
+        hbm_peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    timed_kernel_ms = sum(v["ms"] for v in kinds.values())
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": max_ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"f32": "f32", "bf16": "bf16 tables, f32 math", "f16": "f16 tables, f32 math"}[a.dtype] +
+                 "; f64 weights",
+        "data": "synthetic (seeded procedural corridor + trunk scene, 64x1024 lidar ray-cast)",
+        "config": {"workload": f"single session, {P} particles x {N}-point scans x {K} keyframes "
+                               f"(8192 pts, 0.2 m lattice), 3 neighbour keyframes, 3 moves/frame",
+                   "particles": P, "points": N, "keyframes": K, "k_nb": 3, "moves": 3,
+                   "table": a.dtype, "l2": "flushed before every timed step (256 MB write)" if not a.no_flush
+                   else "not flushed", "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "frame_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                     "min": float(step_ms.min()), "max": float(step_ms.max())},
+        "lookups_per_s": float(P) * N * 3 * 4 * a.steps * world / (max_ms / 1e3),
+        "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in kinds.items() if v["launches"]},
+        "roofline": {"kernel": "pass_grad (lookup + gradient + moments)", "bound": "hbm",
+                     "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm_peak, "traffic": None,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": lookups_per_launch * rec_bytes,
+                     "avg_launch_ms": avg_ms},
+        "clocks": clk,
+        "gpu_launches": int(stats["launches"]),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 12,
+                "d2h_bytes_per_step": 128, "frame_ms": e2e_max / a.e2e_steps * 1e3},
+        "estimate_error_m": float(np.linalg.norm(res["estimate"][[3, 7, 11]] -
+                                                 w["truth"][a.warmup + a.steps][[3, 7, 11]])),
+        "device_bytes": dev_bytes,
+        "timed_kernel_share": timed_kernel_ms / total_ms if total_ms > 0 else None,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, dt, desc = oracle_sample(w, min(a.cpu_particles, P))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                "seconds": dt}
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+# ----------------------------------------------------------------------------- reference arm (the oracle)
+def run_reference(a, world, rank):
+    """The FP64 oracle as the reference implementation, on the host cores: each
+    step is one whole frame on a bounded particle sample of the same session."""
+    if rank != 0:
+        return None
+    import synth
+    P_s = min(64, a.particles)
+    frames = a.warmup + a.steps
+    w = synth.forest_workload(seed=0, n_particles=P_s, n_points=a.points, n_keyframes=a.keyframes,
+                              n_frames=frames)
+    st = oracle_prepare(w, P_s)
+    times = oracle_frames(st, w, frames)[a.warmup:]
+    N = a.points
+    value = P_s * N * 3 * len(times) / times.sum()
+    desc = (f"FP64 oracle, whole frame on the first {P_s} particles per step ({N} points, "
+            f"{a.keyframes} keyframes, 3 moves), single thread")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": float(times.mean()) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"single session, {a.particles} particles x {N}-point scans x "
+                                   f"{a.keyframes} keyframes; each step a {P_s}-particle sample",
+                       "particles": a.particles, "points": N, "keyframes": a.keyframes},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    world, rank, local = dist_env()
+    if a.impl == "reference":
+        line = run_reference(a, world, rank)
+    else:
+        line = run_native(a, world, rank, local)
+    if rank == 0 and line is not None:
+        s = json.dumps(line)
+        print(s, flush=True)
+        if a.out:
+            with open(a.out, "w") as fh:
+                fh.write(s + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * gmcs.h -- C ABI of the B300 (sm_103a) per-frame particle update of
+ * gradient-guided Monte Carlo SLAM (Nakao et al., "Range-based 6-DoF Monte
+ * Carlo SLAM with Gradient-guided Particle Filter on GPU", arXiv 2504.18056).
+ *
+ * The problem statement of Sec. III-A: estimate the sensor pose T_t and the map
+ * from range scans and odometry, with every particle x_t^i holding its current
+ * pose T_t^i plus its own copy T_k^i of every keyframe pose, while keyframe
+ * point clouds are stored once and shared by all particles.
+ *
+ * The map of each keyframe is a voxel likelihood field: on a lattice of edge h,
+ * vertex value exp(-d^2 / 2 sigma^2) with d the distance to the nearest
+ * keyframe point (0 beyond r_t), read by trilinear interpolation. This replaces
+ * the GICP distribution-to-distribution metric of Eq. 2-4 on the hot path.
+ *
+ * Conventions (all entry points)
+ *   - Return GMCS_OK (0) or a negative GMCS_E_* code; nothing is thrown across
+ *     the ABI; gmcs_strerror() names the code. After GMCS_E_INVALID or
+ *     GMCS_E_CAPACITY the context is unchanged and usable. GMCS_E_CUDA means a
+ *     CUDA call failed and the context should be destroyed.
+ *   - Poses at the boundary are 12 floats (or doubles where stated), row-major
+ *     3x4 [R | t], mapping sensor-frame points into the frame of reference:
+ *     x = R p + t. Arrays of poses are P x 12 (particle-major).
+ *   - Tangent vectors are xi = [omega(3); v(3)], rotation first; poses are
+ *     perturbed on the right, T exp(xi) (Eq. 1, Eq. 7, Eq. 10).
+ *   - Pointer arguments marked "host or device" are classified with
+ *     cudaPointerGetAttributes; device pointers must belong to the context's
+ *     device. The caller keeps ownership of every buffer it passes; inputs are
+ *     consumed in stream order on the context's stream (a host input is copied
+ *     before the call returns). The library owns all state it allocates.
+ *   - All GPU work is enqueued on the stream given to gmcs_create. Calls that
+ *     return results to host memory synchronise that stream.
+ *   - One context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef GMCS_H
+#define GMCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GMCS_OK 0
+#define GMCS_E_INVALID (-1)   /* bad argument, size or pointer */
+#define GMCS_E_OOM (-2)       /* device or pinned allocation failed */
+#define GMCS_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define GMCS_E_CAPACITY (-4)  /* more particles / keyframes / points than the context holds */
+#define GMCS_E_STATE (-5)     /* call out of order (e.g. step before particles exist) */
+#define GMCS_E_NONFINITE (-6) /* weights degenerated (all log-weights -inf or NaN); reset to uniform */
+
+#define GMCS_TABLE_F32 0
+#define GMCS_TABLE_BF16 1
+#define GMCS_TABLE_F16 2
+
+#define GMCS_RESAMPLE_ALWAYS 0
+#define GMCS_RESAMPLE_ESS_HALF 1
+#define GMCS_RESAMPLE_NEVER 2
+
+#define GMCS_MAX_NB 8         /* upper bound on k_nb */
+
+typedef struct {
+    float sigma;       /* field width (m): vertex value exp(-d^2 / 2 sigma^2) */
+    float r_t;         /* truncation radius (m): value 0 where d > r_t */
+    float eps;         /* likelihood floor: per-lookup log-likelihood log(L + eps) */
+    float lambda;      /* Levenberg-Marquardt factor: H_ii *= (1 + lambda) */
+    float theta_max;   /* rad, clamp on |psi_omega| per move */
+    float t_max;       /* m, clamp on |psi_v| per move */
+    float w_min;       /* no move when the contact weight W = sum L/(L+eps) < w_min */
+    int k_nb;          /* neighbour keyframes per particle (Sec. III-C: three) */
+    int steps;         /* gradient-guided moves per frame */
+    int table_dtype;   /* GMCS_TABLE_* storage type of the likelihood tables */
+    int resample;      /* GMCS_RESAMPLE_* policy */
+    int reserved;
+    uint64_t seed;     /* key of the Philox4x32-10 draws (motion noise, resampling offset) */
+} gmcs_config;
+
+/* Lattice of one keyframe table, in the keyframe's own frame: vertex (ix,iy,iz)
+ * sits at origin + h*(ix,iy,iz), 0 <= ix < n[0] etc. At least 2 vertices per axis. */
+typedef struct {
+    double origin[3];
+    double h;
+    int n[3];
+} gmcs_grid;
+
+typedef struct {
+    double estimate[12];  /* current pose of the largest-weight particle (Sec. IV-A), before resampling */
+    double ess;           /* effective sample size 1 / sum w^2 of the normalised weights */
+    double max_w;         /* largest normalised weight */
+    double log_norm;      /* M + log S of the log-sum-exp normalisation */
+    int argmax;           /* its index (lowest index on ties) */
+    int resampled;        /* 1 if systematic resampling ran this frame */
+    uint32_t frame;       /* frame counter used for this frame's draws */
+    int status;           /* GMCS_OK or GMCS_E_NONFINITE */
+} gmcs_step_out;
+
+typedef struct {
+    uint64_t launches;        /* kernels launched by this context since creation */
+    uint64_t frames;          /* gmcs_step calls completed */
+    int profiling;            /* 1 while per-kernel event timing is enabled */
+    int n_kinds;              /* entries used below */
+    const char* kind[16];     /* kernel family names */
+    uint64_t kind_launches[16];
+    double kind_ms[16];       /* summed event time per family (profiling only) */
+} gmcs_stats;
+
+typedef struct gmcs_ctx gmcs_ctx;
+
+/* Defaults: sigma 0.2 m, r_t 1.0 m, eps 1e-3, lambda 1e-3, theta_max 2 deg,
+ * t_max 0.1 m, w_min 1e-6, k_nb 3, steps 3, FP32 tables, resample always, seed 0. */
+void gmcs_config_default(gmcs_config* cfg);
+
+/*
+ * Create a context on the current CUDA device, holding up to max_particles
+ * particles, max_keyframes keyframes and scans of up to max_points points.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream). Allocates all
+ * per-particle device state up front: poses and keyframe poses double-buffered
+ * (2 x 48 B x (1 + max_keyframes) per particle) plus per-frame scratch.
+ * Errors: GMCS_E_INVALID (sizes <= 0, k_nb outside 1..GMCS_MAX_NB, bad config),
+ * GMCS_E_OOM.
+ */
+int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, int max_points,
+                void* cuda_stream, gmcs_ctx** out);
+
+/* Free everything the context owns (synchronises its stream). NULL is a no-op. */
+int gmcs_destroy(gmcs_ctx* ctx);
+
+/*
+ * Set the particle set: P current poses (P x 12 floats, host or device) and
+ * optional log-weights (P doubles, host or device; NULL = uniform -log P).
+ * Resets the frame counter to 0 and drops nothing else (keyframes stay).
+ * Errors: GMCS_E_INVALID, GMCS_E_CAPACITY (P > max_particles).
+ */
+int gmcs_init_particles(gmcs_ctx* ctx, const float* poses, int P, const double* logw);
+
+/*
+ * Insert a keyframe (Sec. III-A: shared cloud P_k, per-particle pose T_k^i).
+ * pts: n points (n x 3 floats, host or device) in the keyframe's own frame.
+ * grid: the table lattice in that frame. The library builds the table on the
+ * device (K8: splat of d^2 within r_t, then exp) and stores it packed per cell
+ * (8 corner values contiguous) in cfg.table_dtype.
+ * kf_poses: P x 12 floats (host or device), the keyframe pose held by each
+ * particle, or NULL to copy every particle's current pose (the paper's
+ * insertion of the current frame as a keyframe). Needs particles to exist.
+ * *kf_id receives the keyframe index (0, 1, ...).
+ * Errors: GMCS_E_INVALID, GMCS_E_CAPACITY (too many keyframes), GMCS_E_STATE,
+ * GMCS_E_OOM (table allocation).
+ */
+int gmcs_add_keyframe(gmcs_ctx* ctx, const float* pts, int n, const gmcs_grid* grid,
+                      const float* kf_poses, int* kf_id);
+
+/*
+ * One frame of the hot path, all on the device:
+ *   prediction (Eq. 1) with Philox4x32-10 noise of covariance cov,
+ *   neighbour keyframes by translation distance (Sec. III-C1), frozen for the frame,
+ *   cfg.steps x [scan transform, table lookup, log-likelihood, se(3) gradient and
+ *               Gauss-Newton moments per particle, damped move (Eq. 5-7)],
+ *   value pass at the moved poses, log-weight update (Eq. 11) with log-sum-exp
+ *   normalisation in FP64, argmax estimate,
+ *   systematic resampling per cfg.resample (FP64 offsets on 2^-52-quantised
+ *   weights, exact integer prefix sums), and the gather of all particle state.
+ * scan: N points (N x 3 floats, host or device) in the sensor frame.
+ * delta_T: odometry increment (T^o_{t-1})^-1 T^o_t as 12 doubles (host).
+ * cov: 6 x 6 motion covariance in the tangent space (36 doubles, host, row-major).
+ * u_override: NULL, or a host double in [0,1) used as the systematic offset.
+ * out: NULL (asynchronous: nothing is read back; see gmcs_last_result), or a
+ * host struct filled after synchronising the stream.
+ * Errors: GMCS_E_INVALID, GMCS_E_CAPACITY (N > max_points), GMCS_E_STATE (no
+ * particles or no keyframes), GMCS_E_CUDA.
+ */
+int gmcs_step(gmcs_ctx* ctx, const float* scan, int N, const double delta_T[12], const double cov[36],
+              const double* u_override, gmcs_step_out* out);
+
+/* Result of the last gmcs_step (synchronises the stream). */
+int gmcs_last_result(gmcs_ctx* ctx, gmcs_step_out* out);
+
+/* ---- stage entry points (each one row of the hot path, on the resident state) */
+
+/* Eq. 1 on all particles. z: NULL (Philox draws for frame `frame`) or P x 6
+ * standard normals (host or device floats). Does not advance the frame counter. */
+int gmcs_predict(gmcs_ctx* ctx, const double delta_T[12], const double cov[36], const float* z, uint32_t frame);
+
+/* Neighbour keyframes of every particle for its current pose: the k_nb smallest
+ * squared distances |t_k^i - t_t^i|^2 (float, formed as (dx*dx + dy*dy) + dz*dz
+ * without fused multiply-add), ties to the lower index. nbr_out: NULL or P x k_nb
+ * ints (host or device) receiving the indices (-1 for unused slots). */
+int gmcs_select(gmcs_ctx* ctx, int* nbr_out);
+
+/*
+ * Evaluate the current particles against the scan with the current neighbour
+ * sets (gmcs_select or the last step): per particle
+ *   ll  = sum_{j, k} log(L_jk + eps)                       (P floats)
+ *   g   = d ll / d xi for T_t exp(xi) at xi = 0             (P x 6 floats)
+ *   mom = [W, Sx, Sy, Sz, Qxx, Qxy, Qxz, Qyy, Qyz, Qzz], w = L/(L+eps),
+ *         W = sum w, S = sum w p, Q = sum w p p^T            (P x 10 floats)
+ * Any output may be NULL; outputs are host or device (host: synchronises).
+ */
+int gmcs_eval(gmcs_ctx* ctx, const float* scan, int N, float* ll, float* g, float* mom);
+
+/* One gradient-guided move of every particle (eval with gradient, then Eq. 5-7
+ * with H = sigma^-2 sum w B^T B assembled from the moments). */
+int gmcs_move(gmcs_ctx* ctx, const float* scan, int N);
+
+/*
+ * Log-sum-exp weighting (Eq. 11): logw += ll (ll: P floats, host or device),
+ * then w = exp(logw - M - log S) in FP64. w_out: NULL or P doubles (host or
+ * device). res: NULL or host struct receiving ess, max_w, argmax, log_norm and
+ * the argmax particle's pose. Leaves logw unnormalised (logw + ll).
+ */
+int gmcs_weigh(gmcs_ctx* ctx, const float* ll, double* w_out, gmcs_step_out* res);
+
+/*
+ * Systematic resampling of arbitrary weights (a stand-alone hook on the same
+ * kernels the step uses): w (P doubles, host or device, normalised), offset u
+ * in [0,1), ancestors written to anc (P ints, host or device):
+ *   q_i = rint(w_i 2^52), C_i = q_0 + ... + q_i (exact), S = C_{P-1},
+ *   a_m = min{ i : C_i > ((u + m) / P) * S } (IEEE double, no contraction),
+ *   clamped to P - 1.
+ * P may exceed max_particles only up to the context's scratch (same bound).
+ */
+int gmcs_resample(gmcs_ctx* ctx, const double* w, int P, double u, int* anc);
+
+/* ---- state access */
+
+/* Copy current poses (P x 12 floats) and/or log-weights (P doubles) out; NULL skips. */
+int gmcs_get_particles(gmcs_ctx* ctx, float* poses, double* logw);
+/* Copy particle keyframe poses of keyframe k (P x 12 floats). */
+int gmcs_get_kf_poses(gmcs_ctx* ctx, int k, float* poses);
+/* Overwrite keyframe k's per-particle poses (P x 12 floats, host or device). */
+int gmcs_set_kf_poses(gmcs_ctx* ctx, int k, const float* poses);
+/*
+ * Per-particle diagnostics of the last gmcs_step (any pointer may be NULL; host
+ * or device): ll = value-pass log-likelihood (P floats), w = normalised weights
+ * before resampling (P doubles), anc = ancestors (P ints; identity when the
+ * frame did not resample), nbr = neighbour keyframes (P x k_nb ints).
+ */
+int gmcs_get_frame_diag(gmcs_ctx* ctx, float* ll, double* w, int* anc, int* nbr);
+/* Copy table k as float vertex values [n2][n1][n0] (unpacked from its cells). */
+int gmcs_get_table(gmcs_ctx* ctx, int k, float* vals);
+/* Current sizes. Any pointer may be NULL. */
+int gmcs_get_sizes(gmcs_ctx* ctx, int* P, int* K, uint32_t* frame);
+
+/* Per-kernel CUDA-event timing (on the context stream) on/off; counters. */
+int gmcs_set_profiling(gmcs_ctx* ctx, int on);
+int gmcs_get_stats(gmcs_ctx* ctx, gmcs_stats* out);
+int gmcs_reset_stats(gmcs_ctx* ctx);
+
+/* Bytes of device memory the context holds (state, scratch and tables). */
+int gmcs_device_bytes(gmcs_ctx* ctx, uint64_t* bytes);
+
+const char* gmcs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMCS_H */

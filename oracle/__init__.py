@@ -176,6 +176,7 @@ def eval_particle(Tt, Tk, tables, grids, scan, eps=1e-3, face_delta=1e-3, cells=
     g = np.zeros(6)
     mom = np.zeros(10)
     slack = C.c_double()
+    gabs = C.c_double()
     if cells is None and (want_cells or frozen):
         cells = np.zeros((n_nb, N, 3), np.int32)
     cp = None
@@ -184,8 +185,8 @@ def eval_particle(Tt, Tk, tables, grids, scan, eps=1e-3, face_delta=1e-3, cells=
         cp = cells.ctypes.data_as(_ip)
     lib().ora_eval_particle(pt, C.c_int(n_nb), Tk.ctypes.data_as(_dp), tab_ptrs, grs, ps, C.c_int(N),
                             C.byref(prm), C.byref(ll), g.ctypes.data_as(_dp), mom.ctypes.data_as(_dp),
-                            C.byref(slack), cp, C.c_int(1 if frozen else 0))
-    out = {"ll": ll.value, "g": g, "mom": mom, "slack": slack.value}
+                            C.byref(slack), C.byref(gabs), cp, C.c_int(1 if frozen else 0))
+    out = {"ll": ll.value, "g": g, "mom": mom, "slack": slack.value, "gabs": gabs.value}
     if cells is not None:
         out["cells"] = cells
     return out
@@ -198,12 +199,13 @@ def eval_batch(poses, nbr, kf_poses, tables, grids, scan, eps=1e-3, face_delta=1
     P = poses.shape[0]
     idx = np.arange(P) if idx is None else np.asarray(idx)
     res = {"ll": np.zeros(len(idx)), "g": np.zeros((len(idx), 6)), "mom": np.zeros((len(idx), 10)),
-           "slack": np.zeros(len(idx))}
+           "slack": np.zeros(len(idx)), "gabs": np.zeros(len(idx))}
     for r, i in enumerate(idx):
         ks = [int(k) for k in nbr[i] if k >= 0]
         o = eval_particle(poses[i], [kf_poses[k][i] for k in ks], [tables[k] for k in ks],
                           [grids[k] for k in ks], scan, eps, face_delta)
         res["ll"][r] = o["ll"]; res["g"][r] = o["g"]; res["mom"][r] = o["mom"]; res["slack"][r] = o["slack"]
+        res["gabs"][r] = o["gabs"]
     return res
 
 

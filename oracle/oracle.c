@@ -160,7 +160,8 @@ void ora_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 #define ORA_TAG_NORMAL 0x4E4F524Du  /* counter word 3 for motion noise */
 #define ORA_TAG_RESAMPLE 0x52534D50u /* counter word 3 for the resampling offset */
 
-static double u24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* uniform in (0,1) from the top 23 bits: (k + 1/2) 2^-23 is exact in float and double */
+static double u23(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 void ora_normal6(uint64_t seed, uint32_t i, uint32_t t, double z[6]) {
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -171,7 +172,7 @@ void ora_normal6(uint64_t seed, uint32_t i, uint32_t t, double z[6]) {
     ora_philox4x32_10(c1, key, b);
     uint32_t x[6] = {a[0], a[1], a[2], a[3], b[0], b[1]};
     for (int pair = 0; pair < 3; ++pair) {
-        double u1 = u24(x[2 * pair]), u2 = u24(x[2 * pair + 1]);
+        double u1 = u23(x[2 * pair]), u2 = u23(x[2 * pair + 1]);
         double r = sqrt(-2.0 * log(u1));
         z[2 * pair] = r * cos(2.0 * M_PI * u2);
         z[2 * pair + 1] = r * sin(2.0 * M_PI * u2);
@@ -306,8 +307,9 @@ static void lookup_grad(const double Rrel[9], const double p[3], double h, doubl
 
 void ora_eval_particle(const double Tt[12], int n_nb, const double* Tk, const double* const* tables,
                        const ora_grid* grids, const float* scan, int N, const ora_eval_params* prm,
-                       double* ll, double g[6], double mom[10], double* slack, int* cells, int frozen) {
-    double acc_ll = 0.0, acc_g[6] = {0}, acc_m[10] = {0}, acc_s = 0.0;
+                       double* ll, double g[6], double mom[10], double* slack, double* gabs,
+                       int* cells, int frozen) {
+    double acc_ll = 0.0, acc_g[6] = {0}, acc_m[10] = {0}, acc_s = 0.0, acc_a = 0.0;
     for (int s = 0; s < n_nb; ++s) {
         /* relative pose kT_t = (T_k)^-1 T_t (Eq. 4) */
         double inv[12], rel[12];
@@ -341,6 +343,7 @@ void ora_eval_particle(const double Tt[12], int n_nb, const double* Tk, const do
             double gj[6];
             lookup_grad(Rrel, p, gr->h, L, dL, prm->eps, gj);
             for (int d = 0; d < 6; ++d) acc_g[d] += gj[d];
+            acc_a += sqrt(gj[0] * gj[0] + gj[1] * gj[1] + gj[2] * gj[2] + gj[3] * gj[3] + gj[4] * gj[4] + gj[5] * gj[5]);
             double w = L / (L + prm->eps);
             acc_m[0] += w;
             acc_m[1] += w * p[0]; acc_m[2] += w * p[1]; acc_m[3] += w * p[2];
@@ -372,6 +375,7 @@ void ora_eval_particle(const double Tt[12], int n_nb, const double* Tk, const do
     if (g) for (int d = 0; d < 6; ++d) g[d] = acc_g[d];
     if (mom) for (int d = 0; d < 10; ++d) mom[d] = acc_m[d];
     if (slack) *slack = acc_s;
+    if (gabs) *gabs = acc_a;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -621,11 +625,11 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
             if (pass < sp->steps) {
                 double psi[6];
                 ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
-                                  NULL, g, mom, NULL, NULL, 0);
+                                  NULL, g, mom, NULL, NULL, NULL, 0);
                 ora_move(poses + 12 * (size_t)i, g, mom, &mp, poses + 12 * (size_t)i, psi);
             } else {
                 ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
-                                  ll + i, NULL, NULL, NULL, NULL, 0);
+                                  ll + i, NULL, NULL, NULL, NULL, NULL, 0);
             }
         }
     }

@@ -41,7 +41,9 @@ void ora_se3_log(const double T[12], double xi[6]);
 
 /* ---- Philox4x32-10 (Salmon et al., SC'11) and the draws built on it */
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
-/* Six standard normals for particle i at frame t (Box-Muller on 24-bit uniforms). */
+/* Six standard normals for particle i at frame t: Box-Muller on uniforms
+ * (k + 1/2) 2^-23 built from the top 23 bits of two Philox blocks with
+ * counters (i, t, 0|1, 'NORM'). */
 void ora_normal6(uint64_t seed, uint32_t i, uint32_t t, double z[6]);
 /* Systematic-resampling offset u in [0,1) for frame t (53-bit uniform). */
 double ora_systematic_u(uint64_t seed, uint32_t t);
@@ -77,13 +79,15 @@ typedef struct {
  *           W = sum w, S = sum w p, Q = sum w p p^T (p in the sensor frame)
  *   slack   sum over lookups within face_delta of a face of the norm of the
  *           change in that lookup's d l / d xi when the neighbouring cell is used
+ *   gabs    sum over lookups of the norm of that lookup's d l / d xi
  *   cells   if frozen == 0 and cells != NULL: the cell used per (s, j) is written
  *           (3 ints, -1 -1 -1 when outside); if frozen == 1 those cells are used
  *           instead of floor(u), their polynomial extended past the faces.
  */
 void ora_eval_particle(const double Tt[12], int n_nb, const double* Tk, const double* const* tables,
                        const ora_grid* grids, const float* scan, int N, const ora_eval_params* prm,
-                       double* ll, double g[6], double mom[10], double* slack, int* cells, int frozen);
+                       double* ll, double g[6], double mom[10], double* slack, double* gabs,
+                       int* cells, int frozen);
 
 /* Gauss-Newton matrix from the moments (Eq. 6 on the field, sigma^-2 sum w B^T B). */
 void ora_h_from_moments(const double mom[10], double sigma, double H[36]);

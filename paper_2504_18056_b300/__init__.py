@@ -1,0 +1,287 @@
+"""Thin Python binding of libgmcs.so, the C ABI declared in include/gmcs.h.
+
+Argument marshalling only: every step of the per-frame particle update runs in
+the library's CUDA kernels. Arrays may be numpy arrays (host memory) or torch
+tensors (host or CUDA memory); they must be C-contiguous with the dtypes the
+header names (float32 poses / points, float64 weights, int32 indices).
+
+The library is loaded from this package's directory. If it is missing, import
+fails loudly: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgmcs.so")
+
+OK = 0
+E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE = -1, -2, -3, -4, -5, -6
+TABLE_F32, TABLE_BF16, TABLE_F16 = 0, 1, 2
+RESAMPLE_ALWAYS, RESAMPLE_ESS_HALF, RESAMPLE_NEVER = 0, 1, 2
+MAX_NB = 8
+
+
+class GmcsError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("sigma", C.c_float), ("r_t", C.c_float), ("eps", C.c_float), ("lambda_", C.c_float),
+                ("theta_max", C.c_float), ("t_max", C.c_float), ("w_min", C.c_float), ("k_nb", C.c_int),
+                ("steps", C.c_int), ("table_dtype", C.c_int), ("resample", C.c_int), ("reserved", C.c_int),
+                ("seed", C.c_uint64)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("h", C.c_double), ("n", C.c_int * 3)]
+
+
+class StepOut(C.Structure):
+    _fields_ = [("estimate", C.c_double * 12), ("ess", C.c_double), ("max_w", C.c_double),
+                ("log_norm", C.c_double), ("argmax", C.c_int), ("resampled", C.c_int),
+                ("frame", C.c_uint32), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {"estimate": np.array(list(self.estimate)), "ess": self.ess, "max_w": self.max_w,
+                "log_norm": self.log_norm, "argmax": self.argmax, "resampled": bool(self.resampled),
+                "frame": self.frame, "status": self.status}
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("frames", C.c_uint64), ("profiling", C.c_int), ("n_kinds", C.c_int),
+                ("kind", C.c_char_p * 16), ("kind_launches", C.c_uint64 * 16), ("kind_ms", C.c_double * 16)]
+
+
+_LIB = None
+
+_SIGS = {
+    "gmcs_config_default": (None, [C.POINTER(Config)]),
+    "gmcs_create": (C.c_int, [C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "gmcs_destroy": (C.c_int, [C.c_void_p]),
+    "gmcs_init_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_add_keyframe": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Grid), C.c_void_p,
+                                    C.POINTER(C.c_int)]),
+    "gmcs_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                            C.POINTER(C.c_double), C.POINTER(StepOut)]),
+    "gmcs_last_result": (C.c_int, [C.c_void_p, C.POINTER(StepOut)]),
+    "gmcs_predict": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p, C.c_uint32]),
+    "gmcs_select": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gmcs_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gmcs_move": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "gmcs_weigh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(StepOut)]),
+    "gmcs_resample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
+    "gmcs_get_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gmcs_get_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_get_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_set_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_get_frame_diag": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gmcs_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_uint32)]),
+    "gmcs_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "gmcs_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "gmcs_reset_stats": (C.c_int, [C.c_void_p]),
+    "gmcs_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "gmcs_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib():
+    """Load libgmcs.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2504_18056_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def strerror(code):
+    return lib().gmcs_strerror(int(code)).decode()
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise GmcsError(rc, where)
+    return rc
+
+
+def _ptr(a, dtype=None):
+    """Address of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    if dtype is not None and a.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {a.dtype}")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _dbl(vals, n):
+    arr = (C.c_double * n)(*[float(v) for v in np.asarray(vals, np.float64).reshape(-1)[:n]])
+    return arr
+
+
+def default_config(**kw):
+    cfg = Config()
+    lib().gmcs_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        k2 = "lambda_" if k == "lambda" else k
+        if not hasattr(cfg, k2):
+            raise KeyError(k)
+        setattr(cfg, k2, v)
+    return cfg
+
+
+def make_grid(g):
+    gr = Grid()
+    for a in range(3):
+        gr.origin[a] = float(g["origin"][a])
+        gr.n[a] = int(g["dims"][a])
+    gr.h = float(g["h"])
+    return gr
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+class Filter:
+    """One filter session: a gmcs_ctx with its particles, keyframe tables and scratch."""
+
+    def __init__(self, max_particles, max_keyframes, max_points, stream=None, **config):
+        self.cfg = default_config(**config)
+        self.ctx = C.c_void_p()
+        st = _current_stream() if stream is None else C.c_void_p(int(stream))
+        _check(lib().gmcs_create(C.byref(self.cfg), int(max_particles), int(max_keyframes), int(max_points), st,
+                                 C.byref(self.ctx)), "gmcs_create")
+
+    def close(self):
+        if self.ctx:
+            lib().gmcs_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- state
+    def init_particles(self, poses, logw=None):
+        _check(lib().gmcs_init_particles(self.ctx, _ptr(poses), int(poses.shape[0]), _ptr(logw)), "gmcs_init_particles")
+
+    def add_keyframe(self, points, grid, kf_poses=None):
+        kid = C.c_int()
+        gr = make_grid(grid) if isinstance(grid, dict) else grid
+        _check(lib().gmcs_add_keyframe(self.ctx, _ptr(points), int(points.shape[0]), C.byref(gr), _ptr(kf_poses),
+                                       C.byref(kid)), "gmcs_add_keyframe")
+        return kid.value
+
+    def sizes(self):
+        P, K, f = C.c_int(), C.c_int(), C.c_uint32()
+        _check(lib().gmcs_get_sizes(self.ctx, C.byref(P), C.byref(K), C.byref(f)), "gmcs_get_sizes")
+        return P.value, K.value, f.value
+
+    # --- the frame
+    def step(self, scan, delta_T, cov, u=None, sync=True):
+        out = StepOut()
+        uu = C.c_double(u) if u is not None else None
+        _check(lib().gmcs_step(self.ctx, _ptr(scan), int(scan.shape[0]), _dbl(delta_T, 12), _dbl(cov, 36),
+                               C.byref(uu) if uu is not None else None, C.byref(out) if sync else None), "gmcs_step")
+        return out.as_dict() if sync else None
+
+    def last_result(self):
+        out = StepOut()
+        _check(lib().gmcs_last_result(self.ctx, C.byref(out)), "gmcs_last_result")
+        return out.as_dict()
+
+    # --- stages
+    def predict(self, delta_T, cov, z=None, frame=0):
+        _check(lib().gmcs_predict(self.ctx, _dbl(delta_T, 12), _dbl(cov, 36), _ptr(z), int(frame)), "gmcs_predict")
+
+    def select(self, nbr_out=None):
+        _check(lib().gmcs_select(self.ctx, _ptr(nbr_out)), "gmcs_select")
+        return nbr_out
+
+    def eval(self, scan, ll=None, g=None, mom=None):
+        _check(lib().gmcs_eval(self.ctx, _ptr(scan), int(scan.shape[0]), _ptr(ll), _ptr(g), _ptr(mom)), "gmcs_eval")
+
+    def move(self, scan):
+        _check(lib().gmcs_move(self.ctx, _ptr(scan), int(scan.shape[0])), "gmcs_move")
+
+    def weigh(self, ll, w_out=None):
+        res = StepOut()
+        _check(lib().gmcs_weigh(self.ctx, _ptr(ll), _ptr(w_out), C.byref(res)), "gmcs_weigh")
+        return res.as_dict()
+
+    def resample(self, w, u, anc):
+        _check(lib().gmcs_resample(self.ctx, _ptr(w), int(w.shape[0]), float(u), _ptr(anc)), "gmcs_resample")
+        return anc
+
+    # --- readback
+    def get_particles(self, poses=None, logw=None):
+        _check(lib().gmcs_get_particles(self.ctx, _ptr(poses), _ptr(logw)), "gmcs_get_particles")
+
+    def get_kf_poses(self, k, poses):
+        _check(lib().gmcs_get_kf_poses(self.ctx, int(k), _ptr(poses)), "gmcs_get_kf_poses")
+
+    def set_kf_poses(self, k, poses):
+        _check(lib().gmcs_set_kf_poses(self.ctx, int(k), _ptr(poses)), "gmcs_set_kf_poses")
+
+    def frame_diag(self, ll=None, w=None, anc=None, nbr=None):
+        _check(lib().gmcs_get_frame_diag(self.ctx, _ptr(ll), _ptr(w), _ptr(anc), _ptr(nbr)), "gmcs_get_frame_diag")
+
+    def get_table(self, k, vals):
+        _check(lib().gmcs_get_table(self.ctx, int(k), _ptr(vals)), "gmcs_get_table")
+
+    def particles(self):
+        P, _, _ = self.sizes()
+        poses = np.zeros((P, 12), np.float32)
+        logw = np.zeros(P, np.float64)
+        self.get_particles(poses, logw)
+        return poses, logw
+
+    # --- instrumentation
+    def set_profiling(self, on=True):
+        _check(lib().gmcs_set_profiling(self.ctx, 1 if on else 0), "gmcs_set_profiling")
+
+    def stats(self):
+        s = Stats()
+        _check(lib().gmcs_get_stats(self.ctx, C.byref(s)), "gmcs_get_stats")
+        kinds = {s.kind[k].decode(): {"launches": int(s.kind_launches[k]), "ms": float(s.kind_ms[k])}
+                 for k in range(s.n_kinds)}
+        return {"launches": int(s.launches), "frames": int(s.frames), "kinds": kinds}
+
+    def reset_stats(self):
+        _check(lib().gmcs_reset_stats(self.ctx), "gmcs_reset_stats")
+
+    def device_bytes(self):
+        b = C.c_uint64()
+        _check(lib().gmcs_device_bytes(self.ctx, C.byref(b)), "gmcs_device_bytes")
+        return int(b.value)

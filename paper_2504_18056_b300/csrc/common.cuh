@@ -1,0 +1,182 @@
+// common.cuh -- device-side types and helpers of the particle-update library.
+//
+// Layouts (device memory, all particle arrays padded to the context's
+// particle capacity `ld`):
+//   current poses       float [12][ld]          component c of particle i at c*ld + i
+//   keyframe poses      float [K][12][ld]       (k*12 + c)*ld + i
+//   neighbour indices   int   [k_nb][ld]
+//   log-weights         double[ld]
+//   scan                float4[N]               (x, y, z, 0) in the sensor frame
+//   tables              per keyframe, one record of 8 corner values per lattice
+//                       cell, cells ordered x fastest: FP32 records are 32 B
+//                       (two float4), BF16/FP16 records are 16 B (one uint4).
+//                       Corner order (dx + 2 dy + 4 dz).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gmcs {
+
+constexpr int kPoseC = 12;   // row-major 3x4 [R | t]
+constexpr int kMaxNb = 8;
+
+struct TableDesc {
+    const void* cells;   // packed cell records
+    float ox, oy, oz;    // lattice origin in the keyframe frame
+    float inv_h;         // 1 / h
+    int ncx, ncy, ncz;   // cells per axis (vertices - 1)
+    int dtype;           // 0 f32, 1 bf16, 2 f16
+    float h;
+    int pad;
+};
+static_assert(sizeof(TableDesc) == 48, "TableDesc layout");
+
+// ---------------------------------------------------------------- pose algebra
+
+// C = A * B for row-major 3x4 poses held in registers.
+__device__ __forceinline__ void pose_mul(const float* A, const float* B, float* C) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float a0 = A[r * 4 + 0], a1 = A[r * 4 + 1], a2 = A[r * 4 + 2];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float s = a0 * B[0 * 4 + c] + a1 * B[1 * 4 + c] + a2 * B[2 * 4 + c];
+            if (c == 3) s += A[r * 4 + 3];
+            C[r * 4 + c] = s;
+        }
+    }
+}
+
+// Relative pose rel = inv(Tk) * Tt: R = Rk^T Rt, t = Rk^T (tt - tk)  (Eq. 4).
+__device__ __forceinline__ void pose_rel(const float* Tk, const float* Tt, float* rel) {
+    const float dx = Tt[3] - Tk[3], dy = Tt[7] - Tk[7], dz = Tt[11] - Tk[11];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            rel[r * 4 + c] = Tk[0 * 4 + r] * Tt[0 * 4 + c] + Tk[1 * 4 + r] * Tt[1 * 4 + c] + Tk[2 * 4 + r] * Tt[2 * 4 + c];
+        rel[r * 4 + 3] = Tk[0 * 4 + r] * dx + Tk[1 * 4 + r] * dy + Tk[2 * 4 + r] * dz;
+    }
+}
+
+// exp of xi = [omega; v] in SE(3): R = I + a W + b W^2, t = (I + b W + c W^2) v with
+// a = sin th / th, b = (1 - cos th) / th^2 = 2 (sin(th/2) / th)^2, c = (th - sin th) / th^3;
+// power series where the closed forms lose float precision.
+__device__ __forceinline__ void se3_exp(const float* xi, float* T) {
+    const float wx = xi[0], wy = xi[1], wz = xi[2];
+    const float th2 = wx * wx + wy * wy + wz * wz;
+    float a, b, c;
+    if (th2 < 1e-6f) {
+        a = 1.f - th2 * (1.f / 6.f);
+        b = 0.5f - th2 * (1.f / 24.f);
+        c = (1.f / 6.f) - th2 * (1.f / 120.f);
+    } else {
+        const float th = sqrtf(th2);
+        const float sh = sinf(0.5f * th) / th;
+        a = sinf(th) / th;
+        b = 2.f * sh * sh;
+        if (th2 < 0.25f)
+            c = (1.f / 6.f) - th2 * ((1.f / 120.f) - th2 * ((1.f / 5040.f) - th2 * (1.f / 362880.f)));
+        else
+            c = (th - sinf(th)) / (th2 * th);
+    }
+    // W^2 = w w^T - th2 I
+    const float w[3] = {wx, wy, wz};
+    const float W[9] = {0.f, -wz, wy, wz, 0.f, -wx, -wy, wx, 0.f};
+    float V[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float W2 = w[r] * w[k] - (r == k ? th2 : 0.f);
+            const float I = (r == k) ? 1.f : 0.f;
+            T[r * 4 + k] = I + a * W[r * 3 + k] + b * W2;
+            V[r * 3 + k] = I + b * W[r * 3 + k] + c * W2;
+        }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) T[r * 4 + 3] = V[r * 3 + 0] * xi[3] + V[r * 3 + 1] * xi[4] + V[r * 3 + 2] * xi[5];
+}
+
+__device__ __forceinline__ void load_pose(const float* __restrict__ base, size_t ld, int i, float* T) {
+#pragma unroll
+    for (int c = 0; c < kPoseC; ++c) T[c] = base[(size_t)c * ld + i];
+}
+
+__device__ __forceinline__ void store_pose(float* __restrict__ base, size_t ld, int i, const float* T) {
+#pragma unroll
+    for (int c = 0; c < kPoseC; ++c) base[(size_t)c * ld + i] = T[c];
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11): ten rounds,
+// each two 32x32 -> 64-bit products mixed into the counter, key advanced by the
+// Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+constexpr uint32_t kTagNormal = 0x4E4F524Du;    // 'NORM': motion-noise counters
+constexpr uint32_t kTagResample = 0x52534D50u;  // 'RSMP': resampling offset counter
+
+// (k + 1/2) 2^-23 from the top 23 bits: exactly representable in float.
+__device__ __forceinline__ float u23(uint32_t x) { return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f); }
+
+// Six standard normals of particle i at frame t (Box-Muller on three uniform pairs).
+__device__ __forceinline__ void normal6(uint64_t seed, uint32_t i, uint32_t t, float* z) {
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint4 a = philox4x32_10(make_uint4(i, t, 0u, kTagNormal), key);
+    const uint4 b = philox4x32_10(make_uint4(i, t, 1u, kTagNormal), key);
+    const uint32_t x[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const float r = sqrtf(-2.f * logf(u23(x[2 * p])));
+        float s, c;
+        sincospif(2.f * u23(x[2 * p + 1]), &s, &c);
+        z[2 * p] = r * c;
+        z[2 * p + 1] = r * s;
+    }
+}
+
+// ---------------------------------------------------------------- table cells
+
+// The 8 corner values of cell `idx`, widened to float.
+template <int DT>
+__device__ __forceinline__ void load_cell(const void* __restrict__ cells, uint32_t idx, bool valid, float* v) {
+    if (DT == 0) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (valid) {
+            const float4* p = reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx;
+            a = __ldg(p);
+            b = __ldg(p + 1);
+        }
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (DT == 1) {
+                v[2 * e] = __uint_as_float(w[e] << 16);
+                v[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+            } else {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
+                v[2 * e] = f.x;
+                v[2 * e + 1] = f.y;
+            }
+        }
+    }
+}
+
+}  // namespace gmcs

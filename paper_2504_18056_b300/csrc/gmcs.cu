@@ -1,0 +1,959 @@
+// gmcs.cu -- the C ABI (include/gmcs.h): context, state, and the frame driver.
+//
+// The host side only validates arguments, moves caller buffers into the
+// context's device layout and enqueues kernels on the context stream; every
+// step of the per-frame path runs in the kernels of k_filter.cu and
+// k_weights.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gmcs.h"
+#include "kernels.h"
+
+using namespace gmcs;
+
+namespace {
+
+enum Kind { K_PREDICT, K_SELECT, K_PASS_GRAD, K_PASS_VALUE, K_FINISH, K_WEIGH, K_RESAMPLE, K_GATHER, K_TABLE, K_MISC, K_COUNT };
+const char* kKindName[K_COUNT] = {"predict", "select", "pass_grad", "pass_value", "finish",
+                                  "weigh", "resample", "gather", "table", "layout"};
+
+struct HostTable {
+    void* cells = nullptr;
+    size_t bytes = 0;
+    gmcs_grid grid;
+    int dtype = 0;
+};
+
+struct EvPair {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct gmcs_ctx {
+    gmcs_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int Pmax = 0, Kmax = 0, Nmax = 0;
+    size_t ld = 0;
+    int P = 0, K = 0;
+    uint32_t frame = 0;
+    bool have_particles = false;
+    int cur = 0;
+    float* pose[2] = {nullptr, nullptr};
+    float* kf[2] = {nullptr, nullptr};
+    double* logw = nullptr;
+    double* w = nullptr;             // normalised weights of the last frame
+    float* ll = nullptr;
+    int* nbr = nullptr;
+    float* part = nullptr;
+    size_t part_floats = 0;
+    float4* scan = nullptr;
+    float* stage = nullptr;          // N x 3 points / P x 6 noise staging
+    size_t stage_floats = 0;
+    double* wpart = nullptr;
+    unsigned* counter = nullptr;
+    WeighResult* d_res = nullptr;
+    WeighResult* h_res = nullptr;    // pinned
+    unsigned long long* cl = nullptr;
+    unsigned long long* btot = nullptr;
+    int* anc = nullptr;
+    TableDesc* d_tables = nullptr;
+    std::vector<HostTable> tables;
+    unsigned* d2 = nullptr;
+    size_t d2_cap = 0;
+    size_t dev_bytes = 0;
+    // stats
+    uint64_t launches = 0, frames = 0;
+    uint64_t kind_launches[K_COUNT] = {0};
+    double kind_ms[K_COUNT] = {0};
+    bool profiling = false;
+    std::vector<EvPair> pending;
+    std::vector<cudaEvent_t> free_events;
+    gmcs_step_out last{};
+    bool last_valid = false;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GMCS_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return GMCS_E_OOM;
+    }
+    return GMCS_E_CUDA;
+}
+
+#define CK(expr)                                   \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) return cuda_status(_e); \
+    } while (0)
+
+template <typename T>
+int dalloc(gmcs_ctx* c, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return GMCS_E_OOM;
+    }
+    c->dev_bytes += count * sizeof(T);
+    return GMCS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t take_event(gmcs_ctx* c) {
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one launch: count it, and time it with events when profiling.
+struct Launch {
+    gmcs_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Launch(gmcs_ctx* ctx, int k) : c(ctx), kind(k) {
+        if (c->profiling) {
+            a = take_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~Launch() {
+        c->launches++;
+        c->kind_launches[kind]++;
+        if (c->profiling) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->stream);
+            c->pending.push_back({kind, a, b});
+        }
+    }
+};
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GMCS_OK : cuda_status(e);
+}
+
+void harvest(gmcs_ctx* c) {
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+            c->kind_ms[p.kind] += ms;
+        c->free_events.push_back(p.a);
+        c->free_events.push_back(p.b);
+    }
+    c->pending.clear();
+    cudaGetLastError();
+}
+
+// Chunking of the scan for the lookup pass: enough CTAs for several waves on
+// 148 SMs, at most kMaxGroups groups of kPassWarps chunks, chunks of >= 8 points.
+void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len) {
+    const int nt = (P + 31) / 32;
+    const int target = 148 * 8 * 4;
+    int g = (target + nt - 1) / nt;
+    g = std::max(1, std::min(g, kMaxGroups));
+    const int max_chunks = std::max(1, (N + 7) / 8);
+    while (g > 1 && g * kPassWarps > max_chunks) --g;
+    const int chunks = g * kPassWarps;
+    *ntiles = nt;
+    *groups = g;
+    *chunk_len = std::max(1, (N + chunks - 1) / chunks);
+}
+
+int upload_scan(gmcs_ctx* c, const float* scan, int N) {
+    if (N < 0 || (N > 0 && !scan)) return GMCS_E_INVALID;
+    if (N > c->Nmax) return GMCS_E_CAPACITY;
+    if (N == 0) return GMCS_OK;
+    const float* src = scan;
+    if (!is_device_ptr(scan)) {
+        CK(cudaMemcpyAsync(c->stage, scan, sizeof(float) * 3 * (size_t)N, cudaMemcpyHostToDevice, c->stream));
+        src = c->stage;
+    }
+    {
+        Launch L(c, K_MISC);
+        launch_scan_pack(src, N, c->scan, c->stream);
+    }
+    return check_launch();
+}
+
+int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw) {
+    int nt, groups, chunk;
+    pass_shape(c->P, N, &nt, &groups, &chunk);
+    PassArgs pa;
+    pa.pose = c->pose[c->cur];
+    pa.kf = c->kf[c->cur];
+    pa.nbr = c->nbr;
+    pa.tables = c->d_tables;
+    pa.scan = c->scan;
+    pa.part = c->part;
+    pa.ld = c->ld;
+    pa.P = c->P;
+    pa.N = N;
+    pa.k_nb = std::min(c->cfg.k_nb, c->K);
+    pa.ntiles = nt;
+    pa.groups = groups;
+    pa.chunk_len = chunk;
+    pa.eps = c->cfg.eps;
+    {
+        Launch L(c, grad ? K_PASS_GRAD : K_PASS_VALUE);
+        launch_pass(pa, c->cfg.table_dtype, grad, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    FinishArgs fa;
+    fa.part = c->part;
+    fa.pose = c->pose[c->cur];
+    fa.ld = c->ld;
+    fa.P = c->P;
+    fa.groups = groups;
+    fa.do_move = move ? 1 : 0;
+    fa.sigma = c->cfg.sigma;
+    fa.lambda = c->cfg.lambda;
+    fa.theta_max = c->cfg.theta_max;
+    fa.t_max = c->cfg.t_max;
+    fa.w_min = c->cfg.w_min;
+    fa.out_ll = out_ll;
+    fa.out_g = out_g;
+    fa.out_mom = out_mom;
+    fa.logw = logw;
+    {
+        Launch L(c, K_FINISH);
+        launch_finish(fa, grad, c->stream);
+    }
+    return check_launch();
+}
+
+int run_select(gmcs_ctx* c, int* nbr_out_dev) {
+    SelectArgs sa;
+    sa.pose = c->pose[c->cur];
+    sa.kf = c->kf[c->cur];
+    sa.ld = c->ld;
+    sa.P = c->P;
+    sa.K = c->K;
+    sa.k_nb = std::min(c->cfg.k_nb, std::max(c->K, 1));
+    sa.nbr = c->nbr;
+    sa.nbr_out = nbr_out_dev;
+    {
+        Launch L(c, K_SELECT);
+        launch_select(sa, c->stream);
+    }
+    return check_launch();
+}
+
+int run_predict(gmcs_ctx* c, const double dT[12], const double cov[36], const float* z_dev, uint32_t frame) {
+    for (int e = 0; e < 12; ++e)
+        if (!std::isfinite(dT[e])) return GMCS_E_INVALID;
+    for (int e = 0; e < 36; ++e)
+        if (!std::isfinite(cov[e])) return GMCS_E_INVALID;
+    PredictArgs a;
+    a.pose = c->pose[c->cur];
+    a.ld = c->ld;
+    a.P = c->P;
+    for (int e = 0; e < 12; ++e) a.dT[e] = (float)dT[e];
+    for (int e = 0; e < 36; ++e) a.cov[e] = (float)cov[e];
+    a.z = z_dev;
+    a.seed = c->cfg.seed;
+    a.frame = frame;
+    {
+        Launch L(c, K_PREDICT);
+        launch_predict(a, c->stream);
+    }
+    return check_launch();
+}
+
+int run_weigh(gmcs_ctx* c, const float* ll_dev) {
+    WeighArgs a;
+    a.logw = c->logw;
+    a.ll = ll_dev;
+    a.P = c->P;
+    a.policy = c->cfg.resample;
+    a.part = c->wpart;
+    a.counter = c->counter;
+    a.res = c->d_res;
+    a.pose = c->pose[c->cur];
+    a.ld = c->ld;
+    {
+        Launch L(c, K_WEIGH);
+        launch_weigh(a, weigh_blocks(c->P), c->stream);
+    }
+    return check_launch();
+}
+
+// Quantise, scan, search (ancestors into c->anc). w_dev: given weights or null.
+int run_resample_core(gmcs_ctx* c, int P, const double* w_dev, const WeighResult* res, double* w_out,
+                      double u, int u_from_philox, uint32_t frame, int* anc_dev) {
+    const int nb = (P + kScanBlock - 1) / kScanBlock;
+    ScanArgs sa;
+    sa.logw = c->logw;
+    sa.w = w_dev;
+    sa.res = res;
+    sa.w_out = w_out;
+    sa.P = P;
+    sa.cl = c->cl;
+    sa.btot = c->btot;
+    {
+        Launch L(c, K_RESAMPLE);
+        launch_resample_scan(sa, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    {
+        Launch L(c, K_RESAMPLE);
+        launch_scan_totals(c->btot, nb, c->stream);
+    }
+    rc = check_launch();
+    if (rc) return rc;
+    SearchArgs se;
+    se.cl = c->cl;
+    se.boff = c->btot;
+    se.nblocks = nb;
+    se.P = P;
+    se.u = u;
+    se.u_from_philox = u_from_philox;
+    se.seed = c->cfg.seed;
+    se.frame = frame;
+    se.res = res;
+    se.anc = anc_dev;
+    {
+        Launch L(c, K_RESAMPLE);
+        launch_resample_search(se, c->stream);
+    }
+    return check_launch();
+}
+
+int run_gather(gmcs_ctx* c, const WeighResult* res) {
+    GatherArgs g;
+    g.pose_src = c->pose[c->cur];
+    g.pose_dst = c->pose[1 - c->cur];
+    g.kf_src = c->kf[c->cur];
+    g.kf_dst = c->kf[1 - c->cur];
+    g.ld = c->ld;
+    g.P = c->P;
+    g.K = c->K;
+    g.anc = c->anc;
+    g.logw = c->logw;
+    g.res = res;
+    {
+        Launch L(c, K_GATHER);
+        launch_gather(g, c->stream);
+    }
+    int rc = check_launch();
+    if (rc == GMCS_OK) c->cur = 1 - c->cur;
+    return rc;
+}
+
+void fill_out(const WeighResult& r, uint32_t frame, gmcs_step_out* o) {
+    for (int e = 0; e < 12; ++e) o->estimate[e] = r.est[e];
+    o->ess = r.ess;
+    o->max_w = r.max_w;
+    o->log_norm = r.M + r.logS;
+    o->argmax = r.argmax;
+    o->resampled = r.do_resample;
+    o->frame = frame;
+    o->status = r.nonfinite ? GMCS_E_NONFINITE : GMCS_OK;
+}
+
+// Copy n bytes from device src to dst (host or device); host destinations synchronise.
+int copy_out(gmcs_ctx* c, void* dst, const void* src, size_t n) {
+    const bool dev = is_device_ptr(dst);
+    CK(cudaMemcpyAsync(dst, src, n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!dev) CK(cudaStreamSynchronize(c->stream));
+    return GMCS_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+void gmcs_config_default(gmcs_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->sigma = 0.2f;
+    cfg->r_t = 1.0f;
+    cfg->eps = 1e-3f;
+    cfg->lambda = 1e-3f;
+    cfg->theta_max = (float)(2.0 * M_PI / 180.0);
+    cfg->t_max = 0.1f;
+    cfg->w_min = 1e-6f;
+    cfg->k_nb = 3;
+    cfg->steps = 3;
+    cfg->table_dtype = GMCS_TABLE_F32;
+    cfg->resample = GMCS_RESAMPLE_ALWAYS;
+    cfg->seed = 0;
+}
+
+const char* gmcs_strerror(int code) {
+    switch (code) {
+        case GMCS_OK: return "ok";
+        case GMCS_E_INVALID: return "invalid argument";
+        case GMCS_E_OOM: return "out of device memory";
+        case GMCS_E_CUDA: return "CUDA error";
+        case GMCS_E_CAPACITY: return "capacity exceeded";
+        case GMCS_E_STATE: return "call out of order";
+        case GMCS_E_NONFINITE: return "weights degenerated (reset to uniform)";
+        default: return "unknown error";
+    }
+}
+
+static bool config_ok(const gmcs_config* c) {
+    return c && c->sigma > 0.f && c->r_t > 0.f && c->eps > 0.f && c->lambda >= 0.f && c->theta_max > 0.f &&
+           c->t_max > 0.f && c->w_min >= 0.f && c->k_nb >= 1 && c->k_nb <= GMCS_MAX_NB && c->steps >= 0 &&
+           c->steps <= 64 && c->table_dtype >= 0 && c->table_dtype <= 2 && c->resample >= 0 && c->resample <= 2;
+}
+
+int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, int max_points, void* cuda_stream,
+                gmcs_ctx** out) {
+    if (!out) return GMCS_E_INVALID;
+    *out = nullptr;
+    if (!config_ok(cfg) || max_particles <= 0 || max_keyframes <= 0 || max_points <= 0) return GMCS_E_INVALID;
+    if ((size_t)max_particles * (size_t)(1 + max_keyframes) > ((size_t)1 << 34)) return GMCS_E_INVALID;
+    gmcs_ctx* c = new (std::nothrow) gmcs_ctx();
+    if (!c) return GMCS_E_OOM;
+    c->cfg = *cfg;
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->Pmax = max_particles;
+    c->Kmax = max_keyframes;
+    c->Nmax = max_points;
+    c->ld = ((size_t)max_particles + 31) / 32 * 32;
+    const size_t ld = c->ld;
+    const int nb = (max_particles + kScanBlock - 1) / kScanBlock;
+    c->part_floats = std::max((size_t)kMaxGroups * kAccGrad * ld, (size_t)12 * ld);
+    c->stage_floats = std::max((size_t)3 * max_points, (size_t)6 * ld);
+    int rc = GMCS_OK;
+    for (int b = 0; b < 2 && !rc; ++b) {
+        rc = dalloc(c, &c->pose[b], (size_t)kPoseC * ld);
+        if (!rc) rc = dalloc(c, &c->kf[b], (size_t)kPoseC * ld * max_keyframes);
+    }
+    if (!rc) rc = dalloc(c, &c->logw, ld);
+    if (!rc) rc = dalloc(c, &c->ll, ld);
+    if (!rc) rc = dalloc(c, &c->w, ld);
+    if (!rc) rc = dalloc(c, &c->nbr, (size_t)GMCS_MAX_NB * ld);
+    if (!rc) rc = dalloc(c, &c->part, c->part_floats);
+    if (!rc) rc = dalloc(c, &c->scan, (size_t)max_points);
+    if (!rc) rc = dalloc(c, &c->stage, c->stage_floats);
+    if (!rc) rc = dalloc(c, &c->wpart, (size_t)4 * 148 * 4);
+    if (!rc) rc = dalloc(c, &c->counter, 1);
+    if (!rc) rc = dalloc(c, &c->d_res, 1);
+    if (!rc) rc = dalloc(c, &c->cl, ld);
+    if (!rc) rc = dalloc(c, &c->btot, (size_t)nb + 1);
+    if (!rc) rc = dalloc(c, &c->anc, ld);
+    if (!rc) rc = dalloc(c, &c->d_tables, (size_t)max_keyframes);
+    if (!rc && cudaMallocHost((void**)&c->h_res, sizeof(WeighResult)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_res = nullptr;
+        rc = GMCS_E_OOM;
+    }
+    if (!rc && cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
+    if (!rc && cudaMemsetAsync(c->nbr, 0xff, sizeof(int) * GMCS_MAX_NB * ld, c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
+    if (!rc && cudaMemsetAsync(c->d_res, 0, sizeof(WeighResult), c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
+    if (rc) {
+        gmcs_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return GMCS_OK;
+}
+
+int gmcs_destroy(gmcs_ctx* c) {
+    if (!c) return GMCS_OK;
+    cudaStreamSynchronize(c->stream);
+    harvest(c);
+    for (auto e : c->free_events) cudaEventDestroy(e);
+    for (auto& t : c->tables) cudaFree(t.cells);
+    void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->ll, c->nbr, c->part, c->scan,
+                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->anc, c->d_tables, c->d2};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_res) cudaFreeHost(c->h_res);
+    cudaGetLastError();
+    delete c;
+    return GMCS_OK;
+}
+
+int gmcs_init_particles(gmcs_ctx* c, const float* poses, int P, const double* logw) {
+    if (!c || !poses || P <= 0) return GMCS_E_INVALID;
+    if (P > c->Pmax) return GMCS_E_CAPACITY;
+    // stage the P x 12 block in the scratch buffer, then transpose to SoA
+    CK(cudaMemcpyAsync(c->part, poses, sizeof(float) * 12 * (size_t)P, cudaMemcpyDefault, c->stream));
+    {
+        Launch L(c, K_MISC);
+        launch_aos_to_soa(c->part, P, 12, c->pose[c->cur], c->ld, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    if (logw) {
+        CK(cudaMemcpyAsync(c->logw, logw, sizeof(double) * P, cudaMemcpyDefault, c->stream));
+    } else {
+        std::vector<double> u(P, -std::log((double)P));
+        CK(cudaMemcpyAsync(c->logw, u.data(), sizeof(double) * P, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    c->P = P;
+    c->frame = 0;
+    c->have_particles = true;
+    c->last_valid = false;
+    return GMCS_OK;
+}
+
+int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* grid, const float* kf_poses, int* kf_id) {
+    if (!c || !grid || n < 0 || (n > 0 && !pts)) return GMCS_E_INVALID;
+    if (!c->have_particles) return GMCS_E_STATE;
+    if (c->K >= c->Kmax) return GMCS_E_CAPACITY;
+    for (int a = 0; a < 3; ++a)
+        if (grid->n[a] < 2 || !std::isfinite(grid->origin[a])) return GMCS_E_INVALID;
+    if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return GMCS_E_INVALID;
+    const size_t nx = grid->n[0], ny = grid->n[1], nz = grid->n[2];
+    const size_t nv = nx * ny * nz;
+    const size_t ncell = (nx - 1) * (ny - 1) * (nz - 1);
+    if (ncell >= ((size_t)1 << 31)) return GMCS_E_INVALID;
+    const int dtype = c->cfg.table_dtype;
+    const size_t rec = dtype == 0 ? 32 : 16;
+    HostTable t;
+    t.grid = *grid;
+    t.dtype = dtype;
+    t.bytes = ncell * rec;
+    if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return GMCS_E_OOM;
+    }
+    // squared-distance scratch, grown to the largest table seen
+    if (c->d2_cap < nv) {
+        if (c->d2) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->d2);
+            c->dev_bytes -= c->d2_cap * sizeof(unsigned);
+            c->d2 = nullptr;
+            c->d2_cap = 0;
+        }
+        if (cudaMalloc((void**)&c->d2, nv * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(t.cells);
+            return GMCS_E_OOM;
+        }
+        c->d2_cap = nv;
+        c->dev_bytes += nv * sizeof(unsigned);
+    }
+    // points: device pointer used in place, host points staged (grows the stage if needed)
+    const float* dpts = pts;
+    float* tmp = nullptr;
+    if (n > 0 && !is_device_ptr(pts)) {
+        if (cudaMalloc((void**)&tmp, sizeof(float) * 3 * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(t.cells);
+            return GMCS_E_OOM;
+        }
+        if (cudaMemcpyAsync(tmp, pts, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            cudaFree(tmp);
+            cudaFree(t.cells);
+            return GMCS_E_CUDA;
+        }
+        dpts = tmp;
+    }
+    int rc = GMCS_OK;
+    {
+        Launch L(c, K_TABLE);
+        launch_fill_u32(c->d2, nv, 0x7f800000u, c->stream);
+    }
+    SplatArgs sa;
+    sa.pts = dpts;
+    sa.n = n;
+    for (int a = 0; a < 3; ++a) {
+        sa.o_hi[a] = (float)grid->origin[a];
+        sa.o_lo[a] = (float)(grid->origin[a] - (double)sa.o_hi[a]);
+    }
+    sa.h_hi = (float)grid->h;
+    sa.h_lo = (float)(grid->h - (double)sa.h_hi);
+    sa.nx = (int)nx;
+    sa.ny = (int)ny;
+    sa.nz = (int)nz;
+    sa.r_t = c->cfg.r_t;
+    sa.d2 = c->d2;
+    {
+        Launch L(c, K_TABLE);
+        launch_splat(sa, c->stream);
+    }
+    PackArgs pa;
+    pa.d2 = c->d2;
+    pa.nx = (int)nx;
+    pa.ny = (int)ny;
+    pa.nz = (int)nz;
+    pa.inv_two_sigma2 = 1.0f / (2.0f * c->cfg.sigma * c->cfg.sigma);
+    pa.r_t2 = c->cfg.r_t * c->cfg.r_t;
+    pa.cells = t.cells;
+    pa.dtype = dtype;
+    {
+        Launch L(c, K_TABLE);
+        launch_pack(pa, c->stream);
+    }
+    rc = check_launch();
+    if (tmp) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+    }
+    if (rc) {
+        cudaFree(t.cells);
+        return rc;
+    }
+    TableDesc td;
+    std::memset(&td, 0, sizeof(td));
+    td.cells = t.cells;
+    td.ox = (float)grid->origin[0];
+    td.oy = (float)grid->origin[1];
+    td.oz = (float)grid->origin[2];
+    td.inv_h = (float)(1.0 / grid->h);
+    td.h = (float)grid->h;
+    td.ncx = (int)nx - 1;
+    td.ncy = (int)ny - 1;
+    td.ncz = (int)nz - 1;
+    td.dtype = dtype;
+    const int k = c->K;
+    rc = cuda_status(cudaMemcpyAsync(c->d_tables + k, &td, sizeof(td), cudaMemcpyHostToDevice, c->stream));
+    if (!rc) {
+        float* dst = c->kf[c->cur] + (size_t)k * kPoseC * c->ld;
+        if (kf_poses) {
+            rc = cuda_status(cudaMemcpyAsync(c->part, kf_poses, sizeof(float) * 12 * (size_t)c->P, cudaMemcpyDefault,
+                                             c->stream));
+            if (!rc) {
+                Launch L(c, K_MISC);
+                launch_aos_to_soa(c->part, c->P, 12, dst, c->ld, c->stream);
+            }
+        } else {
+            rc = cuda_status(cudaMemcpy2DAsync(dst, c->ld * sizeof(float), c->pose[c->cur], c->ld * sizeof(float),
+                                               c->P * sizeof(float), kPoseC, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        if (!rc) rc = check_launch();
+    }
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));   // td lives on this stack frame
+    if (rc) {
+        cudaFree(t.cells);
+        return rc;
+    }
+    c->dev_bytes += t.bytes;
+    c->tables.push_back(t);
+    c->K = k + 1;
+    if (kf_id) *kf_id = k;
+    return GMCS_OK;
+}
+
+int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], const double cov[36],
+              const double* u_override, gmcs_step_out* out) {
+    if (!c || !delta_T || !cov) return GMCS_E_INVALID;
+    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
+    if (u_override && !(*u_override >= 0.0 && *u_override < 1.0)) return GMCS_E_INVALID;
+    int rc = upload_scan(c, scan, N);
+    if (rc) return rc;
+    const uint32_t frame = c->frame;
+    if ((rc = run_predict(c, delta_T, cov, nullptr, frame))) return rc;
+    if ((rc = run_select(c, nullptr))) return rc;
+    for (int s = 0; s < c->cfg.steps; ++s)
+        if ((rc = run_pass(c, N, true, true, nullptr, nullptr, nullptr, nullptr))) return rc;
+    if ((rc = run_pass(c, N, false, false, c->ll, nullptr, nullptr, c->logw))) return rc;
+    if ((rc = run_weigh(c, nullptr))) return rc;
+    if (c->cfg.resample == GMCS_RESAMPLE_NEVER) {
+        {
+            Launch L(c, K_WEIGH);
+            launch_normalize(c->logw, c->P, c->d_res, c->w, c->anc, c->stream);
+        }
+        if ((rc = check_launch())) return rc;
+    } else {
+        const double u = u_override ? *u_override : 0.0;
+        if ((rc = run_resample_core(c, c->P, nullptr, c->d_res, c->w, u, u_override ? 0 : 1, frame, c->anc)))
+            return rc;
+        if ((rc = run_gather(c, c->d_res))) return rc;
+    }
+    CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(WeighResult), cudaMemcpyDeviceToHost, c->stream));
+    c->frame = frame + 1;
+    c->frames++;
+    c->last_valid = true;
+    if (out) {
+        CK(cudaStreamSynchronize(c->stream));
+        fill_out(*c->h_res, frame, out);
+        c->last = *out;
+    }
+    return GMCS_OK;
+}
+
+int gmcs_last_result(gmcs_ctx* c, gmcs_step_out* out) {
+    if (!c || !out) return GMCS_E_INVALID;
+    if (!c->last_valid) return GMCS_E_STATE;
+    CK(cudaStreamSynchronize(c->stream));
+    fill_out(*c->h_res, c->frame - 1, out);
+    return GMCS_OK;
+}
+
+int gmcs_predict(gmcs_ctx* c, const double delta_T[12], const double cov[36], const float* z, uint32_t frame) {
+    if (!c || !delta_T || !cov) return GMCS_E_INVALID;
+    if (!c->have_particles) return GMCS_E_STATE;
+    const float* zd = z;
+    if (z && !is_device_ptr(z)) {
+        CK(cudaMemcpyAsync(c->stage, z, sizeof(float) * 6 * (size_t)c->P, cudaMemcpyHostToDevice, c->stream));
+        zd = c->stage;
+    }
+    return run_predict(c, delta_T, cov, zd, frame);
+}
+
+int gmcs_select(gmcs_ctx* c, int* nbr_out) {
+    if (!c) return GMCS_E_INVALID;
+    if (!c->have_particles) return GMCS_E_STATE;
+    const int knb = std::min(c->cfg.k_nb, std::max(c->K, 1));
+    const bool dev = nbr_out && is_device_ptr(nbr_out);
+    int* tmp = nullptr;
+    if (nbr_out && !dev) tmp = reinterpret_cast<int*>(c->part);   // P x k_nb ints fit in the scratch
+    int rc = run_select(c, dev ? nbr_out : tmp);
+    if (rc) return rc;
+    if (tmp) return copy_out(c, nbr_out, tmp, sizeof(int) * (size_t)c->P * knb);
+    return GMCS_OK;
+}
+
+int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float* mom) {
+    if (!c) return GMCS_E_INVALID;
+    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
+    int rc = upload_scan(c, scan, N);
+    if (rc) return rc;
+    // outputs go to device staging (ll: c->ll; g and mom: the stage buffer) unless device pointers were given
+    const bool gd = g && is_device_ptr(g), md = mom && is_device_ptr(mom), ld_ = ll && is_device_ptr(ll);
+    float* dg = g ? (gd ? g : nullptr) : nullptr;
+    float* dm = mom ? (md ? mom : nullptr) : nullptr;
+    float* tmp = nullptr;
+    if ((g && !gd) || (mom && !md)) {
+        if (cudaMalloc((void**)&tmp, sizeof(float) * 16 * (size_t)c->P) != cudaSuccess) {
+            cudaGetLastError();
+            return GMCS_E_OOM;
+        }
+        if (g && !gd) dg = tmp;
+        if (mom && !md) dm = tmp + 6 * (size_t)c->P;
+    }
+    float* dl = ll ? (ld_ ? ll : c->ll) : nullptr;
+    const bool grad = (g != nullptr) || (mom != nullptr);
+    rc = run_pass(c, N, grad, false, dl, dg, dm, nullptr);
+    if (!rc && ll && !ld_) rc = copy_out(c, ll, c->ll, sizeof(float) * c->P);
+    if (!rc && g && !gd) rc = copy_out(c, g, dg, sizeof(float) * 6 * (size_t)c->P);
+    if (!rc && mom && !md) rc = copy_out(c, mom, dm, sizeof(float) * 10 * (size_t)c->P);
+    if (tmp) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+    }
+    return rc;
+}
+
+int gmcs_move(gmcs_ctx* c, const float* scan, int N) {
+    if (!c) return GMCS_E_INVALID;
+    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
+    int rc = upload_scan(c, scan, N);
+    if (rc) return rc;
+    return run_pass(c, N, true, true, nullptr, nullptr, nullptr, nullptr);
+}
+
+int gmcs_weigh(gmcs_ctx* c, const float* ll, double* w_out, gmcs_step_out* res) {
+    if (!c || !ll) return GMCS_E_INVALID;
+    if (!c->have_particles) return GMCS_E_STATE;
+    const float* dll = ll;
+    if (!is_device_ptr(ll)) {
+        CK(cudaMemcpyAsync(c->ll, ll, sizeof(float) * c->P, cudaMemcpyHostToDevice, c->stream));
+        dll = c->ll;
+    }
+    int rc = run_weigh(c, dll);
+    if (rc) return rc;
+    if (w_out) {
+        const bool dev = is_device_ptr(w_out);
+        double* dw = dev ? w_out : reinterpret_cast<double*>(c->part);
+        ScanArgs sa;   // the scan kernel's first half writes the normalised weights
+        sa.logw = c->logw;
+        sa.w = nullptr;
+        sa.res = c->d_res;
+        sa.w_out = dw;
+        sa.P = c->P;
+        sa.cl = c->cl;
+        sa.btot = c->btot;
+        {
+            Launch L(c, K_RESAMPLE);
+            launch_resample_scan(sa, c->stream);
+        }
+        if ((rc = check_launch())) return rc;
+        if (!dev && (rc = copy_out(c, w_out, dw, sizeof(double) * c->P))) return rc;
+    }
+    if (res) {
+        CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(WeighResult), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        fill_out(*c->h_res, c->frame, res);
+    }
+    return GMCS_OK;
+}
+
+int gmcs_resample(gmcs_ctx* c, const double* w, int P, double u, int* anc) {
+    if (!c || !w || !anc || P <= 0) return GMCS_E_INVALID;
+    if (P > c->Pmax) return GMCS_E_CAPACITY;
+    if (!(u >= 0.0 && u < 1.0)) return GMCS_E_INVALID;
+    const double* dw = w;
+    if (!is_device_ptr(w)) {
+        CK(cudaMemcpyAsync(c->part, w, sizeof(double) * P, cudaMemcpyHostToDevice, c->stream));
+        dw = reinterpret_cast<const double*>(c->part);
+    }
+    const bool dev = is_device_ptr(anc);
+    int rc = run_resample_core(c, P, dw, nullptr, nullptr, u, 0, 0, dev ? anc : c->anc);
+    if (rc) return rc;
+    if (!dev) return copy_out(c, anc, c->anc, sizeof(int) * P);
+    return GMCS_OK;
+}
+
+int gmcs_get_particles(gmcs_ctx* c, float* poses, double* logw) {
+    if (!c) return GMCS_E_INVALID;
+    if (!c->have_particles) return GMCS_E_STATE;
+    if (poses) {
+        {
+            Launch L(c, K_MISC);
+            launch_soa_to_aos(c->pose[c->cur], c->ld, c->P, 12, c->part, c->stream);
+        }
+        int rc = check_launch();
+        if (rc) return rc;
+        if ((rc = copy_out(c, poses, c->part, sizeof(float) * 12 * (size_t)c->P))) return rc;
+    }
+    if (logw) return copy_out(c, logw, c->logw, sizeof(double) * c->P);
+    return GMCS_OK;
+}
+
+int gmcs_get_kf_poses(gmcs_ctx* c, int k, float* poses) {
+    if (!c || !poses || k < 0 || k >= c->K) return GMCS_E_INVALID;
+    {
+        Launch L(c, K_MISC);
+        launch_soa_to_aos(c->kf[c->cur] + (size_t)k * kPoseC * c->ld, c->ld, c->P, 12, c->part, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    return copy_out(c, poses, c->part, sizeof(float) * 12 * (size_t)c->P);
+}
+
+int gmcs_set_kf_poses(gmcs_ctx* c, int k, const float* poses) {
+    if (!c || !poses || k < 0 || k >= c->K) return GMCS_E_INVALID;
+    CK(cudaMemcpyAsync(c->part, poses, sizeof(float) * 12 * (size_t)c->P, cudaMemcpyDefault, c->stream));
+    {
+        Launch L(c, K_MISC);
+        launch_aos_to_soa(c->part, c->P, 12, c->kf[c->cur] + (size_t)k * kPoseC * c->ld, c->ld, c->stream);
+    }
+    int rc = check_launch();
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+int gmcs_get_frame_diag(gmcs_ctx* c, float* ll, double* w, int* anc, int* nbr) {
+    if (!c) return GMCS_E_INVALID;
+    if (!c->last_valid) return GMCS_E_STATE;
+    int rc = GMCS_OK;
+    if (ll && (rc = copy_out(c, ll, c->ll, sizeof(float) * c->P))) return rc;
+    if (w && (rc = copy_out(c, w, c->w, sizeof(double) * c->P))) return rc;
+    if (anc && (rc = copy_out(c, anc, c->anc, sizeof(int) * c->P))) return rc;
+    if (nbr) {
+        const int knb = std::min(c->cfg.k_nb, std::max(c->K, 1));
+        {
+            Launch L(c, K_MISC);   // [k_nb][ld] -> P x k_nb, bit copies
+            launch_soa_to_aos(reinterpret_cast<const float*>(c->nbr), c->ld, c->P, knb, c->part, c->stream);
+        }
+        if ((rc = check_launch())) return rc;
+        if ((rc = copy_out(c, nbr, c->part, sizeof(int) * (size_t)c->P * knb))) return rc;
+    }
+    return GMCS_OK;
+}
+
+int gmcs_get_table(gmcs_ctx* c, int k, float* vals) {
+    if (!c || !vals || k < 0 || k >= c->K) return GMCS_E_INVALID;
+    const HostTable& t = c->tables[k];
+    const size_t nv = (size_t)t.grid.n[0] * t.grid.n[1] * t.grid.n[2];
+    const bool dev = is_device_ptr(vals);
+    float* dst = dev ? vals : nullptr;
+    if (!dev) {
+        if (cudaMalloc((void**)&dst, nv * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return GMCS_E_OOM;
+        }
+    }
+    {
+        Launch L(c, K_MISC);
+        launch_unpack(t.cells, t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], dst, c->stream);
+    }
+    int rc = check_launch();
+    if (!rc && !dev) rc = copy_out(c, vals, dst, nv * sizeof(float));
+    if (!dev) cudaFree(dst);
+    return rc;
+}
+
+int gmcs_get_sizes(gmcs_ctx* c, int* P, int* K, uint32_t* frame) {
+    if (!c) return GMCS_E_INVALID;
+    if (P) *P = c->P;
+    if (K) *K = c->K;
+    if (frame) *frame = c->frame;
+    return GMCS_OK;
+}
+
+int gmcs_set_profiling(gmcs_ctx* c, int on) {
+    if (!c) return GMCS_E_INVALID;
+    c->profiling = on != 0;
+    return GMCS_OK;
+}
+
+int gmcs_get_stats(gmcs_ctx* c, gmcs_stats* out) {
+    if (!c || !out) return GMCS_E_INVALID;
+    harvest(c);
+    std::memset(out, 0, sizeof(*out));
+    out->launches = c->launches;
+    out->frames = c->frames;
+    out->profiling = c->profiling ? 1 : 0;
+    out->n_kinds = K_COUNT;
+    for (int k = 0; k < K_COUNT; ++k) {
+        out->kind[k] = kKindName[k];
+        out->kind_launches[k] = c->kind_launches[k];
+        out->kind_ms[k] = c->kind_ms[k];
+    }
+    return GMCS_OK;
+}
+
+int gmcs_reset_stats(gmcs_ctx* c) {
+    if (!c) return GMCS_E_INVALID;
+    harvest(c);
+    c->launches = 0;
+    c->frames = 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        c->kind_launches[k] = 0;
+        c->kind_ms[k] = 0.0;
+    }
+    return GMCS_OK;
+}
+
+int gmcs_device_bytes(gmcs_ctx* c, uint64_t* bytes) {
+    if (!c || !bytes) return GMCS_E_INVALID;
+    *bytes = c->dev_bytes;
+    return GMCS_OK;
+}
+
+}  // extern "C"

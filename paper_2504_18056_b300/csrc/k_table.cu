@@ -1,0 +1,154 @@
+// k_table.cu -- keyframe likelihood tables (map insertion, not on the per-frame path).
+//
+// A keyframe table holds, at every lattice vertex, exp(-d^2 / 2 sigma^2) with d
+// the distance to the nearest keyframe point, 0 where d > r_t. It is built in
+// two launches: each point relaxes the squared distance of every vertex within
+// r_t (atomicMin on the float bit pattern, which orders like the value for
+// non-negative floats), then every cell packs its 8 corner values into one
+// record so that a lookup is a single 32 B (FP32) or 16 B (BF16/FP16) load.
+#include "kernels.h"
+
+namespace gmcs {
+
+__global__ void k_fill_u32(unsigned* __restrict__ p, size_t n, unsigned v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Offset (o + h i) - p of a vertex coordinate from a point coordinate, carried in
+// float pairs: the product h_hi * i and the sum with o_hi are split into value and
+// exact rounding error (fma product error, two-sum), so the offset keeps ~1e-7 m
+// accuracy even 100 m from the origin where a plain float sum loses ~1e-5 m.
+__device__ __forceinline__ float vertex_offset(float o_hi, float o_lo, float h_hi, float h_lo, int i, float p) {
+    // explicit round-to-nearest operations: no contraction may merge these steps
+    const float fi = (float)i;
+    const float prod = __fmul_rn(h_hi, fi);
+    const float perr = fmaf(h_hi, fi, -prod);
+    const float s = __fadd_rn(o_hi, prod);
+    const float bb = __fsub_rn(s, o_hi);
+    const float serr = __fadd_rn(__fsub_rn(o_hi, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
+    const float lo = serr + perr + o_lo + h_lo * fi;
+    return __fsub_rn(s, p) + lo;
+}
+
+// One CTA per point; its threads walk the box of vertices within r_t.
+__global__ void k_splat(SplatArgs a) {
+    const int j = blockIdx.x;
+    if (j >= a.n) return;
+    const float p3[3] = {a.pts[3 * j], a.pts[3 * j + 1], a.pts[3 * j + 2]};
+    // vertex index range covering [p - r_t, p + r_t], widened by one vertex so that
+    // float rounding of the bounds cannot drop a vertex; the value pass applies the
+    // exact d^2 <= r_t^2 test
+    const float inv_h = 1.0f / a.h_hi;
+    int lo[3], hi[3];
+    const int n3[3] = {a.nx, a.ny, a.nz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        lo[ax] = max(0, (int)floorf((p3[ax] - a.r_t - a.o_hi[ax]) * inv_h) - 1);
+        hi[ax] = min(n3[ax] - 1, (int)ceilf((p3[ax] + a.r_t - a.o_hi[ax]) * inv_h) + 1);
+    }
+    if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]) return;
+    const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
+    const int total = sx * sy * sz;
+    const float r2 = a.r_t * a.r_t;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int ix = lo[0] + t % sx;
+        const int iy = lo[1] + (t / sx) % sy;
+        const int iz = lo[2] + t / (sx * sy);
+        const float dx = vertex_offset(a.o_hi[0], a.o_lo[0], a.h_hi, a.h_lo, ix, p3[0]);
+        const float dy = vertex_offset(a.o_hi[1], a.o_lo[1], a.h_hi, a.h_lo, iy, p3[1]);
+        const float dz = vertex_offset(a.o_hi[2], a.o_lo[2], a.h_hi, a.h_lo, iz, p3[2]);
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 <= r2 * 1.0001f) {
+            const size_t v = ((size_t)iz * a.ny + iy) * a.nx + ix;
+            atomicMin(&a.d2[v], __float_as_uint(d2));
+        }
+    }
+}
+
+__device__ __forceinline__ float field_value(unsigned bits, float inv_two_sigma2, float r_t2) {
+    const float d2 = __uint_as_float(bits);
+    return (d2 <= r_t2) ? expf(-d2 * inv_two_sigma2) : 0.0f;
+}
+
+// One thread per cell: 8 corner values -> one packed record.
+__global__ void k_pack(PackArgs a) {
+    const int ncx = a.nx - 1, ncy = a.ny - 1, ncz = a.nz - 1;
+    const size_t ncell = (size_t)ncx * ncy * ncz;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < ncell; c += (size_t)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % ncx);
+        const int cy = (int)((c / ncx) % ncy);
+        const int cz = (int)(c / ((size_t)ncx * ncy));
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+            const size_t vi = ((size_t)(cz + dz) * a.ny + (cy + dy)) * a.nx + (cx + dx);
+            v[k] = field_value(a.d2[vi], a.inv_two_sigma2, a.r_t2);
+        }
+        if (a.dtype == 0) {
+            float4* out = reinterpret_cast<float4*>(a.cells) + 2 * c;
+            out[0] = make_float4(v[0], v[1], v[2], v[3]);
+            out[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                uint32_t lo16, hi16;
+                if (a.dtype == 1) {
+                    lo16 = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * e]));
+                    hi16 = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * e + 1]));
+                } else {
+                    lo16 = __half_as_ushort(__float2half_rn(v[2 * e]));
+                    hi16 = __half_as_ushort(__float2half_rn(v[2 * e + 1]));
+                }
+                w[e] = lo16 | (hi16 << 16);
+            }
+            reinterpret_cast<uint4*>(a.cells)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Vertex values read back from the cell records (vertex i lives in cell min(i, nc-1)).
+__global__ void k_unpack(const void* __restrict__ cells, int dtype, int nx, int ny, int nz, float* __restrict__ out) {
+    const size_t nv = (size_t)nx * ny * nz;
+    const int ncx = nx - 1, ncy = ny - 1, ncz = nz - 1;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((size_t)nx * ny));
+        const int cx = min(ix, ncx - 1), cy = min(iy, ncy - 1), cz = min(iz, ncz - 1);
+        const int corner = (ix - cx) + 2 * (iy - cy) + 4 * (iz - cz);
+        const size_t c = ((size_t)cz * ncy + cy) * ncx + cx;
+        float val;
+        if (dtype == 0) {
+            val = reinterpret_cast<const float*>(cells)[8 * c + corner];
+        } else {
+            const unsigned short b = reinterpret_cast<const unsigned short*>(cells)[8 * c + corner];
+            val = (dtype == 1) ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));
+        }
+        out[v] = val;
+    }
+}
+
+static int grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    if (b > 148 * 32) b = 148 * 32;
+    return (int)(b > 0 ? b : 1);
+}
+
+void launch_fill_u32(unsigned* p, size_t n, unsigned v, cudaStream_t s) {
+    k_fill_u32<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
+}
+
+void launch_splat(const SplatArgs& a, cudaStream_t s) {
+    if (a.n > 0) k_splat<<<a.n, 128, 0, s>>>(a);
+}
+
+void launch_pack(const PackArgs& a, cudaStream_t s) {
+    const size_t ncell = (size_t)(a.nx - 1) * (a.ny - 1) * (a.nz - 1);
+    k_pack<<<grid_for(ncell, 256), 256, 0, s>>>(a);
+}
+
+void launch_unpack(const void* cells, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s) {
+    k_unpack<<<grid_for((size_t)nx * ny * nz, 256), 256, 0, s>>>(cells, dtype, nx, ny, nz, out);
+}
+
+}  // namespace gmcs

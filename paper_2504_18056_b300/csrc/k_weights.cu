@@ -1,0 +1,300 @@
+// k_weights.cu -- importance weighting (Eq. 11) and systematic resampling.
+//
+// Weights live as FP64 log-weights. One launch adds the frame's log-likelihood,
+// finds M = max logw (argmax, lowest index on ties), S = sum exp(logw - M) and
+// S2 = sum exp(2 (logw - M)) with an online (max, sum) reduction: per thread,
+// per warp by shuffles, per CTA through shared memory, and across CTAs by the
+// last CTA to finish (a ticket counter), always in the same order. The
+// normalised weight is w_i = exp(logw_i - M - log S), ESS = S^2 / S2.
+//
+// Resampling quantises w_i to q_i = rint(w_i 2^52) so that every prefix sum
+// is an exact integer below 2^53 (exactly representable as a double), takes
+// C_i by a block scan plus a scan of block totals, and finds for each output
+// slot m the ancestor a_m = min{i : C_i > tau_m}, tau_m = ((u + m) / P) S in
+// IEEE double with explicit round-to-nearest operations, by binary search.
+// The result is independent of the scan order and bit-identical to a serial
+// evaluation of the same definition.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace gmcs {
+
+namespace {
+
+struct Lse {
+    double m, s, s2;
+    int im;
+};
+
+__device__ __forceinline__ Lse lse_combine(Lse a, Lse b) {
+    const bool b_first = (b.m > a.m) || (b.m == a.m && b.im < a.im);
+    Lse hi = b_first ? b : a;
+    const Lse lo = b_first ? a : b;
+    if (lo.m == -INFINITY) return hi;
+    const double e = exp(lo.m - hi.m);
+    hi.s += lo.s * e;
+    hi.s2 += lo.s2 * e * e;
+    return hi;
+}
+
+__device__ __forceinline__ Lse lse_shfl(Lse v, int off) {
+    Lse o;
+    o.m = __shfl_down_sync(0xffffffffu, v.m, off);
+    o.s = __shfl_down_sync(0xffffffffu, v.s, off);
+    o.s2 = __shfl_down_sync(0xffffffffu, v.s2, off);
+    o.im = __shfl_down_sync(0xffffffffu, v.im, off);
+    return o;
+}
+
+// Reduce over the CTA; the result is valid in thread 0.
+__device__ Lse lse_block(Lse v) {
+    __shared__ Lse sh[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = lse_combine(v, lse_shfl(v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (warp == 0) {
+        v = (lane < nw) ? sh[lane] : Lse{-INFINITY, 0.0, 0.0, 0x7fffffff};
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = lse_combine(v, lse_shfl(v, off));
+    }
+    __syncthreads();
+    return v;
+}
+
+constexpr int kWeighThreads = 256;
+
+}  // namespace
+
+__global__ void __launch_bounds__(kWeighThreads) k_weigh(WeighArgs a) {
+    Lse acc{-INFINITY, 0.0, 0.0, 0x7fffffff};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.P; i += gridDim.x * blockDim.x) {
+        double v = a.logw[i];
+        if (a.ll) {
+            v += (double)a.ll[i];
+            a.logw[i] = v;
+        }
+        if (isnan(v)) v = -INFINITY;
+        const Lse one{v, v == -INFINITY ? 0.0 : 1.0, v == -INFINITY ? 0.0 : 1.0, i};
+        acc = lse_combine(acc, one);
+    }
+    acc = lse_block(acc);
+    __shared__ int is_last;
+    if (threadIdx.x == 0) {
+        double* p = a.part + 4 * (size_t)blockIdx.x;
+        p[0] = acc.m; p[1] = acc.s; p[2] = acc.s2; p[3] = (double)acc.im;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    Lse tot{-INFINITY, 0.0, 0.0, 0x7fffffff};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double* p = a.part + 4 * (size_t)b;
+        const Lse one{__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), (int)__ldcg(p + 3)};
+        tot = lse_combine(tot, one);
+    }
+    tot = lse_block(tot);
+    if (threadIdx.x == 0) {
+        WeighResult r;
+        r.M = tot.m;
+        r.nonfinite = (tot.m == -INFINITY || !(tot.s > 0.0)) ? 1 : 0;
+        r.logS = r.nonfinite ? 0.0 : log(tot.s);
+        r.ess = r.nonfinite ? 0.0 : (tot.s * tot.s) / tot.s2;
+        r.max_w = r.nonfinite ? 0.0 : 1.0 / tot.s;
+        r.argmax = r.nonfinite ? 0 : tot.im;
+        r.pad = 0;
+        int doit = (a.policy == 0) || (a.policy == 1 && r.ess < 0.5 * (double)a.P);
+        r.do_resample = r.nonfinite ? 0 : doit;
+        for (int c = 0; c < 12; ++c) r.est[c] = a.pose[(size_t)c * a.ld + r.argmax];
+        *a.res = r;
+        *a.counter = 0u;
+    }
+}
+
+// q_i = rint(w_i 2^52) and the block-local inclusive prefix sums.
+__global__ void __launch_bounds__(kScanBlock) k_resample_scan(ScanArgs a) {
+    __shared__ unsigned long long wsum[32];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    double w = 0.0;
+    if (i < a.P) {
+        if (a.w) {
+            w = a.w[i];
+        } else {
+            const WeighResult r = *a.res;
+            w = r.nonfinite ? 1.0 / (double)a.P : exp(a.logw[i] - r.M - r.logS);
+        }
+        if (a.w_out) a.w_out[i] = w;
+    }
+    unsigned long long q = (w > 0.0 && w <= 1.0) ? __double2ull_rn(w * 4503599627370496.0) : 0ull;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, q, off);
+        if (lane >= off) q += t;
+    }
+    if (lane == 31) wsum[warp] = q;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long t = wsum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += u;
+        }
+        wsum[lane] = t;   // inclusive over warps
+    }
+    __syncthreads();
+    if (warp > 0) q += wsum[warp - 1];
+    if (i < a.P) a.cl[i] = q;
+    if (threadIdx.x == kScanBlock - 1) a.btot[blockIdx.x] = q;
+}
+
+// Exclusive scan of the block totals in place; the grand total goes to btot[nblocks].
+__global__ void __launch_bounds__(1024) k_scan_totals(unsigned long long* btot, int nblocks) {
+    __shared__ unsigned long long wsum[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < nblocks; base += 1024) {
+        const int b = base + threadIdx.x;
+        const unsigned long long x = (b < nblocks) ? btot[b] : 0ull;
+        unsigned long long q = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, q, off);
+            if (lane >= off) q += t;
+        }
+        if (lane == 31) wsum[warp] = q;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long t = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long u = __shfl_up_sync(0xffffffffu, t, off);
+                if (lane >= off) t += u;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        if (warp > 0) q += wsum[warp - 1];
+        const unsigned long long c0 = carry;
+        if (b < nblocks) btot[b] = c0 + q - x;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c0 + q;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) btot[nblocks] = carry;
+}
+
+__device__ __forceinline__ double systematic_u(uint64_t seed, uint32_t t) {
+    const uint4 o = philox4x32_10(make_uint4(0xFFFFFFFFu, t, 0u, kTagResample),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double hi = (double)(o.x >> 5), lo = (double)(o.y >> 6);
+    return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 1.0 / 9007199254740992.0);
+}
+
+__global__ void __launch_bounds__(256) k_resample_search(SearchArgs a) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.P) return;
+    if (a.res && !a.res->do_resample) {
+        a.anc[m] = m;
+        return;
+    }
+    const double u = a.u_from_philox ? systematic_u(a.seed, a.frame) : a.u;
+    const double S = (double)a.boff[a.nblocks];
+    const double tau = __dmul_rn(__ddiv_rn(__dadd_rn(u, (double)m), (double)a.P), S);
+    // block: smallest b whose inclusive prefix boff[b+1] exceeds tau
+    int lo = 0, hi = a.nblocks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((double)a.boff[mid + 1] > tau) hi = mid; else lo = mid + 1;
+    }
+    const unsigned long long base = a.boff[lo];
+    int l = lo * kScanBlock, h = min(a.P, (lo + 1) * kScanBlock) - 1;
+    while (l < h) {
+        const int mid = (l + h) >> 1;
+        if ((double)(base + a.cl[mid]) > tau) h = mid; else l = mid + 1;
+    }
+    a.anc[m] = ((double)(base + a.cl[l]) > tau) ? l : a.P - 1;
+}
+
+// State gather by ancestor: current pose and every keyframe pose, then log-weights.
+__global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
+    const size_t per = (size_t)(1 + a.K) * kPoseC;
+    const size_t n = per * a.P;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = e / a.P;
+        const int m = (int)(e % a.P);
+        const int src = a.anc[m];
+        if (row < kPoseC) {
+            a.pose_dst[row * a.ld + m] = a.pose_src[row * a.ld + src];
+        } else {
+            const size_t r2 = row - kPoseC;
+            a.kf_dst[r2 * a.ld + m] = a.kf_src[r2 * a.ld + src];
+        }
+    }
+    const double uni = -log((double)a.P);
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < a.P; m += gridDim.x * blockDim.x) {
+        if (!a.res) {
+            a.logw[m] = uni;
+        } else {
+            const WeighResult& r = *a.res;
+            a.logw[m] = (r.nonfinite || r.do_resample) ? uni : a.logw[m] - r.M - r.logS;
+        }
+    }
+}
+
+// No resampling: normalise the log-weights in place (w_out: weights, anc: identity).
+__global__ void __launch_bounds__(256) k_normalize(double* logw, int P, const WeighResult* res, double* w_out,
+                                                   int* anc) {
+    const double uni = -log((double)P);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        const double v = res->nonfinite ? uni : logw[i] - res->M - res->logS;
+        logw[i] = v;
+        if (w_out) w_out[i] = exp(v);
+        if (anc) anc[i] = i;
+    }
+}
+
+int weigh_blocks(int P) {
+    int b = (P + kWeighThreads * 4 - 1) / (kWeighThreads * 4);
+    if (b > 148 * 4) b = 148 * 4;
+    return b > 0 ? b : 1;
+}
+
+void launch_weigh(const WeighArgs& a, int nblocks, cudaStream_t s) {
+    k_weigh<<<nblocks, kWeighThreads, 0, s>>>(a);
+}
+
+void launch_resample_scan(const ScanArgs& a, cudaStream_t s) {
+    const int nb = (a.P + kScanBlock - 1) / kScanBlock;
+    if (nb > 0) k_resample_scan<<<nb, kScanBlock, 0, s>>>(a);
+}
+
+void launch_scan_totals(unsigned long long* btot, int nblocks, cudaStream_t s) {
+    k_scan_totals<<<1, 1024, 0, s>>>(btot, nblocks);
+}
+
+void launch_resample_search(const SearchArgs& a, cudaStream_t s) {
+    if (a.P > 0) k_resample_search<<<(a.P + 255) / 256, 256, 0, s>>>(a);
+}
+
+void launch_gather(const GatherArgs& a, cudaStream_t s) {
+    const size_t n = (size_t)(1 + a.K) * kPoseC * a.P;
+    size_t b = (n + 255) / 256;
+    if (b > 148 * 16) b = 148 * 16;
+    if (a.P > 0) k_gather<<<(int)b, 256, 0, s>>>(a);
+}
+
+void launch_normalize(double* logw, int P, const WeighResult* res, double* w_out, int* anc, cudaStream_t s) {
+    if (P > 0) k_normalize<<<(P + 255) / 256, 256, 0, s>>>(logw, P, res, w_out, anc);
+}
+
+}  // namespace gmcs

@@ -1,0 +1,165 @@
+// kernels.h -- argument records and host launchers of the device kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gmcs {
+
+constexpr int kPassWarps = 4;           // warps per CTA of the lookup pass (one particle tile)
+constexpr int kPassThreads = 32 * kPassWarps;
+constexpr int kAccGrad = 17;            // ll, d ll/d omega (3), d ll/d v (3), moments (10)
+constexpr int kMaxGroups = 8;           // point-chunk groups per particle tile (scratch bound)
+
+// ------------------------------------------------------------------ tables
+struct SplatArgs {
+    const float* pts;   // n x 3
+    int n;
+    float o_hi[3], o_lo[3];   // lattice origin as an unevaluated float pair (hi + lo)
+    float h_hi, h_lo;         // lattice step likewise
+    int nx, ny, nz;
+    float r_t;
+    unsigned* d2;       // [nz][ny][nx] squared distance as float bits
+};
+
+struct PackArgs {
+    const unsigned* d2;
+    int nx, ny, nz;
+    float inv_two_sigma2;   // 1 / (2 sigma^2)
+    float r_t2;
+    void* cells;
+    int dtype;
+};
+
+void launch_fill_u32(unsigned* p, size_t n, unsigned v, cudaStream_t s);
+void launch_splat(const SplatArgs& a, cudaStream_t s);
+void launch_pack(const PackArgs& a, cudaStream_t s);
+void launch_unpack(const void* cells, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s);
+
+// ------------------------------------------------------------------ filter
+struct PredictArgs {
+    float* pose;            // [12][ld], in/out
+    size_t ld;
+    int P;
+    float dT[12];
+    float cov[36];
+    const float* z;         // P x 6 or null
+    uint64_t seed;
+    uint32_t frame;
+};
+
+struct SelectArgs {
+    const float* pose;
+    const float* kf;        // [K][12][ld]
+    size_t ld;
+    int P, K, k_nb;
+    int* nbr;               // [k_nb][ld]
+    int* nbr_out;           // P x k_nb (row-major) or null
+};
+
+struct PassArgs {
+    const float* pose;
+    const float* kf;
+    const int* nbr;
+    const TableDesc* tables;
+    const float4* scan;
+    float* part;            // [groups][nacc][ld]
+    size_t ld;
+    int P, N, k_nb;
+    int ntiles, groups, chunk_len;
+    float eps;
+};
+
+struct FinishArgs {
+    const float* part;
+    float* pose;            // moved in place when do_move
+    size_t ld;
+    int P, groups;
+    int do_move;
+    float sigma, lambda, theta_max, t_max, w_min;
+    float* out_ll;          // P
+    float* out_g;           // P x 6
+    float* out_mom;         // P x 10
+    double* logw;           // value pass: logw += ll when non-null
+};
+
+void launch_scan_pack(const float* xyz, int n, float4* out, cudaStream_t s);
+void launch_aos_to_soa(const float* aos, int P, int C, float* soa, size_t ld, cudaStream_t s);
+void launch_soa_to_aos(const float* soa, size_t ld, int P, int C, float* aos, cudaStream_t s);
+void launch_predict(const PredictArgs& a, cudaStream_t s);
+void launch_select(const SelectArgs& a, cudaStream_t s);
+void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s);
+void launch_finish(const FinishArgs& a, bool grad, cudaStream_t s);
+
+// ------------------------------------------------------------------ weights / resampling
+struct WeighResult {
+    double M;           // max log-weight
+    double logS;        // log sum exp(logw - M)
+    double ess;         // S^2 / S2
+    double max_w;
+    int argmax;
+    int nonfinite;      // 1 if every log-weight was -inf or NaN
+    int do_resample;    // policy decision
+    int pad;
+    float est[12];      // pose of argmax (before resampling)
+};
+
+struct WeighArgs {
+    double* logw;       // in/out
+    const float* ll;    // added to logw first when non-null
+    int P;
+    int policy;         // 0 always, 1 ESS < P/2, 2 never
+    double* part;       // 4 doubles + 1 index per block
+    unsigned* counter;  // zero between launches
+    WeighResult* res;
+    const float* pose;  // current poses (for the estimate)
+    size_t ld;
+};
+
+struct ScanArgs {
+    const double* logw;     // weights from log-weights (when w is null)
+    const double* w;        // given normalised weights, or null
+    const WeighResult* res; // M, logS (when w is null)
+    double* w_out;          // optional normalised weights
+    int P;
+    unsigned long long* cl;     // block-local inclusive prefix of q
+    unsigned long long* btot;   // per-block totals -> exclusive offsets
+};
+
+struct SearchArgs {
+    const unsigned long long* cl;
+    const unsigned long long* boff;   // exclusive block offsets, then total at [nblocks]
+    int nblocks;
+    int P;
+    double u;               // systematic offset when u_from_philox == 0
+    int u_from_philox;      // 1: u = 53-bit Philox draw for (seed, frame)
+    uint64_t seed;
+    uint32_t frame;
+    const WeighResult* res; // do_resample flag (identity when 0); may be null
+    int* anc;
+};
+
+struct GatherArgs {
+    const float* pose_src;
+    float* pose_dst;
+    const float* kf_src;
+    float* kf_dst;
+    size_t ld;
+    int P, K;
+    const int* anc;
+    double* logw;
+    const WeighResult* res;   // null: resampled unconditionally
+};
+
+constexpr int kScanBlock = 1024;
+
+void launch_weigh(const WeighArgs& a, int nblocks, cudaStream_t s);
+int weigh_blocks(int P);
+void launch_resample_scan(const ScanArgs& a, cudaStream_t s);
+void launch_scan_totals(unsigned long long* btot, int nblocks, cudaStream_t s);
+void launch_resample_search(const SearchArgs& a, cudaStream_t s);
+void launch_gather(const GatherArgs& a, cudaStream_t s);
+void launch_normalize(double* logw, int P, const WeighResult* res, double* w_out, int* anc, cudaStream_t s);
+
+}  // namespace gmcs
