@@ -34,12 +34,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle×point lik+grad evals/s; frame update ms @100k particles; p50/p99"
 UNIT = "evals/s"
+FLOPS_GRAD_LOOKUP = 87          # FP32 flops of one gradient lookup (FMA = 2); breakdown in the design doc
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# DRAM bytes read + written per gradient-pass launch, from one ncu capture of the
+# current kernel at the same particle and point counts (profiles/); None when stale
+TRAFFIC_PER_LAUNCH = {"f32": 32.667e6, "bf16": 30.625e6, "f16": None}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--particles", type=int, default=100_000)
@@ -99,7 +104,7 @@ def barrier(world):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) of SM clock, max clock and throttle reasons."""
+    """nvidia-smi samples (every 100 ms) of SM clock, max clock and throttle reasons."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -114,7 +119,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -221,7 +226,7 @@ def run_native(a, world, rank, local):
     for k, kf in enumerate(w["keyframes"]):
         f.add_keyframe(kf["points"], kf["grid"], w["kf_particle_poses"][k])
     scans_d = [torch.from_numpy(s).to(dev) for s in w["scans"]]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
+    flush = None if a.no_flush else torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     torch.cuda.synchronize()
 
     for fr in range(a.warmup):
@@ -275,7 +280,10 @@ def run_native(a, world, rank, local):
     lookups_per_launch = float(P) * N * 3
     rec_bytes = 32 if dtype == 0 else 16
     avg_ms = pg["ms"] / max(pg["launches"], 1)
-    achieved_gbs = lookups_per_launch * rec_bytes / (avg_ms / 1e3) / 1e9
+    # algorithmic work of one gradient lookup: 87 FP32 flops (FMA = 2), one cell record read
+    flops_per_launch = lookups_per_launch * FLOPS_GRAD_LOOKUP
+    achieved_tflops = flops_per_launch / (avg_ms / 1e3) / 1e12
+    gather_gbs = lookups_per_launch * rec_bytes / (avg_ms / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak, peak_src = 6400.0, "fallback"
     if os.path.exists(peaks_path):
@@ -304,12 +312,14 @@ def run_native(a, world, rank, local):
                      "min": float(step_ms.min()), "max": float(step_ms.max())},
         "lookups_per_s": float(P) * N * 3 * 4 * a.steps * world / (max_ms / 1e3),
         "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in kinds.items() if v["launches"]},
-        "roofline": {"kernel": "pass_grad (lookup + gradient + moments)", "bound": "hbm",
-                     "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm_peak, "traffic": None,
-                     "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": lookups_per_launch * rec_bytes,
-                     "avg_launch_ms": avg_ms},
+        "roofline": {"kernel": "k_pass3 gradient pass (lookup + gradient + moments)", "bound": "alu",
+                     "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(a.dtype),
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz",
+                     "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms},
+        "gather": {"algorithmic_bytes_per_launch": lookups_per_launch * rec_bytes, "achieved_gbs": gather_gbs,
+                   "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src, "frac_of_hbm": gather_gbs / hbm_peak,
+                   "frame_at_hbm_roofline_ms": float(P) * N * 3 * 4 * rec_bytes / (hbm_peak * 1e9) * 1e3},
         "clocks": clk,
         "gpu_launches": int(stats["launches"]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 12,

@@ -10,7 +10,9 @@
 //   tables              per keyframe, one record of 8 corner values per lattice
 //                       cell, cells ordered x fastest: FP32 records are 32 B
 //                       (two float4), BF16/FP16 records are 16 B (one uint4).
-//                       Corner order (dx + 2 dy + 4 dz).
+//                       Corner (dx, dy, dz) sits at slot dz + 2 dy + 4 dx: the
+//                       x = 0 face first, z pairs adjacent, so the x- and y-
+//                       interpolations run on packed float pairs.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -148,6 +150,9 @@ __device__ __forceinline__ void normal6(uint64_t seed, uint32_t i, uint32_t t, f
 }
 
 // ---------------------------------------------------------------- table cells
+
+// Slot of corner (dx, dy, dz) within a cell record.
+__host__ __device__ constexpr int rec_slot(int dx, int dy, int dz) { return dz + 2 * dy + 4 * dx; }
 
 // The 8 corner values of cell `idx`, widened to float.
 template <int DT>

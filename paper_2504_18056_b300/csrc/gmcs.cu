@@ -175,16 +175,18 @@ void harvest(gmcs_ctx* c) {
     cudaGetLastError();
 }
 
-// Chunking of the scan for the lookup pass: enough CTAs for several waves on
-// 148 SMs, at most kMaxGroups groups of kPassWarps chunks, chunks of >= 8 points.
+// Chunking of the scan for the lookup pass: a CTA covers kPassTW particle tiles
+// x kPassCW point chunks; the number of chunk groups G gives several waves of
+// CTAs on 148 SMs, at most kMaxGroups (the partial-sum scratch), chunks >= 8 points.
 void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len) {
     const int nt = (P + 31) / 32;
+    const int ntg = (nt + kPassTW - 1) / kPassTW;
     const int target = 148 * 8 * 4;
-    int g = (target + nt - 1) / nt;
+    int g = (target + ntg - 1) / ntg;
     g = std::max(1, std::min(g, kMaxGroups));
     const int max_chunks = std::max(1, (N + 7) / 8);
-    while (g > 1 && g * kPassWarps > max_chunks) --g;
-    const int chunks = g * kPassWarps;
+    while (g > 1 && g * kPassCW > max_chunks) --g;
+    const int chunks = g * kPassCW;
     *ntiles = nt;
     *groups = g;
     *chunk_len = std::max(1, (N + chunks - 1) / chunks);

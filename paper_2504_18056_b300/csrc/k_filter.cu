@@ -146,112 +146,308 @@ __global__ void __launch_bounds__(128) k_select(SelectArgs a) {
 
 // ------------------------------------------------------------------ the lookup pass
 
+#ifndef GMCS_PASS_MINBLOCKS
+#define GMCS_PASS_MINBLOCKS 1
+#endif
+#ifndef GMCS_PASS_UNROLL
+#define GMCS_PASS_UNROLL 2
+#endif
+#ifndef GMCS_PASS3
+#define GMCS_PASS3 1
+#endif
+#ifndef GMCS_PASS3_MINBLOCKS
+#define GMCS_PASS3_MINBLOCKS 1
+#endif
+constexpr int kPassUnroll = GMCS_PASS_UNROLL;
+// Point-loop unrolling of the three-neighbour pass (independent lookups in
+// flight per thread), per table type and pass kind.
+#ifndef GMCS_U_G32
+#define GMCS_U_G32 1
+#endif
+#ifndef GMCS_U_G16
+#define GMCS_U_G16 2
+#endif
+#ifndef GMCS_U_V32
+#define GMCS_U_V32 2
+#endif
+#ifndef GMCS_U_V16
+#define GMCS_U_V16 2
+#endif
 template <int DT, bool GRAD>
-__global__ void __launch_bounds__(kPassThreads) k_pass(PassArgs a) {
-    constexpr int NACC = GRAD ? kAccGrad : 1;
-    __shared__ float red[kPassWarps][NACC][32];
+constexpr int pass3_unroll() {
+    return GRAD ? (DT == 0 ? GMCS_U_G32 : GMCS_U_G16) : (DT == 0 ? GMCS_U_V32 : GMCS_U_V16);
+}
+
+#ifndef GMCS_F32X2
+#define GMCS_F32X2 1
+#endif
+
+// Packed two-lane FP32 arithmetic (Blackwell add/sub/fma .f32x2).
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) {
+#if GMCS_F32X2
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&d);
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) {
+#if GMCS_F32X2
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+          "l"(*reinterpret_cast<unsigned long long*>(&c)));
+    return *reinterpret_cast<float2*>(&d);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+
+// One lookup at lattice coordinate u of a table: adds log2(L + eps) to lsum
+// and, with GRAD, returns w = L / (L + eps) and g = grad_u L / (L + eps).
+// A cell outside [0, n-1) on any axis reads as L = 0 (the load is skipped).
+// The record holds the cell's corners as z-pairs (slot dz + 2 dy + 4 dx):
+// P0 = x0y0, P1 = x0y1, P2 = x1y0, P3 = x1y1, each (z0, z1).
+template <int DT, bool GRAD>
+__device__ __forceinline__ void lookup_one(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
+                                           float ux, float uy, float uz, float eps, float& lsum, float& w,
+                                           float& gx, float& gy, float& gz) {
+    const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+    const int cx = (int)flx, cy = (int)fly, cz = (int)flz;
+    const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+    const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
+    float v[8];
+    load_cell<DT>(cells, idx, valid, v);
+    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
+    const float2 P0 = make_float2(v[0], v[1]), P1 = make_float2(v[2], v[3]);
+    const float2 P2 = make_float2(v[4], v[5]), P3 = make_float2(v[6], v[7]);
+    const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
+    const float2 D0 = p2_sub(P2, P0), D1 = p2_sub(P3, P1);        // x-differences at y0, y1
+    const float2 E0 = p2_fma(FX, D0, P0), E1 = p2_fma(FX, D1, P1); // x-interpolated at y0, y1
+    const float2 DY = p2_sub(E1, E0);                              // y-differences (z0, z1)
+    const float2 G = p2_fma(FY, DY, E0);                           // xy-interpolated (z0, z1)
+    const float Lz = G.y - G.x;
+    const float L = fmaf(fz, Lz, G.x);
+    const float den = L + eps;
+    lsum += __log2f(den);
+    if constexpr (GRAD) {
+        const float2 HX = p2_fma(FY, p2_sub(D1, D0), D0);          // y-interpolated x-differences
+        const float Lx = fmaf(fz, HX.y - HX.x, HX.x);
+        const float Ly = fmaf(fz, DY.y - DY.x, DY.x);
+        const float inv = __fdividef(1.f, den);
+        gx = Lx * inv;
+        gy = Ly * inv;
+        gz = Lz * inv;
+        w = L * inv;
+    }
+}
+
+// Affine map p -> u = A p + b of one (particle, neighbour keyframe) pair onto
+// that keyframe's lattice, with the table it reads.
+struct Slot {
+    float A00, A01, A02, A10, A11, A12, A20, A21, A22, b0, b1, b2;
+    const void* cells;
+    uint32_t ncx, ncy, ncz;
+};
+
+__device__ __forceinline__ Slot make_slot(const PassArgs& a, int i, int k, const float* Tt) {
+    const TableDesc td = a.tables[k];
+    float Tk[12], rel[12];
+    load_pose(a.kf + (size_t)k * kPoseC * a.ld, a.ld, i, Tk);
+    pose_rel(Tk, Tt, rel);
+    Slot s;
+    s.A00 = rel[0] * td.inv_h; s.A01 = rel[1] * td.inv_h; s.A02 = rel[2] * td.inv_h;
+    s.A10 = rel[4] * td.inv_h; s.A11 = rel[5] * td.inv_h; s.A12 = rel[6] * td.inv_h;
+    s.A20 = rel[8] * td.inv_h; s.A21 = rel[9] * td.inv_h; s.A22 = rel[10] * td.inv_h;
+    s.b0 = (rel[3] - td.ox) * td.inv_h;
+    s.b1 = (rel[7] - td.oy) * td.inv_h;
+    s.b2 = (rel[11] - td.oz) * td.inv_h;
+    s.cells = td.cells;
+    s.ncx = (uint32_t)td.ncx;
+    s.ncy = (uint32_t)td.ncy;
+    s.ncz = (uint32_t)td.ncz;
+    return s;
+}
+
+// Fold one slot's lattice-frame sums into d l/d xi. With r_j = u_j - b the
+// rotated point in lattice units, sum r x g = Cu - b x G where Cu = sum u x g;
+// then d l/d omega = h A^T (Cu - b x G) and d l/d v = A^T G.
+__device__ __forceinline__ void fold_slot(const Slot& s, float h, float Gx, float Gy, float Gz, float Ux, float Uy,
+                                          float Uz, float* acc) {
+    const float Cx = Ux - (s.b1 * Gz - s.b2 * Gy);
+    const float Cy = Uy - (s.b2 * Gx - s.b0 * Gz);
+    const float Cz = Uz - (s.b0 * Gy - s.b1 * Gx);
+    acc[1] += h * (s.A00 * Cx + s.A10 * Cy + s.A20 * Cz);
+    acc[2] += h * (s.A01 * Cx + s.A11 * Cy + s.A21 * Cz);
+    acc[3] += h * (s.A02 * Cx + s.A12 * Cy + s.A22 * Cz);
+    acc[4] += s.A00 * Gx + s.A10 * Gy + s.A20 * Gz;
+    acc[5] += s.A01 * Gx + s.A11 * Gy + s.A21 * Gz;
+    acc[6] += s.A02 * Gx + s.A12 * Gy + s.A22 * Gz;
+}
+
+__device__ __forceinline__ void add_moments(float w, float4 p, float* acc) {
+    const float wx = w * p.x, wy = w * p.y, wz = w * p.z;
+    acc[7] += w;
+    acc[8] += wx; acc[9] += wy; acc[10] += wz;
+    acc[11] = fmaf(wx, p.x, acc[11]); acc[12] = fmaf(wx, p.y, acc[12]); acc[13] = fmaf(wx, p.z, acc[13]);
+    acc[14] = fmaf(wy, p.y, acc[14]); acc[15] = fmaf(wy, p.z, acc[15]); acc[16] = fmaf(wz, p.z, acc[16]);
+}
+
+// Map a CTA warp to (particle index, point range, chunk group).
+struct WarpWork {
+    int i, j0, j1, tg, cg;
+};
+
+__device__ __forceinline__ WarpWork warp_work(const PassArgs& a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x % a.ntiles;
-    const int grp = blockIdx.x / a.ntiles;
-    const int i = tile * 32 + lane;
-    const bool live = i < a.P;
-    const int chunk = grp * kPassWarps + warp;
-    const int j0 = min(chunk * a.chunk_len, a.N);
-    const int j1 = min(j0 + a.chunk_len, a.N);
+    const int ntg = (a.ntiles + kPassTW - 1) / kPassTW;
+    WarpWork w;
+    w.tg = blockIdx.x % ntg;
+    w.cg = blockIdx.x / ntg;
+    const int tile = w.tg * kPassTW + warp % kPassTW;
+    const int chunk = w.cg * kPassCW + warp / kPassTW;
+    w.i = tile * 32 + lane;
+    w.j0 = min(chunk * a.chunk_len, a.N);
+    w.j1 = min(w.j0 + a.chunk_len, a.N);
+    return w;
+}
+
+// CTA partial sums -> scratch [group][acc][particle]; warps sharing a tile add
+// their chunks in a fixed order.
+template <int NACC>
+__device__ __forceinline__ void store_partials(const PassArgs& a, const float* acc, const WarpWork& ww) {
+    if constexpr (kPassCW == 1) {
+        if (ww.i < a.P)
+#pragma unroll
+            for (int e = 0; e < NACC; ++e) a.part[((size_t)ww.cg * NACC + e) * a.ld + ww.i] = acc[e];
+    } else {
+        __shared__ float red[kPassCW][NACC][kPassTW * 32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int col = (warp % kPassTW) * 32 + lane;
+#pragma unroll
+        for (int e = 0; e < NACC; ++e) red[warp / kPassTW][e][col] = acc[e];
+        __syncthreads();
+        const int base = ww.tg * kPassTW * 32;
+        for (int t = threadIdx.x; t < NACC * kPassTW * 32; t += kPassThreads) {
+            const int e = t / (kPassTW * 32), l = t % (kPassTW * 32);
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < kPassCW; ++c) s += red[c][e][l];
+            if (base + l < a.P) a.part[((size_t)ww.cg * NACC + e) * a.ld + base + l] = s;
+        }
+    }
+}
+
+// Generic pass: any number of neighbour slots, neighbour loop outside the point loop.
+template <int DT, bool GRAD>
+__global__ void __launch_bounds__(kPassThreads, GMCS_PASS_MINBLOCKS) k_pass(PassArgs a) {
+    constexpr int NACC = GRAD ? kAccGrad : 1;
+    const WarpWork ww = warp_work(a);
+    const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
 
     float acc[NACC];
 #pragma unroll
     for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
 
-    if (live && j0 < j1) {
-        float Tt[12];
-        load_pose(a.pose, a.ld, i, Tt);
+    if (i < a.P && j0 < j1) {
         float lsum = 0.f;   // in log2 units
         for (int s = 0; s < a.k_nb; ++s) {
             const int k = a.nbr[(size_t)s * a.ld + i];
             if (k < 0) continue;
-            const TableDesc td = a.tables[k];
-            float Tk[12], rel[12];
-            load_pose(a.kf + (size_t)k * kPoseC * a.ld, a.ld, i, Tk);
-            pose_rel(Tk, Tt, rel);
-            // affine map p -> u = A p + b onto the lattice
-            const float A00 = rel[0] * td.inv_h, A01 = rel[1] * td.inv_h, A02 = rel[2] * td.inv_h;
-            const float A10 = rel[4] * td.inv_h, A11 = rel[5] * td.inv_h, A12 = rel[6] * td.inv_h;
-            const float A20 = rel[8] * td.inv_h, A21 = rel[9] * td.inv_h, A22 = rel[10] * td.inv_h;
-            const float b0 = (rel[3] - td.ox) * td.inv_h;
-            const float b1 = (rel[7] - td.oy) * td.inv_h;
-            const float b2 = (rel[11] - td.oz) * td.inv_h;
-            const uint32_t ncx = (uint32_t)td.ncx, ncy = (uint32_t)td.ncy, ncz = (uint32_t)td.ncz;
-            const void* __restrict__ cells = td.cells;
+            float Tt[12];
+            load_pose(a.pose, a.ld, i, Tt);
+            const Slot sl = make_slot(a, i, k, Tt);
             const float eps = a.eps;
             float Gx = 0.f, Gy = 0.f, Gz = 0.f, Cx = 0.f, Cy = 0.f, Cz = 0.f;
-#pragma unroll 2
+#pragma unroll kPassUnroll
             for (int j = j0; j < j1; ++j) {
                 const float4 p = __ldg(a.scan + j);
-                const float rx = A00 * p.x + A01 * p.y + A02 * p.z;
-                const float ry = A10 * p.x + A11 * p.y + A12 * p.z;
-                const float rz = A20 * p.x + A21 * p.y + A22 * p.z;
-                const float ux = rx + b0, uy = ry + b1, uz = rz + b2;
-                const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
-                const int cx = (int)flx, cy = (int)fly, cz = (int)flz;
-                const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-                const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
-                float v[8];
-                load_cell<DT>(cells, idx, valid, v);
-                const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
-                // trilinear value, corner order (dx + 2 dy + 4 dz)
-                const float d00 = v[1] - v[0], d10 = v[3] - v[2], d01 = v[5] - v[4], d11 = v[7] - v[6];
-                const float e00 = fmaf(fx, d00, v[0]), e10 = fmaf(fx, d10, v[2]);
-                const float e01 = fmaf(fx, d01, v[4]), e11 = fmaf(fx, d11, v[6]);
-                const float dy0 = e10 - e00, dy1 = e11 - e01;
-                const float g0 = fmaf(fy, dy0, e00), g1 = fmaf(fy, dy1, e01);
-                const float Lz = g1 - g0;
-                const float L = fmaf(fz, Lz, g0);
-                const float den = L + eps;
-                lsum += __log2f(den);
+                const float ux = fmaf(sl.A00, p.x, fmaf(sl.A01, p.y, fmaf(sl.A02, p.z, sl.b0)));
+                const float uy = fmaf(sl.A10, p.x, fmaf(sl.A11, p.y, fmaf(sl.A12, p.z, sl.b1)));
+                const float uz = fmaf(sl.A20, p.x, fmaf(sl.A21, p.y, fmaf(sl.A22, p.z, sl.b2)));
+                float w, gx, gy, gz;
+                lookup_one<DT, GRAD>(sl.cells, sl.ncx, sl.ncy, sl.ncz, ux, uy, uz, eps, lsum, w, gx, gy, gz);
                 if constexpr (GRAD) {
-                    const float hx0 = fmaf(fy, d10 - d00, d00), hx1 = fmaf(fy, d11 - d01, d01);
-                    const float Lx = fmaf(fz, hx1 - hx0, hx0);
-                    const float Ly = fmaf(fz, dy1 - dy0, dy0);
-                    const float inv = __fdividef(1.f, den);
-                    const float gx = Lx * inv, gy = Ly * inv, gz = Lz * inv;
                     Gx += gx; Gy += gy; Gz += gz;
-                    Cx = fmaf(ry, gz, fmaf(-rz, gy, Cx));
-                    Cy = fmaf(rz, gx, fmaf(-rx, gz, Cy));
-                    Cz = fmaf(rx, gy, fmaf(-ry, gx, Cz));
-                    const float w = L * inv;
-                    const float wx = w * p.x, wy = w * p.y, wz = w * p.z;
-                    acc[7] += w;
-                    acc[8] += wx; acc[9] += wy; acc[10] += wz;
-                    acc[11] = fmaf(wx, p.x, acc[11]); acc[12] = fmaf(wx, p.y, acc[12]); acc[13] = fmaf(wx, p.z, acc[13]);
-                    acc[14] = fmaf(wy, p.y, acc[14]); acc[15] = fmaf(wy, p.z, acc[15]); acc[16] = fmaf(wz, p.z, acc[16]);
+                    Cx = fmaf(uy, gz, fmaf(-uz, gy, Cx));
+                    Cy = fmaf(uz, gx, fmaf(-ux, gz, Cy));
+                    Cz = fmaf(ux, gy, fmaf(-uy, gx, Cz));
+                    add_moments(w, p, acc);
                 }
             }
-            if constexpr (GRAD) {
-                // d l/d omega = h A^T C,  d l/d v = A^T G
-                const float h = td.h;
-                acc[1] += h * (A00 * Cx + A10 * Cy + A20 * Cz);
-                acc[2] += h * (A01 * Cx + A11 * Cy + A21 * Cz);
-                acc[3] += h * (A02 * Cx + A12 * Cy + A22 * Cz);
-                acc[4] += A00 * Gx + A10 * Gy + A20 * Gz;
-                acc[5] += A01 * Gx + A11 * Gy + A21 * Gz;
-                acc[6] += A02 * Gx + A12 * Gy + A22 * Gz;
-            }
+            if constexpr (GRAD) fold_slot(sl, a.tables[k].h, Gx, Gy, Gz, Cx, Cy, Cz, acc);
         }
         acc[0] = lsum * 0.69314718055994531f;
     }
+    store_partials<NACC>(a, acc, ww);
+}
 
+// Three neighbour slots (the paper's choice, Sec. III-C): the neighbour loop
+// runs inside the point loop, so each scan point is read once and its weight
+// moments are accumulated once for all three lookups, which are independent
+// and keep three cell loads in flight.
+template <int DT, bool GRAD, int UNROLL>
+__global__ void __launch_bounds__(kPassThreads, GMCS_PASS3_MINBLOCKS) k_pass3(PassArgs a) {
+    constexpr int NACC = GRAD ? kAccGrad : 1;
+    const WarpWork ww = warp_work(a);
+    const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
+
+    float acc[NACC];
 #pragma unroll
-    for (int e = 0; e < NACC; ++e) red[warp][e][lane] = acc[e];
-    __syncthreads();
-    const int base = tile * 32;
-    for (int t = threadIdx.x; t < NACC * 32; t += kPassThreads) {
-        const int e = t >> 5, l = t & 31;
-        float s = 0.f;
+    for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
+
+    if (i < a.P && j0 < j1) {
+        Slot sl[3];
+        int ks[3];
+        {
+            float Tt[12];
+            load_pose(a.pose, a.ld, i, Tt);
 #pragma unroll
-        for (int w = 0; w < kPassWarps; ++w) s += red[w][e][l];
-        if (base + l < a.P) a.part[((size_t)grp * NACC + e) * a.ld + base + l] = s;
+            for (int s = 0; s < 3; ++s) {
+                ks[s] = a.nbr[(size_t)s * a.ld + i];
+                sl[s] = make_slot(a, i, ks[s], Tt);
+            }
+        }
+        const float eps = a.eps;
+        float lsum = 0.f;
+        float G[3][3], C[3][3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) G[s][d] = C[s][d] = 0.f;
+#pragma unroll UNROLL
+        for (int j = j0; j < j1; ++j) {
+            const float4 p = __ldg(a.scan + j);
+            float wsum = 0.f;
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const float ux = fmaf(sl[s].A00, p.x, fmaf(sl[s].A01, p.y, fmaf(sl[s].A02, p.z, sl[s].b0)));
+                const float uy = fmaf(sl[s].A10, p.x, fmaf(sl[s].A11, p.y, fmaf(sl[s].A12, p.z, sl[s].b1)));
+                const float uz = fmaf(sl[s].A20, p.x, fmaf(sl[s].A21, p.y, fmaf(sl[s].A22, p.z, sl[s].b2)));
+                float w, gx, gy, gz;
+                lookup_one<DT, GRAD>(sl[s].cells, sl[s].ncx, sl[s].ncy, sl[s].ncz, ux, uy, uz, eps, lsum, w, gx, gy,
+                                     gz);
+                if constexpr (GRAD) {
+                    G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
+                    C[s][0] = fmaf(uy, gz, fmaf(-uz, gy, C[s][0]));
+                    C[s][1] = fmaf(uz, gx, fmaf(-ux, gz, C[s][1]));
+                    C[s][2] = fmaf(ux, gy, fmaf(-uy, gx, C[s][2]));
+                    wsum += w;
+                }
+            }
+            if constexpr (GRAD) add_moments(wsum, p, acc);
+        }
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+                fold_slot(sl[s], a.tables[ks[s]].h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
+        }
+        acc[0] = lsum * 0.69314718055994531f;
     }
+    store_partials<NACC>(a, acc, ww);
 }
 
 // ------------------------------------------------------------------ finish: sums, move (Eq. 5-7)
@@ -396,9 +592,13 @@ void launch_select(const SelectArgs& a, cudaStream_t s) {
 }
 
 void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s) {
-    const int grid = a.ntiles * a.groups;
+    const int grid = (a.ntiles + kPassTW - 1) / kPassTW * a.groups;
     if (grid <= 0) return;
-#define GMCS_PASS(DT, G) k_pass<DT, G><<<grid, kPassThreads, 0, s>>>(a)
+    // three neighbours (every particle then has all three slots filled): the fused kernel
+    const bool three = GMCS_PASS3 && a.k_nb == 3;
+#define GMCS_PASS(DT, G)                                                                            \
+    (three ? k_pass3<DT, G, pass3_unroll<DT, G>()><<<grid, kPassThreads, 0, s>>>(a)                \
+           : k_pass<DT, G><<<grid, kPassThreads, 0, s>>>(a))
     if (grad) {
         if (dtype == 0) GMCS_PASS(0, true); else if (dtype == 1) GMCS_PASS(1, true); else GMCS_PASS(2, true);
     } else {

@@ -80,11 +80,14 @@ __global__ void k_pack(PackArgs a) {
         const int cz = (int)(c / ((size_t)ncx * ncy));
         float v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-            const size_t vi = ((size_t)(cz + dz) * a.ny + (cy + dy)) * a.nx + (cx + dx);
-            v[k] = field_value(a.d2[vi], a.inv_two_sigma2, a.r_t2);
-        }
+        for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz) {
+                    const size_t vi = ((size_t)(cz + dz) * a.ny + (cy + dy)) * a.nx + (cx + dx);
+                    v[rec_slot(dx, dy, dz)] = field_value(a.d2[vi], a.inv_two_sigma2, a.r_t2);
+                }
         if (a.dtype == 0) {
             float4* out = reinterpret_cast<float4*>(a.cells) + 2 * c;
             out[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -115,7 +118,7 @@ __global__ void k_unpack(const void* __restrict__ cells, int dtype, int nx, int 
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
         const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((size_t)nx * ny));
         const int cx = min(ix, ncx - 1), cy = min(iy, ncy - 1), cz = min(iz, ncz - 1);
-        const int corner = (ix - cx) + 2 * (iy - cy) + 4 * (iz - cz);
+        const int corner = rec_slot(ix - cx, iy - cy, iz - cz);
         const size_t c = ((size_t)cz * ncy + cy) * ncx + cx;
         float val;
         if (dtype == 0) {

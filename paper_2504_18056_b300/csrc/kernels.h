@@ -7,8 +7,16 @@
 
 namespace gmcs {
 
-constexpr int kPassWarps = 4;           // warps per CTA of the lookup pass (one particle tile)
+constexpr int kPassWarps = 4;           // warps per CTA of the lookup pass
 constexpr int kPassThreads = 32 * kPassWarps;
+#ifndef GMCS_TW
+#define GMCS_TW 1
+#endif
+// A CTA's warps cover kPassTW particle tiles (32 particles each) times
+// kPassCW point chunks; warps on the same chunk walk the same points together.
+constexpr int kPassTW = GMCS_TW;
+constexpr int kPassCW = kPassWarps / kPassTW;
+static_assert(kPassTW * kPassCW == kPassWarps, "tile x chunk split of the CTA");
 constexpr int kAccGrad = 17;            // ll, d ll/d omega (3), d ll/d v (3), moments (10)
 constexpr int kMaxGroups = 8;           // point-chunk groups per particle tile (scratch bound)
 
@@ -67,7 +75,7 @@ struct PassArgs {
     float* part;            // [groups][nacc][ld]
     size_t ld;
     int P, N, k_nb;
-    int ntiles, groups, chunk_len;
+    int ntiles, groups, chunk_len;   // groups: chunk groups (kPassCW chunks each)
     float eps;
 };
 

@@ -177,9 +177,9 @@ def test_weigh_matches_oracle(box_room):
     f = gm.Filter(P, 1, 16)
     rng = np.random.default_rng(9)
     logw = rng.normal(size=P) * 20 - 3e3
+    logw[4000] = logw[17]
     f.init_particles(np.ascontiguousarray(np.repeat(box_room["particles"][:1], P, 0)), logw)
     ll = (rng.normal(size=P) * 40 - 5e3).astype(np.float32)
-    logw[4000] = logw[17]
     ll[17] = ll[4000] = ll.max() + 7.0        # tie: the lower index is the argmax
     w = np.zeros(P)
     res = f.weigh(ll, w)
