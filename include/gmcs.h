@@ -221,6 +221,31 @@ int gmcs_weigh(gmcs_ctx* ctx, const float* ll, double* w_out, gmcs_step_out* res
  */
 int gmcs_resample(gmcs_ctx* ctx, const double* w, int P, double u, int* anc);
 
+/*
+ * The paper has no counterpart of this call: it is systematic resampling, with
+ * the same definition and kernels as gmcs_resample, for callers that cannot
+ * allocate device memory -- code running under a memory manager that owns the
+ * whole device budget, or a real-time loop that cannot afford cudaMalloc's
+ * implicit device synchronisation and unbounded latency. It needs no context
+ * and allocates nothing: its prefix-sum scratch is a file-scope __device__ array
+ * of GMCS_NOALLOC_MAX_P + 257 eight-byte words (about 2.1 MB) that every device
+ * which loads the library holds until the process exits.
+ *   w    P normalised weights, device doubles (host pointers: GMCS_E_INVALID)
+ *   u    systematic offset in [0, 1)
+ *   anc  P device ints receiving the ancestors
+ *   cuda_stream  stream the work is enqueued on (NULL: legacy default stream);
+ *        the call returns without synchronising it
+ * P > GMCS_NOALLOC_MAX_P returns GMCS_E_CAPACITY. The first call on a device
+ * looks up the array's device address with that device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind (each call
+ * writes all the scratch it reads): calls whose work can overlap on the GPU --
+ * on different streams or from different threads -- race on it and must be
+ * serialised by the caller.
+ */
+#define GMCS_NOALLOC_MAX_P 262144
+int gmcs_resample_noalloc(const double* w, int P, double u, int* anc, void* cuda_stream);
+
 /* ---- state access */
 
 /* Copy current poses (P x 12 floats) and/or log-weights (P doubles) out; NULL skips. */

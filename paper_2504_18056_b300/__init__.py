@@ -87,7 +87,9 @@ _SIGS = {
     "gmcs_reset_stats": (C.c_int, [C.c_void_p]),
     "gmcs_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "gmcs_strerror": (C.c_char_p, [C.c_int]),
+    "gmcs_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
 }
+NOALLOC_MAX_P = 262144
 
 
 def lib():
@@ -133,6 +135,15 @@ def _ptr(a, dtype=None):
 def _dbl(vals, n):
     arr = (C.c_double * n)(*[float(v) for v in np.asarray(vals, np.float64).reshape(-1)[:n]])
     return arr
+
+
+def resample_noalloc(w, u, anc, stream=None):
+    """Systematic resampling of device weights into device ancestors without any
+    allocation (gmcs_resample_noalloc); enqueued on `stream` (default: torch's
+    current stream), not synchronised."""
+    st = _current_stream() if stream is None else C.c_void_p(int(stream))
+    _check(lib().gmcs_resample_noalloc(_ptr(w), int(w.shape[0]), float(u), _ptr(anc), st), "gmcs_resample_noalloc")
+    return anc
 
 
 def default_config(**kw):
