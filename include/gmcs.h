@@ -203,6 +203,23 @@ int gmcs_eval(gmcs_ctx* ctx, const float* scan, int N, float* ll, float* g, floa
 int gmcs_move(gmcs_ctx* ctx, const float* scan, int N);
 
 /*
+ * Differentiable scan log-likelihood at perturbed poses T_i = T0_i exp(xi_i), T0 the
+ * current particle poses and xi P x 6 floats (host or device), with the neighbour
+ * keyframes of the last gmcs_select / gmcs_step held fixed:
+ *   gmcs_loglik:          ll_i = sum_jk log(L + eps) at T_i            (P floats out)
+ *   gmcs_loglik_backward: grad_xi_i = grad_ll_i * d ll_i / d xi_i       (P x 6 floats out)
+ *                         = grad_ll_i * Jr(xi_i)^T g_i, g_i the right-perturbation
+ *                         gradient at T_i (the lookup pass with gradient) and Jr the
+ *                         right Jacobian of SE(3).
+ * The scan is re-read in both calls; particle state is not modified. The trilinear
+ * field is continuous but its gradient jumps across cell faces; the value is the
+ * derivative of the cell polynomials that contain the points at T_i.
+ */
+int gmcs_loglik(gmcs_ctx* ctx, const float* xi, const float* scan, int N, float* ll);
+int gmcs_loglik_backward(gmcs_ctx* ctx, const float* xi, const float* scan, int N, const float* grad_ll,
+                         float* grad_xi);
+
+/*
  * Log-sum-exp weighting (Eq. 11): logw += ll (ll: P floats, host or device),
  * then w = exp(logw - M - log S) in FP64. w_out: NULL or P doubles (host or
  * device). res: NULL or host struct receiving ess, max_w, argmax, log_norm and

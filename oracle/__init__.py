@@ -110,6 +110,24 @@ def se3_log(T):
     return out
 
 
+def se3_jr(xi):
+    xi, px = _d(xi)
+    J = np.zeros(36)
+    lib().ora_se3_jr(px, J.ctypes.data_as(_dp))
+    return J.reshape(6, 6)
+
+
+def loglik_grad_xi(T0, xi, Tk, tables, grids, scan, eps=1e-3, face_delta=1e-3):
+    """l(T0 exp(xi)) and its derivative in xi: Jr(xi)^T times the right-perturbation
+    gradient at T0 exp(xi); slack and gradient mass are mapped the same way."""
+    T = pose_mul(T0, se3_exp(xi))
+    o = eval_particle(T, Tk, tables, grids, scan, eps, face_delta)
+    J = se3_jr(xi)
+    o["g_xi"] = J.T @ o["g"]
+    o["jr_norm"] = float(np.linalg.norm(J, 2))
+    return o
+
+
 # ---------------------------------------------------------------- random draws
 def philox4x32_10(ctr, key):
     c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])

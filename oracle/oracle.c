@@ -133,6 +133,58 @@ void ora_se3_log(const double T[12], double xi[6]) {
     xi[0] = w[0]; xi[1] = w[1]; xi[2] = w[2];
 }
 
+/* Right Jacobian of SE(3): exp(xi + d) = exp(xi) exp(Jr(xi) d + O(d^2)). With
+ * xi = [omega; v] it is Jl(-xi), and the left Jacobian in this order is
+ * [[J, 0], [Q, J]] with J the SO(3) left Jacobian I + b W + c W^2 and, for
+ * rho = v, phi = omega (Barfoot, State Estimation for Robotics, Sec. 7.1.5),
+ *   Q = rho^/2 + c1 (phi^ rho^ + rho^ phi^ + phi^ rho^ phi^)
+ *       + c2 (phi^ phi^ rho^ + rho^ phi^ phi^ - 3 phi^ rho^ phi^)
+ *       + c3 (phi^ rho^ phi^ phi^ + phi^ phi^ rho^ phi^),
+ *   c1 = (th - sin th)/th^3, c2 = (th^2 + 2 cos th - 2)/(2 th^4),
+ *   c3 = (2 th - 3 sin th + th cos th)/(2 th^5); power series below th = 0.1. */
+void ora_se3_jr(const double xi[6], double J[36]) {
+    double phi[3] = {-xi[0], -xi[1], -xi[2]}, rho[3] = {-xi[3], -xi[4], -xi[5]};
+    double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
+    double th = sqrt(th2);
+    double b, c1, c2, c3;
+    if (th < 0.1) {
+        b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        c1 = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0 - th2 * th2 * th2 / 362880.0;
+        c2 = 1.0 / 24.0 - th2 / 720.0 + th2 * th2 / 40320.0;
+        c3 = 1.0 / 120.0 - th2 / 2520.0 + th2 * th2 / 120960.0;
+    } else {
+        double s = sin(th), c = cos(th);
+        b = (1.0 - c) / th2;
+        c1 = (th - s) / (th2 * th);
+        c2 = (th2 + 2.0 * c - 2.0) / (2.0 * th2 * th2);
+        c3 = (2.0 * th - 3.0 * s + th * c) / (2.0 * th2 * th2 * th);
+    }
+    double P[9], R[9], P2[9], Jso[9];
+    hat(phi, P);
+    hat(rho, R);
+    mat3_mul(P, P, P2);
+    for (int i = 0; i < 9; ++i) Jso[i] = ((i % 4 == 0) ? 1.0 : 0.0) + b * P[i] + c1 * P2[i];
+    double PR[9], RP[9], PRP[9], PPR[9], RPP[9], PRPP[9], PPRP[9];
+    mat3_mul(P, R, PR);
+    mat3_mul(R, P, RP);
+    mat3_mul(PR, P, PRP);
+    mat3_mul(P, PR, PPR);
+    mat3_mul(RP, P, RPP);
+    mat3_mul(PRP, P, PRPP);
+    mat3_mul(P, PRP, PPRP);
+    double Q[9];
+    for (int i = 0; i < 9; ++i)
+        Q[i] = 0.5 * R[i] + c1 * (PR[i] + RP[i] + PRP[i]) + c2 * (PPR[i] + RPP[i] - 3.0 * PRP[i]) +
+               c3 * (PRPP[i] + PPRP[i]);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            J[r * 6 + c] = Jso[r * 3 + c];
+            J[r * 6 + 3 + c] = 0.0;
+            J[(3 + r) * 6 + c] = Q[r * 3 + c];
+            J[(3 + r) * 6 + 3 + c] = Jso[r * 3 + c];
+        }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, as defined by Salmon, Moraes, Dror and Shaw, "Parallel      */
 /* random numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64   */

@@ -38,6 +38,8 @@ void ora_pose_mul(const double A[12], const double B[12], double C[12]);
 void ora_pose_inv(const double A[12], double B[12]);
 void ora_se3_exp(const double xi[6], double T[12]);
 void ora_se3_log(const double T[12], double xi[6]);
+/* Right Jacobian: exp(xi + d) = exp(xi) exp(Jr d) to first order (6 x 6, row-major). */
+void ora_se3_jr(const double xi[6], double J[36]);
 
 /* ---- Philox4x32-10 (Salmon et al., SC'11) and the draws built on it */
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

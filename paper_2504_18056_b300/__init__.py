@@ -74,6 +74,8 @@ _SIGS = {
     "gmcs_select": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gmcs_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmcs_move": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "gmcs_loglik": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_loglik_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "gmcs_weigh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(StepOut)]),
     "gmcs_resample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
     "gmcs_get_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -245,6 +247,15 @@ class Filter:
 
     def move(self, scan):
         _check(lib().gmcs_move(self.ctx, _ptr(scan), int(scan.shape[0])), "gmcs_move")
+
+    def loglik(self, xi, scan, ll):
+        _check(lib().gmcs_loglik(self.ctx, _ptr(xi), _ptr(scan), int(scan.shape[0]), _ptr(ll)), "gmcs_loglik")
+        return ll
+
+    def loglik_backward(self, xi, scan, grad_ll, grad_xi):
+        _check(lib().gmcs_loglik_backward(self.ctx, _ptr(xi), _ptr(scan), int(scan.shape[0]), _ptr(grad_ll),
+                                          _ptr(grad_xi)), "gmcs_loglik_backward")
+        return grad_xi
 
     def weigh(self, ll, w_out=None):
         res = StepOut()

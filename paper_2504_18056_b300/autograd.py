@@ -1,0 +1,35 @@
+"""torch.autograd.Function over the scan log-likelihood (argument marshalling only).
+
+ScanLogLik.apply(xi, filt, scan) returns ll[P], the log-likelihood of the scan
+for every particle of `filt` at the pose T0 exp(xi_i) (T0: the particle's current
+pose, neighbour keyframes as last selected). The forward runs the value-only
+lookup pass; the backward runs the lookup pass with gradient at the same poses
+and the chain rule through the SE(3) right Jacobian, both in CUDA
+(gmcs_loglik / gmcs_loglik_backward).
+"""
+import torch
+
+
+class ScanLogLik(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xi, filt, scan):
+        if not (xi.is_cuda and scan.is_cuda):
+            raise ValueError("xi and scan must be CUDA tensors")
+        xi = xi.detach().to(torch.float32).contiguous()
+        scan = scan.detach().to(torch.float32).contiguous()
+        ll = torch.empty(xi.shape[0], dtype=torch.float32, device=xi.device)
+        filt.loglik(xi, scan, ll)
+        ctx.filt = filt
+        ctx.save_for_backward(xi, scan)
+        return ll
+
+    @staticmethod
+    def backward(ctx, grad_ll):
+        xi, scan = ctx.saved_tensors
+        grad_xi = torch.empty_like(xi)
+        ctx.filt.loglik_backward(xi, scan, grad_ll.detach().to(torch.float32).contiguous(), grad_xi)
+        return grad_xi, None, None
+
+
+def scan_loglik(xi, filt, scan):
+    return ScanLogLik.apply(xi, filt, scan)

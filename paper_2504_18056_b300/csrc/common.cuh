@@ -101,6 +101,62 @@ __device__ __forceinline__ void se3_exp(const float* xi, float* T) {
     for (int r = 0; r < 3; ++r) T[r * 4 + 3] = V[r * 3 + 0] * xi[3] + V[r * 3 + 1] * xi[4] + V[r * 3 + 2] * xi[5];
 }
 
+// Right Jacobian of SE(3) for xi = [omega; v]: exp(xi + d) = exp(xi) exp(Jr d) to
+// first order. Jr(xi) = Jl(-xi); the left Jacobian in this order is [[J, 0], [Q, J]]
+// with J = I + b W + c1 W^2 (W = phi^) and, for rho = v, phi = omega,
+//   Q = rho^/2 + c1 (W R + R W + W R W) + c2 (W W R + R W W - 3 W R W) + c3 (W R W W + W W R W),
+//   c1 = (th - sin th)/th^3, c2 = (th^2 + 2 cos th - 2)/(2 th^4), c3 = (2 th - 3 sin th + th cos th)/(2 th^5)
+// (Barfoot, State Estimation for Robotics); power series below th = 0.5 in float.
+__device__ __forceinline__ void mat3mul(const float* A, const float* B, float* C) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) C[r * 3 + c] = A[r * 3] * B[c] + A[r * 3 + 1] * B[3 + c] + A[r * 3 + 2] * B[6 + c];
+}
+
+__device__ __forceinline__ void se3_jr(const float* xi, float* J) {
+    const float px = -xi[0], py = -xi[1], pz = -xi[2];
+    const float rx = -xi[3], ry = -xi[4], rz = -xi[5];
+    const float th2 = px * px + py * py + pz * pz;
+    float b, c1, c2, c3;
+    if (th2 < 0.25f) {
+        b = 0.5f - th2 * (1.f / 24.f) + th2 * th2 * (1.f / 720.f) - th2 * th2 * th2 * (1.f / 40320.f);
+        c1 = (1.f / 6.f) - th2 * (1.f / 120.f) + th2 * th2 * (1.f / 5040.f) - th2 * th2 * th2 * (1.f / 362880.f);
+        c2 = (1.f / 24.f) - th2 * (1.f / 720.f) + th2 * th2 * (1.f / 40320.f);
+        c3 = (1.f / 120.f) - th2 * (1.f / 2520.f) + th2 * th2 * (1.f / 120960.f);
+    } else {
+        const float th = sqrtf(th2), sn = sinf(th), cs = cosf(th);
+        b = (1.f - cs) / th2;
+        c1 = (th - sn) / (th2 * th);
+        c2 = (th2 + 2.f * cs - 2.f) / (2.f * th2 * th2);
+        c3 = (2.f * th - 3.f * sn + th * cs) / (2.f * th2 * th2 * th);
+    }
+    const float W[9] = {0.f, -pz, py, pz, 0.f, -px, -py, px, 0.f};
+    const float R[9] = {0.f, -rz, ry, rz, 0.f, -rx, -ry, rx, 0.f};
+    float WW[9], WR[9], RW[9], WRW[9], WWR[9], RWW[9], WRWW[9], WWRW[9];
+    mat3mul(W, W, WW);
+    mat3mul(W, R, WR);
+    mat3mul(R, W, RW);
+    mat3mul(WR, W, WRW);
+    mat3mul(W, WR, WWR);
+    mat3mul(RW, W, RWW);
+    mat3mul(WRW, W, WRWW);
+    mat3mul(W, WRW, WWRW);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int e = r * 3 + c;
+            const float Jso = (r == c ? 1.f : 0.f) + b * W[e] + c1 * WW[e];
+            const float Q = 0.5f * R[e] + c1 * (WR[e] + RW[e] + WRW[e]) + c2 * (WWR[e] + RWW[e] - 3.f * WRW[e]) +
+                            c3 * (WRWW[e] + WWRW[e]);
+            J[r * 6 + c] = Jso;
+            J[r * 6 + 3 + c] = 0.f;
+            J[(3 + r) * 6 + c] = Q;
+            J[(3 + r) * 6 + 3 + c] = Jso;
+        }
+}
+
 __device__ __forceinline__ void load_pose(const float* __restrict__ base, size_t ld, int i, float* T) {
 #pragma unroll
     for (int c = 0; c < kPoseC; ++c) T[c] = base[(size_t)c * ld + i];

@@ -53,6 +53,7 @@ struct gmcs_ctx {
     float* kf[2] = {nullptr, nullptr};
     double* logw = nullptr;
     double* w = nullptr;             // normalised weights of the last frame
+    float* gbuf = nullptr;           // P x 6 gradients (differentiable log-likelihood)
     float* ll = nullptr;
     int* nbr = nullptr;
     float* part = nullptr;
@@ -208,11 +209,12 @@ int upload_scan(gmcs_ctx* c, const float* scan, int N) {
     return check_launch();
 }
 
-int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw) {
+int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw,
+             const float* pose_override = nullptr) {
     int nt, groups, chunk;
     pass_shape(c->P, N, &nt, &groups, &chunk);
     PassArgs pa;
-    pa.pose = c->pose[c->cur];
+    pa.pose = pose_override ? pose_override : c->pose[c->cur];
     pa.kf = c->kf[c->cur];
     pa.nbr = c->nbr;
     pa.tables = c->d_tables;
@@ -461,6 +463,7 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     if (!rc) rc = dalloc(c, &c->logw, ld);
     if (!rc) rc = dalloc(c, &c->ll, ld);
     if (!rc) rc = dalloc(c, &c->w, ld);
+    if (!rc) rc = dalloc(c, &c->gbuf, (size_t)6 * ld);
     if (!rc) rc = dalloc(c, &c->nbr, (size_t)GMCS_MAX_NB * ld);
     if (!rc) rc = dalloc(c, &c->part, c->part_floats);
     if (!rc) rc = dalloc(c, &c->scan, (size_t)max_points);
@@ -494,7 +497,7 @@ int gmcs_destroy(gmcs_ctx* c) {
     harvest(c);
     for (auto e : c->free_events) cudaEventDestroy(e);
     for (auto& t : c->tables) cudaFree(t.cells);
-    void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->ll, c->nbr, c->part, c->scan,
+    void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->gbuf, c->ll, c->nbr, c->part, c->scan,
                     c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->anc, c->d_tables, c->d2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -768,6 +771,60 @@ int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float*
         cudaFree(tmp);
     }
     return rc;
+}
+
+// Poses T0 exp(xi) into the alternate pose buffer (xi staged when on the host).
+static int perturbed_poses(gmcs_ctx* c, const float* xi, const float** pose_out) {
+    const float* dxi = xi;
+    if (!is_device_ptr(xi)) {
+        CK(cudaMemcpyAsync(c->stage, xi, sizeof(float) * 6 * (size_t)c->P, cudaMemcpyHostToDevice, c->stream));
+        dxi = c->stage;
+    }
+    float* dst = c->pose[1 - c->cur];
+    {
+        Launch L(c, K_MISC);
+        launch_perturb(c->pose[c->cur], dxi, c->P, c->ld, dst, c->stream);
+    }
+    *pose_out = dst;
+    return check_launch();
+}
+
+int gmcs_loglik(gmcs_ctx* c, const float* xi, const float* scan, int N, float* ll) {
+    if (!c || !xi || !ll) return GMCS_E_INVALID;
+    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
+    int rc = upload_scan(c, scan, N);
+    if (rc) return rc;
+    const float* T = nullptr;
+    if ((rc = perturbed_poses(c, xi, &T))) return rc;
+    const bool dev = is_device_ptr(ll);
+    if ((rc = run_pass(c, N, false, false, dev ? ll : c->ll, nullptr, nullptr, nullptr, T))) return rc;
+    if (!dev) return copy_out(c, ll, c->ll, sizeof(float) * c->P);
+    return GMCS_OK;
+}
+
+int gmcs_loglik_backward(gmcs_ctx* c, const float* xi, const float* scan, int N, const float* grad_ll, float* grad_xi) {
+    if (!c || !xi || !grad_ll || !grad_xi) return GMCS_E_INVALID;
+    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
+    int rc = upload_scan(c, scan, N);
+    if (rc) return rc;
+    const float* T = nullptr;
+    if ((rc = perturbed_poses(c, xi, &T))) return rc;
+    if ((rc = run_pass(c, N, true, false, nullptr, c->gbuf, nullptr, nullptr, T))) return rc;
+    const float* dxi = is_device_ptr(xi) ? xi : c->stage;
+    const float* dgl = grad_ll;
+    if (!is_device_ptr(grad_ll)) {
+        CK(cudaMemcpyAsync(c->ll, grad_ll, sizeof(float) * c->P, cudaMemcpyHostToDevice, c->stream));
+        dgl = c->ll;
+    }
+    const bool dev = is_device_ptr(grad_xi);
+    float* out = dev ? grad_xi : reinterpret_cast<float*>(c->part);
+    {
+        Launch L(c, K_MISC);
+        launch_chain(dxi, c->gbuf, dgl, c->P, out, c->stream);
+    }
+    if ((rc = check_launch())) return rc;
+    if (!dev) return copy_out(c, grad_xi, out, sizeof(float) * 6 * (size_t)c->P);
+    return GMCS_OK;
 }
 
 int gmcs_move(gmcs_ctx* c, const float* scan, int N) {

@@ -563,7 +563,53 @@ __global__ void __launch_bounds__(128) k_finish(FinishArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ differentiable log-likelihood
+
+// dst_i = T0_i exp(xi_i)  (xi: P x 6, row-major)
+__global__ void __launch_bounds__(128) k_perturb(const float* __restrict__ pose0, const float* __restrict__ xi, int P,
+                                                 size_t ld, float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    float x[6], T[12], E[12], out[12];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x[d] = xi[(size_t)i * 6 + d];
+    load_pose(pose0, ld, i, T);
+    se3_exp(x, E);
+    pose_mul(T, E, out);
+    store_pose(dst, ld, i, out);
+}
+
+// grad_xi_i = grad_ll_i * Jr(xi_i)^T g_i, with g_i the right-perturbation gradient at T0_i exp(xi_i)
+__global__ void __launch_bounds__(128) k_chain(const float* __restrict__ xi, const float* __restrict__ g,
+                                               const float* __restrict__ grad_ll, int P, float* __restrict__ grad_xi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    float x[6], J[36], gi[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        x[d] = xi[(size_t)i * 6 + d];
+        gi[d] = g[(size_t)i * 6 + d];
+    }
+    se3_jr(x, J);
+    const float s = grad_ll[i];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) acc += J[r * 6 + c] * gi[r];
+        grad_xi[(size_t)i * 6 + c] = s * acc;
+    }
+}
+
 // ------------------------------------------------------------------ launchers
+
+void launch_perturb(const float* pose0, const float* xi, int P, size_t ld, float* dst, cudaStream_t s) {
+    if (P > 0) k_perturb<<<(P + 127) / 128, 128, 0, s>>>(pose0, xi, P, ld, dst);
+}
+
+void launch_chain(const float* xi, const float* g, const float* grad_ll, int P, float* grad_xi, cudaStream_t s) {
+    if (P > 0) k_chain<<<(P + 127) / 128, 128, 0, s>>>(xi, g, grad_ll, P, grad_xi);
+}
 
 static int blocks_for(size_t n, int threads, int cap = 148 * 16) {
     size_t b = (n + threads - 1) / threads;

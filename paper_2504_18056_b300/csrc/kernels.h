@@ -92,6 +92,10 @@ struct FinishArgs {
     double* logw;           // value pass: logw += ll when non-null
 };
 
+// Differentiable log-likelihood: poses T0 exp(xi) and the chain rule through Jr(xi).
+void launch_perturb(const float* pose0, const float* xi, int P, size_t ld, float* dst, cudaStream_t s);
+void launch_chain(const float* xi, const float* g, const float* grad_ll, int P, float* grad_xi, cudaStream_t s);
+
 void launch_scan_pack(const float* xyz, int n, float4* out, cudaStream_t s);
 void launch_aos_to_soa(const float* aos, int P, int C, float* soa, size_t ld, cudaStream_t s);
 void launch_soa_to_aos(const float* soa, size_t ld, int P, int C, float* aos, cudaStream_t s);

@@ -395,3 +395,28 @@ def test_resample_exact_rational_definition():
 def test_paper_memory_claim():
     P, K, b, mib = [int(x) for x in open(os.path.join(GOLDEN, "paper_memory_claim.txt")).read().split("\n")[-2].split()]
     assert round(P * K * b / 2 ** 20) == mib
+
+
+# ----------------------------------------------------------------- SE(3) right Jacobian
+@pytest.mark.parametrize("scale", [0.0, 1e-6, 0.05, 0.099, 0.101, 0.7, 2.0])
+def test_se3_right_jacobian_matches_matrix_exponential(scale):
+    """Column d of Jr(xi) is log(exp(xi)^-1 exp(xi + h e_d)) / h, from scipy's
+    expm and logm (central differences, h = 1e-6)."""
+    rng = np.random.default_rng(int(scale * 1000) + 7)
+    for _ in range(3):
+        w = rng.normal(size=3)
+        w = w / np.linalg.norm(w) * scale
+        xi = np.concatenate([w, rng.normal(size=3)])
+        J = oracle.se3_jr(xi)
+        h = 1e-6
+        E0inv = np.linalg.inv(scipy.linalg.expm(twist(xi)))
+        num = np.zeros((6, 6))
+        for d in range(6):
+            e = np.zeros(6)
+            e[d] = h
+            Lp = scipy.linalg.logm(E0inv @ scipy.linalg.expm(twist(xi + e))).real
+            Lm = scipy.linalg.logm(E0inv @ scipy.linalg.expm(twist(xi - e))).real
+            D = (Lp - Lm) / (2 * h)
+            num[:, d] = [D[2, 1], D[0, 2], D[1, 0], D[0, 3], D[1, 3], D[2, 3]]
+        np.testing.assert_allclose(J, num, atol=2e-7)
+    np.testing.assert_array_equal(oracle.se3_jr(np.zeros(6)), np.eye(6))
