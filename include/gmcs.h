@@ -72,6 +72,11 @@ typedef struct {
     int steps;         /* gradient-guided moves per frame */
     int table_dtype;   /* GMCS_TABLE_* storage type of the likelihood tables */
     int resample;      /* GMCS_RESAMPLE_* policy */
+    int propagate;     /* 1: after every move, propagate psi to the particle's keyframe poses
+                          (Eq. 8-10, see gmcs_set_path); 0: off */
+    int loop_recent;   /* > 0: a particle moves only when its oldest neighbour keyframe is not
+                          among the loop_recent newest keyframes (the loop condition of
+                          Sec. III-C2); 0: every particle moves every frame */
     int reserved;
     uint64_t seed;     /* key of the Philox4x32-10 draws (motion noise, resampling offset) */
 } gmcs_config;
@@ -108,7 +113,8 @@ typedef struct {
 typedef struct gmcs_ctx gmcs_ctx;
 
 /* Defaults: sigma 0.2 m, r_t 1.0 m, eps 1e-3, lambda 1e-3, theta_max 2 deg,
- * t_max 0.1 m, w_min 1e-6, k_nb 3, steps 3, FP32 tables, resample always, seed 0. */
+ * t_max 0.1 m, w_min 1e-6, k_nb 3, steps 3, FP32 tables, resample always,
+ * no propagation, no loop condition, seed 0. */
 void gmcs_config_default(gmcs_config* cfg);
 
 /*
@@ -171,6 +177,16 @@ int gmcs_add_keyframe(gmcs_ctx* ctx, const float* pts, int n, const gmcs_grid* g
  */
 int gmcs_step(gmcs_ctx* ctx, const float* scan, int N, const double delta_T[12], const double cov[36],
               const double* u_override, gmcs_step_out* out);
+
+/*
+ * Odometry path lengths for keyframe pose propagation (Eq. 9): `now` is the
+ * travelled distance at the current frame; kf_path (K doubles, host, or NULL)
+ * that at each keyframe's frame. gmcs_add_keyframe records the current value for
+ * the new keyframe and gmcs_step adds |t(delta_T)| before its moves. With o the
+ * particle's oldest neighbour keyframe, keyframe k > o moves by exp(r_k psi),
+ * r_k = (D_k - D_o) / (now - D_o), clamped to [0, 1]; nothing moves if now <= D_o.
+ */
+int gmcs_set_path(gmcs_ctx* ctx, double now, const double* kf_path);
 
 /* Result of the last gmcs_step (synchronises the stream). */
 int gmcs_last_result(gmcs_ctx* ctx, gmcs_step_out* out);

@@ -39,7 +39,7 @@ class StepParams(C.Structure):
     _fields_ = [("sigma", C.c_double), ("eps", C.c_double), ("lambda_", C.c_double),
                 ("theta_max", C.c_double), ("t_max", C.c_double), ("w_min", C.c_double),
                 ("face_delta", C.c_double), ("k_nb", C.c_int), ("steps", C.c_int),
-                ("resample", C.c_int), ("seed", C.c_uint64)]
+                ("resample", C.c_int), ("propagate", C.c_int), ("loop_recent", C.c_int), ("seed", C.c_uint64)]
 
 
 class StepOut(C.Structure):
@@ -48,7 +48,7 @@ class StepOut(C.Structure):
 
 
 DEFAULTS = dict(sigma=0.2, eps=1e-3, lambda_=1e-3, theta_max=np.deg2rad(2.0), t_max=0.1,
-                w_min=1e-6, face_delta=1e-3, k_nb=3, steps=3, resample=0, seed=0)
+                w_min=1e-6, face_delta=1e-3, k_nb=3, steps=3, resample=0, propagate=0, loop_recent=0, seed=0)
 
 
 def lib():
@@ -266,6 +266,22 @@ def predict(T, dT, cov, z):
     return out
 
 
+def propagate(psi, nbr, kf_path, path_now, kf_i):
+    """Eq. 8-10 on one particle's keyframe poses kf_i (K x 12), returned updated."""
+    psi, pp = _d(psi)
+    nb = np.ascontiguousarray(nbr, np.int32)
+    D, pd = _d(kf_path)
+    kf = np.ascontiguousarray(np.asarray(kf_i, np.float64).reshape(-1, 12)).copy()
+    lib().ora_propagate(pp, nb.ctypes.data_as(_ip), C.c_int(nb.size), C.c_int(kf.shape[0]), pd, C.c_double(path_now),
+                        kf.ctypes.data_as(_dp))
+    return kf
+
+
+def loop(nbr, K, recent):
+    nb = np.ascontiguousarray(nbr, np.int32)
+    return bool(lib().ora_loop(nb.ctypes.data_as(_ip), C.c_int(nb.size), C.c_int(K), C.c_int(recent)))
+
+
 def lse(logw, ll):
     logw, pl = _d(logw); ll, pll = _d(ll)
     P = logw.shape[0]
@@ -288,7 +304,9 @@ class State:
     """Particle set held by the oracle in FP64: poses (P, 12), keyframe poses
     (K, P, 12), log-weights (P,), plus the shared keyframe tables."""
 
-    def __init__(self, poses, kf_poses, tables, grids, logw=None):
+    def __init__(self, poses, kf_poses, tables, grids, logw=None, kf_path=None, path_now=0.0):
+        self.kf_path = None if kf_path is None else np.ascontiguousarray(kf_path, np.float64)
+        self.path_now = float(path_now)
         self.poses = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 12))
         self.kf_poses = np.ascontiguousarray(np.asarray(kf_poses, np.float64))
         P = self.poses.shape[0]
@@ -300,7 +318,11 @@ class State:
         prm = dict(DEFAULTS)
         prm.update(params)
         sp = StepParams(prm["sigma"], prm["eps"], prm["lambda_"], prm["theta_max"], prm["t_max"], prm["w_min"],
-                        prm["face_delta"], prm["k_nb"], prm["steps"], prm["resample"], prm["seed"])
+                        prm["face_delta"], prm["k_nb"], prm["steps"], prm["resample"], prm["propagate"],
+                        prm["loop_recent"], prm["seed"])
+        # odometry path length of this frame (Eq. 9 along the odometry trajectory)
+        self.path_now += float(np.linalg.norm(np.asarray(dT, np.float64).reshape(12)[[3, 7, 11]]))
+        kp = None if self.kf_path is None else self.kf_path.ctypes.data_as(_dp)
         P = self.poses.shape[0]
         K = len(self.tables)
         tab_ptrs = (_dp * max(K, 1))(*[t.ctypes.data_as(_dp) for t in self.tables])
@@ -320,7 +342,8 @@ class State:
         ll = np.zeros(P); w = np.zeros(P); anc = np.zeros(P, np.int32); nbr = np.zeros((P, max(k_nb, 1)), np.int32)
         lib().ora_step(C.c_int(P), C.c_int(K), self.poses.ctypes.data_as(_dp), self.kf_poses.ctypes.data_as(_dp),
                        self.logw.ctypes.data_as(_dp), tab_ptrs, grs, ps, C.c_int(scan.shape[0]), pd, pc,
-                       C.c_uint32(frame), zp, up, C.byref(sp), C.byref(out), ll.ctypes.data_as(_dp),
+                       C.c_uint32(frame), zp, up, C.byref(sp), kp, C.c_double(self.path_now),
+                       C.byref(out), ll.ctypes.data_as(_dp),
                        w.ctypes.data_as(_dp), anc.ctypes.data_as(_ip), nbr.ctypes.data_as(_ip))
         return {"estimate": np.array(list(out.estimate)), "ess": out.ess, "max_w": out.max_w,
                 "argmax": out.argmax, "resampled": bool(out.resampled), "ll": ll, "w": w, "anc": anc,

@@ -521,6 +521,36 @@ void ora_move(const double Tt[12], const double g[6], const double mom[10], cons
 }
 
 /* ------------------------------------------------------------------------ */
+/* keyframe pose propagation, Eq. 8-10                                        */
+/* ------------------------------------------------------------------------ */
+
+void ora_propagate(const double psi[6], const int* nbr, int k_nb, int K, const double* D, double Dt, double* kf_i) {
+    int o = -1;
+    for (int s = 0; s < k_nb; ++s)
+        if (nbr[s] >= 0 && (o < 0 || nbr[s] < o)) o = nbr[s];
+    if (o < 0) return;
+    double total = Dt - D[o];           /* d(t_t, t_o) */
+    if (!(total > 0.0)) return;
+    for (int k = o + 1; k < K; ++k) {
+        double r = (D[k] - D[o]) / total;   /* d(t_k, t_o) / d(t_t, t_o) */
+        if (r < 0.0) r = 0.0;
+        if (r > 1.0) r = 1.0;
+        double pk[6], E[12];
+        for (int d = 0; d < 6; ++d) pk[d] = r * psi[d];
+        ora_se3_exp(pk, E);
+        ora_pose_mul(kf_i + 12 * (size_t)k, E, kf_i + 12 * (size_t)k);
+    }
+}
+
+int ora_loop(const int* nbr, int k_nb, int K, int recent) {
+    if (recent <= 0) return 1;
+    int o = -1;
+    for (int s = 0; s < k_nb; ++s)
+        if (nbr[s] >= 0 && (o < 0 || nbr[s] < o)) o = nbr[s];
+    return o >= 0 && o < K - recent;
+}
+
+/* ------------------------------------------------------------------------ */
 /* neighbours, prediction                                                    */
 /* ------------------------------------------------------------------------ */
 
@@ -635,6 +665,7 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
               const double* const* tables, const ora_grid* grids,
               const float* scan, int N, const double dT[12], const double cov[36],
               uint32_t frame, const double* z, const double* u, const ora_step_params* sp,
+              const double* kf_path, double path_now,
               ora_step_out* out, double* ll_out, double* w_out, int* anc_out, int* nbr_out) {
     int k_nb = sp->k_nb < K ? sp->k_nb : K;
     int* nbr = (int*)malloc(sizeof(int) * (size_t)P * (k_nb > 0 ? k_nb : 1));
@@ -675,10 +706,21 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
             }
             double g[6], mom[10];
             if (pass < sp->steps) {
+                const int* nb = nbr + (size_t)i * k_nb;
+                if (!ora_loop(nb, k_nb, K, sp->loop_recent)) continue;   /* Sec. III-C2 */
                 double psi[6];
                 ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
                                   NULL, g, mom, NULL, NULL, NULL, 0);
                 ora_move(poses + 12 * (size_t)i, g, mom, &mp, poses + 12 * (size_t)i, psi);
+                if (sp->propagate && kf_path) {
+                    double* kfi = (double*)malloc(sizeof(double) * 12 * (size_t)K);
+                    for (int k = 0; k < K; ++k)
+                        memcpy(kfi + 12 * (size_t)k, kf_poses + ((size_t)k * P + i) * 12, 12 * sizeof(double));
+                    ora_propagate(psi, nb, k_nb, K, kf_path, path_now, kfi);
+                    for (int k = 0; k < K; ++k)
+                        memcpy(kf_poses + ((size_t)k * P + i) * 12, kfi + 12 * (size_t)k, 12 * sizeof(double));
+                    free(kfi);
+                }
             } else {
                 ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
                                   ll + i, NULL, NULL, NULL, NULL, NULL, 0);

@@ -108,6 +108,17 @@ typedef struct {
 void ora_move(const double Tt[12], const double g[6], const double mom[10], const ora_move_params* mp,
               double Tout[12], double psi[6]);
 
+/* ---- keyframe pose propagation, Eq. 8-10: with o the oldest (lowest-index)
+ * neighbour keyframe, every keyframe k > o moves by T_k exp(r_k psi),
+ * r_k = (D_k - D_o) / (Dt - D_o), D the odometry path length at each keyframe
+ * and Dt at the current frame (Eq. 9 summed along the odometry trajectory).
+ * kf_i: this particle's K keyframe poses (K x 12, in/out). No change when
+ * Dt - D_o <= 0. */
+void ora_propagate(const double psi[6], const int* nbr, int k_nb, int K, const double* D, double Dt, double* kf_i);
+/* Loop condition of Sec. III-C2: 1 if the particle's oldest neighbour keyframe is
+ * not among the `recent` newest keyframes (recent = 0: always 1). */
+int ora_loop(const int* nbr, int k_nb, int K, int recent);
+
 /* ---- neighbour keyframes: the k_nb smallest |t_k - t_t| (ties -> lower k).
  * The squared distances are formed in float with a fixed order of operations,
  * the precision the GPU takes this decision in. */
@@ -129,6 +140,8 @@ typedef struct {
     double sigma, eps, lambda, theta_max, t_max, w_min, face_delta;
     int k_nb, steps;
     int resample;        /* 0 always, 1 when ESS < P/2, 2 never */
+    int propagate;       /* 1: keyframe pose propagation after every move (Eq. 8-10) */
+    int loop_recent;     /* > 0: move only particles whose oldest neighbour is not among the newest loop_recent */
     uint64_t seed;
 } ora_step_params;
 
@@ -145,12 +158,15 @@ typedef struct {
  * frame     frame counter for the counter-based draws
  * z         optional P x 6 standard normals (NULL -> Philox draws)
  * u         optional systematic offset (NULL -> Philox draw)
+ * kf_path   K odometry path lengths of the keyframes, path_now that of this frame
+ *           (used when sp->propagate; may be NULL otherwise)
  * ll_out, w_out, anc_out, nbr_out   optional diagnostics (P, P, P, P x k_nb)
  */
 void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
               const double* const* tables, const ora_grid* grids,
               const float* scan, int N, const double dT[12], const double cov[36],
               uint32_t frame, const double* z, const double* u, const ora_step_params* sp,
+              const double* kf_path, double path_now,
               ora_step_out* out, double* ll_out, double* w_out, int* anc_out, int* nbr_out);
 
 #ifdef __cplusplus

@@ -34,8 +34,8 @@ class GmcsError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("sigma", C.c_float), ("r_t", C.c_float), ("eps", C.c_float), ("lambda_", C.c_float),
                 ("theta_max", C.c_float), ("t_max", C.c_float), ("w_min", C.c_float), ("k_nb", C.c_int),
-                ("steps", C.c_int), ("table_dtype", C.c_int), ("resample", C.c_int), ("reserved", C.c_int),
-                ("seed", C.c_uint64)]
+                ("steps", C.c_int), ("table_dtype", C.c_int), ("resample", C.c_int), ("propagate", C.c_int),
+                ("loop_recent", C.c_int), ("reserved", C.c_int), ("seed", C.c_uint64)]
 
 
 class Grid(C.Structure):
@@ -70,6 +70,7 @@ _SIGS = {
     "gmcs_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                             C.POINTER(C.c_double), C.POINTER(StepOut)]),
     "gmcs_last_result": (C.c_int, [C.c_void_p, C.POINTER(StepOut)]),
+    "gmcs_set_path": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
     "gmcs_predict": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p, C.c_uint32]),
     "gmcs_select": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gmcs_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -215,6 +216,10 @@ class Filter:
         _check(lib().gmcs_add_keyframe(self.ctx, _ptr(points), int(points.shape[0]), C.byref(gr), _ptr(kf_poses),
                                        C.byref(kid)), "gmcs_add_keyframe")
         return kid.value
+
+    def set_path(self, now, kf_path=None):
+        kp = None if kf_path is None else np.ascontiguousarray(kf_path, np.float64)
+        _check(lib().gmcs_set_path(self.ctx, float(now), _ptr(kp)), "gmcs_set_path")
 
     def sizes(self):
         P, K, f = C.c_int(), C.c_int(), C.c_uint32()

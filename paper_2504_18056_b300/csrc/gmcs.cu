@@ -70,6 +70,9 @@ struct gmcs_ctx {
     int* anc = nullptr;
     TableDesc* d_tables = nullptr;
     std::vector<HostTable> tables;
+    std::vector<double> kf_path;     // odometry path length at each keyframe
+    double path_now = 0.0;           // and at the current frame
+    float* d_kf_path = nullptr;
     unsigned* d2 = nullptr;
     size_t d2_cap = 0;
     size_t dev_bytes = 0;
@@ -250,6 +253,14 @@ int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out
     fa.out_g = out_g;
     fa.out_mom = out_mom;
     fa.logw = logw;
+    fa.kf = c->kf[c->cur];
+    fa.nbr = c->nbr;
+    fa.kf_path = c->d_kf_path;
+    fa.path_now = (float)c->path_now;
+    fa.K = c->K;
+    fa.k_nb = std::min(c->cfg.k_nb, c->K);
+    fa.propagate = c->cfg.propagate;
+    fa.loop_recent = c->cfg.loop_recent;
     {
         Launch L(c, K_FINISH);
         launch_finish(fa, grad, c->stream);
@@ -432,6 +443,7 @@ const char* gmcs_strerror(int code) {
 
 static bool config_ok(const gmcs_config* c) {
     return c && c->sigma > 0.f && c->r_t > 0.f && c->eps > 0.f && c->lambda >= 0.f && c->theta_max > 0.f &&
+           (c->propagate == 0 || c->propagate == 1) && c->loop_recent >= 0 &&
            c->t_max > 0.f && c->w_min >= 0.f && c->k_nb >= 1 && c->k_nb <= GMCS_MAX_NB && c->steps >= 0 &&
            c->steps <= 64 && c->table_dtype >= 0 && c->table_dtype <= 2 && c->resample >= 0 && c->resample <= 2;
 }
@@ -475,6 +487,7 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     if (!rc) rc = dalloc(c, &c->btot, (size_t)nb + 1);
     if (!rc) rc = dalloc(c, &c->anc, ld);
     if (!rc) rc = dalloc(c, &c->d_tables, (size_t)max_keyframes);
+    if (!rc) rc = dalloc(c, &c->d_kf_path, (size_t)max_keyframes);
     if (!rc && cudaMallocHost((void**)&c->h_res, sizeof(WeighResult)) != cudaSuccess) {
         cudaGetLastError();
         c->h_res = nullptr;
@@ -498,7 +511,8 @@ int gmcs_destroy(gmcs_ctx* c) {
     for (auto e : c->free_events) cudaEventDestroy(e);
     for (auto& t : c->tables) cudaFree(t.cells);
     void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->gbuf, c->ll, c->nbr, c->part, c->scan,
-                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->anc, c->d_tables, c->d2};
+                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->anc, c->d_tables, c->d2,
+                    c->d_kf_path};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -665,6 +679,14 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
         cudaFree(t.cells);
         return rc;
     }
+    {
+        const float d = (float)c->path_now;
+        if (cudaMemcpy(c->d_kf_path + k, &d, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(t.cells);
+            return GMCS_E_CUDA;
+        }
+    }
+    c->kf_path.push_back(c->path_now);
     c->dev_bytes += t.bytes;
     c->tables.push_back(t);
     c->K = k + 1;
@@ -680,6 +702,8 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
     int rc = upload_scan(c, scan, N);
     if (rc) return rc;
     const uint32_t frame = c->frame;
+    // odometry path length of this frame (Eq. 9 along the odometry trajectory)
+    c->path_now += std::sqrt(delta_T[3] * delta_T[3] + delta_T[7] * delta_T[7] + delta_T[11] * delta_T[11]);
     if ((rc = run_predict(c, delta_T, cov, nullptr, frame))) return rc;
     if ((rc = run_select(c, nullptr))) return rc;
     for (int s = 0; s < c->cfg.steps; ++s)
@@ -707,6 +731,24 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
         fill_out(*c->h_res, frame, out);
         c->last = *out;
     }
+    return GMCS_OK;
+}
+
+int gmcs_set_path(gmcs_ctx* c, double now, const double* kf_path) {
+    if (!c || !std::isfinite(now)) return GMCS_E_INVALID;
+    if (kf_path) {
+        std::vector<float> f(c->K);
+        for (int k = 0; k < c->K; ++k) {
+            if (!std::isfinite(kf_path[k])) return GMCS_E_INVALID;
+            f[k] = (float)kf_path[k];
+        }
+        if (c->K > 0) {
+            CK(cudaMemcpyAsync(c->d_kf_path, f.data(), sizeof(float) * c->K, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        c->kf_path.assign(kf_path, kf_path + c->K);
+    }
+    c->path_now = now;
     return GMCS_OK;
 }
 

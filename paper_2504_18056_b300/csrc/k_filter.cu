@@ -551,13 +551,38 @@ __global__ void __launch_bounds__(128) k_finish(FinishArgs a) {
         if (a.out_mom)
             for (int d = 0; d < 10; ++d) a.out_mom[(size_t)i * 10 + d] = acc[7 + d];
         if (a.do_move) {
+            // oldest (lowest-index) neighbour keyframe of this particle
+            int o = -1;
+            for (int s = 0; s < a.k_nb; ++s) {
+                const int k = a.nbr[(size_t)s * a.ld + i];
+                if (k >= 0 && (o < 0 || k < o)) o = k;
+            }
+            const bool loop = a.loop_recent <= 0 || (o >= 0 && o < a.K - a.loop_recent);
             float psi[6];
-            if (gn_step(acc + 1, acc + 7, a, psi)) {
+            if (loop && gn_step(acc + 1, acc + 7, a, psi)) {
                 float T[12], E[12], out[12];
                 load_pose(a.pose, a.ld, i, T);
                 se3_exp(psi, E);
                 pose_mul(T, E, out);
                 store_pose(a.pose, a.ld, i, out);
+                if (a.propagate && o >= 0) {
+                    // Eq. 8-10: keyframes after the oldest neighbour follow by their path-length share
+                    const float Do = a.kf_path[o];
+                    const float total = a.path_now - Do;
+                    if (total > 0.f) {
+                        for (int k = o + 1; k < a.K; ++k) {
+                            const float r = fminf(fmaxf((a.kf_path[k] - Do) / total, 0.f), 1.f);
+                            float pk[6];
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) pk[d] = r * psi[d];
+                            float* base = a.kf + (size_t)k * kPoseC * a.ld;
+                            load_pose(base, a.ld, i, T);
+                            se3_exp(pk, E);
+                            pose_mul(T, E, out);
+                            store_pose(base, a.ld, i, out);
+                        }
+                    }
+                }
             }
         }
     }

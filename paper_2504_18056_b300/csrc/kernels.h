@@ -90,6 +90,12 @@ struct FinishArgs {
     float* out_g;           // P x 6
     float* out_mom;         // P x 10
     double* logw;           // value pass: logw += ll when non-null
+    // keyframe pose propagation (Eq. 8-10) and the loop condition (moves only)
+    float* kf;              // [K][12][ld]
+    const int* nbr;         // [k_nb][ld]
+    const float* kf_path;   // K odometry path lengths
+    float path_now;
+    int K, k_nb, propagate, loop_recent;
 };
 
 // Differentiable log-likelihood: poses T0 exp(xi) and the chain rule through Jr(xi).

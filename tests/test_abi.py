@@ -40,7 +40,7 @@ def test_binding_covers_header():
 
 def test_struct_sizes_and_defaults():
     import paper_2504_18056_b300 as g
-    assert C.sizeof(g.Config) == 56
+    assert C.sizeof(g.Config) == 64
     assert C.sizeof(g.Grid) == 48
     cfg = g.default_config()
     assert cfg.k_nb == 3 and cfg.steps == 3 and abs(cfg.sigma - 0.2) < 1e-7 and abs(cfg.r_t - 1.0) < 1e-7

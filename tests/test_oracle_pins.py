@@ -420,3 +420,38 @@ def test_se3_right_jacobian_matches_matrix_exponential(scale):
             num[:, d] = [D[2, 1], D[0, 2], D[1, 0], D[0, 3], D[1, 3], D[2, 3]]
         np.testing.assert_allclose(J, num, atol=2e-7)
     np.testing.assert_array_equal(oracle.se3_jr(np.zeros(6)), np.eye(6))
+
+
+# ----------------------------------------------------------------- keyframe propagation, Eq. 8-10
+def test_propagation_closed_form():
+    """Oldest neighbour o keeps its pose (ratio 0), keyframes before it are not
+    touched, keyframe k > o moves by expm(r_k psi) with r_k = (D_k - D_o)/(Dt - D_o),
+    a keyframe at the current path length moves like the current pose (ratio 1)."""
+    rng = np.random.default_rng(21)
+    K = 7
+    kf = np.stack([expm_pose(rng.normal(size=6)) for _ in range(K)])
+    psi = np.array([0.01, -0.02, 0.015, 0.05, -0.03, 0.02])
+    D = np.array([0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 9.0])
+    out = oracle.propagate(psi, [3, 5, 4], D, 9.0, kf)
+    for k in range(K):
+        if k <= 3:
+            np.testing.assert_array_equal(out[k], kf[k])
+        else:
+            r = (D[k] - 3.0) / 6.0
+            np.testing.assert_allclose(to44(out[k]), to44(kf[k]) @ to44(expm_pose(r * psi)), atol=1e-14)
+    np.testing.assert_allclose(to44(out[6]), to44(kf[6]) @ to44(expm_pose(psi)), atol=1e-14)
+    # no path travelled since the oldest neighbour: nothing moves
+    np.testing.assert_array_equal(oracle.propagate(psi, [3, 5, 4], D, 3.0, kf), kf)
+    # ratios clamp to [0, 1]
+    D2 = D.copy()
+    D2[5] = 20.0
+    out2 = oracle.propagate(psi, [3, 5, 4], D2, 9.0, kf)
+    np.testing.assert_allclose(to44(out2[5]), to44(kf[5]) @ to44(expm_pose(psi)), atol=1e-14)
+
+
+def test_loop_condition():
+    assert oracle.loop([5, 6, 7], 8, 0)
+    assert oracle.loop([5, 6, 7], 8, 2)          # oldest neighbour 5 < 8 - 2
+    assert not oracle.loop([6, 7, 5], 8, 3)      # 5 is among the 3 newest
+    assert oracle.loop([6, 7, 4], 8, 3)
+    assert not oracle.loop([-1, -1, -1], 8, 1)
