@@ -49,6 +49,8 @@ extern "C" {
 #define GMCS_E_CAPACITY (-4)  /* more particles / keyframes / points than the context holds */
 #define GMCS_E_STATE (-5)     /* call out of order (e.g. step before particles exist) */
 #define GMCS_E_NONFINITE (-6) /* weights degenerated (all log-weights -inf or NaN); reset to uniform */
+#define GMCS_E_BUDGET (-7)    /* serving: the session does not fit the memory budget or the session limit */
+#define GMCS_PENDING 1        /* serving: the frame has not completed yet */
 
 #define GMCS_TABLE_F32 0
 #define GMCS_TABLE_BF16 1
@@ -306,6 +308,72 @@ int gmcs_reset_stats(gmcs_ctx* ctx);
 
 /* Bytes of device memory the context holds (state, scratch and tables). */
 int gmcs_device_bytes(gmcs_ctx* ctx, uint64_t* bytes);
+
+/* ---- serving: continuous batching of frames from many sessions
+ *
+ * A server holds filter sessions whose state stays on the device (each is a
+ * gmcs_ctx created with the server's config, its own seed, and capacities given
+ * at open). Frames submitted to any session are queued; the server repeatedly
+ * takes, for up to 32 sessions that have a queued frame and none on the GPU,
+ * their oldest frames and runs all of them as one tick: a CUDA graph (captured
+ * once at creation) that uploads the tick's argument records and replays one
+ * persistent launch per kernel of the frame, each walking a work list over the
+ * sessions' blocks. Two ticks can be in flight on disjoint sessions (two
+ * streams), so frames arriving during a tick start without waiting for it.
+ * Every session's frame is computed exactly as gmcs_step computes it (same
+ * kernels, same block decomposition), so its result does not depend on which
+ * other sessions share its ticks.
+ */
+typedef struct gmcs_server gmcs_server;
+
+typedef struct {
+    uint64_t frames;              /* completed frames */
+    uint64_t ticks;               /* graph launches */
+    int sessions;                 /* open sessions */
+    int pad;
+    uint64_t used_bytes, budget_bytes;
+    double evals;                 /* particle x point likelihood+gradient evaluations (P * N * steps) */
+    double span_s;                /* first submission to last completion */
+    double mean_sessions_per_tick;
+    double latency_p50_s, latency_p99_s, latency_max_s, latency_mean_s;   /* submission to completion */
+} gmcs_server_stats;
+
+/* cfg: shared by all sessions (k_nb must be 3); budget_bytes: device memory the
+ * sessions may hold; max_sessions: open-session limit. Errors: GMCS_E_INVALID,
+ * GMCS_E_OOM, GMCS_E_CUDA. */
+int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_sessions, gmcs_server** out);
+int gmcs_server_destroy(gmcs_server* srv);
+/* Run the scheduler on a background thread (start) or not (stop); without it,
+ * gmcs_server_pump / gmcs_server_poll / gmcs_server_drain advance the work. */
+int gmcs_server_start(gmcs_server* srv);
+int gmcs_server_stop(gmcs_server* srv);
+int gmcs_server_pump(gmcs_server* srv);
+/* Admission: open a session if its context (capacities) plus table_bytes fit the
+ * remaining budget, else GMCS_E_BUDGET (retry after another session closes).
+ * Then fill it through its context (gmcs_server_context: gmcs_init_particles,
+ * gmcs_add_keyframe, gmcs_set_path; at least 3 keyframes) and call
+ * gmcs_server_ready, which charges the session's actual device bytes. The
+ * context may be read (gmcs_get_particles, ...) only while the session has no
+ * frame in flight (after gmcs_server_poll reports its frames or after drain). */
+int gmcs_server_open(gmcs_server* srv, int max_particles, int max_keyframes, int max_points, uint64_t table_bytes,
+                     uint64_t seed, int* sid);
+int gmcs_server_context(gmcs_server* srv, int sid, gmcs_ctx** ctx);
+int gmcs_server_ready(gmcs_server* srv, int sid);
+/* Queue one frame (scan: N x 3 host floats, copied into the session's pinned ring
+ * before return; delta_T, cov as in gmcs_step). At most 64 frames per session may
+ * be queued (GMCS_E_CAPACITY beyond). *ticket identifies the frame. */
+int gmcs_server_submit(gmcs_server* srv, int sid, const float* scan, int N, const double delta_T[12],
+                       const double cov[36], uint64_t* ticket);
+/* GMCS_PENDING until the frame completes; then GMCS_OK (once) with its result and
+ * latency (submission to completion, seconds). */
+int gmcs_server_poll(gmcs_server* srv, uint64_t ticket, gmcs_step_out* out, double* latency_s);
+/* Wait until every queued frame has completed. */
+int gmcs_server_drain(gmcs_server* srv);
+/* Close a session: queued frames are dropped (their tickets report GMCS_E_STATE),
+ * a frame on the GPU is waited for, and the session's memory returns to the budget. */
+int gmcs_server_close(gmcs_server* srv, int sid);
+int gmcs_server_get_stats(gmcs_server* srv, gmcs_server_stats* out);
+int gmcs_server_reset_stats(gmcs_server* srv);
 
 const char* gmcs_strerror(int code);
 

@@ -19,7 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgmcs.so")
 
 OK = 0
-E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE = -1, -2, -3, -4, -5, -6
+E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE, E_BUDGET = -1, -2, -3, -4, -5, -6, -7
+PENDING = 1
 TABLE_F32, TABLE_BF16, TABLE_F16 = 0, 1, 2
 RESAMPLE_ALWAYS, RESAMPLE_ESS_HALF, RESAMPLE_NEVER = 0, 1, 2
 MAX_NB = 8
@@ -58,6 +59,16 @@ class Stats(C.Structure):
                 ("kind", C.c_char_p * 16), ("kind_launches", C.c_uint64 * 16), ("kind_ms", C.c_double * 16)]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("frames", C.c_uint64), ("ticks", C.c_uint64), ("sessions", C.c_int), ("pad", C.c_int),
+                ("used_bytes", C.c_uint64), ("budget_bytes", C.c_uint64), ("evals", C.c_double), ("span_s", C.c_double),
+                ("mean_sessions_per_tick", C.c_double), ("latency_p50_s", C.c_double), ("latency_p99_s", C.c_double),
+                ("latency_max_s", C.c_double), ("latency_mean_s", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
 _LIB = None
 
 _SIGS = {
@@ -91,6 +102,21 @@ _SIGS = {
     "gmcs_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "gmcs_strerror": (C.c_char_p, [C.c_int]),
     "gmcs_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
+    "gmcs_server_create": (C.c_int, [C.POINTER(Config), C.c_uint64, C.c_int, C.POINTER(C.c_void_p)]),
+    "gmcs_server_destroy": (C.c_int, [C.c_void_p]),
+    "gmcs_server_start": (C.c_int, [C.c_void_p]),
+    "gmcs_server_stop": (C.c_int, [C.c_void_p]),
+    "gmcs_server_pump": (C.c_int, [C.c_void_p]),
+    "gmcs_server_open": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_int)]),
+    "gmcs_server_context": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "gmcs_server_ready": (C.c_int, [C.c_void_p, C.c_int]),
+    "gmcs_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+    "gmcs_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(StepOut), C.POINTER(C.c_double)]),
+    "gmcs_server_drain": (C.c_int, [C.c_void_p]),
+    "gmcs_server_close": (C.c_int, [C.c_void_p, C.c_int]),
+    "gmcs_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "gmcs_server_reset_stats": (C.c_int, [C.c_void_p]),
 }
 NOALLOC_MAX_P = 262144
 
@@ -182,17 +208,20 @@ def _current_stream():
 class Filter:
     """One filter session: a gmcs_ctx with its particles, keyframe tables and scratch."""
 
-    def __init__(self, max_particles, max_keyframes, max_points, stream=None, **config):
+    def __init__(self, max_particles, max_keyframes, max_points, stream=None, _ctx=None, **config):
         self.cfg = default_config(**config)
-        self.ctx = C.c_void_p()
+        if _ctx is not None:             # a view of a context owned elsewhere (a server session)
+            self.ctx, self.owned = _ctx, False
+            return
+        self.ctx, self.owned = C.c_void_p(), True
         st = _current_stream() if stream is None else C.c_void_p(int(stream))
         _check(lib().gmcs_create(C.byref(self.cfg), int(max_particles), int(max_keyframes), int(max_points), st,
                                  C.byref(self.ctx)), "gmcs_create")
 
     def close(self):
-        if self.ctx:
+        if self.ctx and self.owned:
             lib().gmcs_destroy(self.ctx)
-            self.ctx = C.c_void_p()
+        self.ctx = C.c_void_p()
 
     def __del__(self):
         try:
@@ -312,3 +341,78 @@ class Filter:
         b = C.c_uint64()
         _check(lib().gmcs_device_bytes(self.ctx, C.byref(b)), "gmcs_device_bytes")
         return int(b.value)
+
+
+class Server:
+    """Continuous batching of frames from many sessions (gmcs_server_*)."""
+
+    def __init__(self, budget_bytes, max_sessions=32, background=True, **config):
+        self.cfg = default_config(**config)
+        self.srv = C.c_void_p()
+        _check(lib().gmcs_server_create(C.byref(self.cfg), int(budget_bytes), int(max_sessions), C.byref(self.srv)),
+               "gmcs_server_create")
+        if background:
+            _check(lib().gmcs_server_start(self.srv), "gmcs_server_start")
+
+    def close(self):
+        if self.srv:
+            lib().gmcs_server_destroy(self.srv)
+            self.srv = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open(self, max_particles, max_keyframes, max_points, table_bytes=0, seed=0):
+        """Session id, or None when it does not fit the budget (GMCS_E_BUDGET)."""
+        sid = C.c_int()
+        rc = lib().gmcs_server_open(self.srv, int(max_particles), int(max_keyframes), int(max_points),
+                                    C.c_uint64(int(table_bytes)), C.c_uint64(int(seed)), C.byref(sid))
+        if rc == E_BUDGET:
+            return None
+        _check(rc, "gmcs_server_open")
+        return sid.value
+
+    def session(self, sid):
+        """A Filter view of the session's context, for setup and readback."""
+        ctx = C.c_void_p()
+        _check(lib().gmcs_server_context(self.srv, int(sid), C.byref(ctx)), "gmcs_server_context")
+        return Filter(0, 0, 0, _ctx=ctx)
+
+    def ready(self, sid):
+        _check(lib().gmcs_server_ready(self.srv, int(sid)), "gmcs_server_ready")
+
+    def submit(self, sid, scan, delta_T, cov):
+        t = C.c_uint64()
+        _check(lib().gmcs_server_submit(self.srv, int(sid), _ptr(scan), int(scan.shape[0]), _dbl(delta_T, 12),
+                                        _dbl(cov, 36), C.byref(t)), "gmcs_server_submit")
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (result dict, latency seconds)."""
+        out = StepOut()
+        lat = C.c_double()
+        rc = lib().gmcs_server_poll(self.srv, C.c_uint64(ticket), C.byref(out), C.byref(lat))
+        if rc == PENDING:
+            return None
+        _check(rc, "gmcs_server_poll")
+        return out.as_dict(), lat.value
+
+    def pump(self):
+        _check(lib().gmcs_server_pump(self.srv), "gmcs_server_pump")
+
+    def drain(self):
+        _check(lib().gmcs_server_drain(self.srv), "gmcs_server_drain")
+
+    def close_session(self, sid):
+        _check(lib().gmcs_server_close(self.srv, int(sid)), "gmcs_server_close")
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().gmcs_server_get_stats(self.srv, C.byref(st)), "gmcs_server_get_stats")
+        return st.as_dict()
+
+    def reset_stats(self):
+        _check(lib().gmcs_server_reset_stats(self.srv), "gmcs_server_reset_stats")

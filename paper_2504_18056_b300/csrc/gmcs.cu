@@ -15,79 +15,52 @@
 #include <vector>
 
 #include "../../include/gmcs.h"
+#include "context.h"
 #include "kernels.h"
 
 using namespace gmcs;
 
 namespace {
 
-enum Kind { K_PREDICT, K_SELECT, K_PASS_GRAD, K_PASS_VALUE, K_FINISH, K_WEIGH, K_RESAMPLE, K_GATHER, K_TABLE, K_MISC, K_COUNT };
 const char* kKindName[K_COUNT] = {"predict", "select", "pass_grad", "pass_value", "finish",
                                   "weigh", "resample", "gather", "table", "layout"};
 
-struct HostTable {
-    void* cells = nullptr;
-    size_t bytes = 0;
-    gmcs_grid grid;
-    int dtype = 0;
-};
-
-struct EvPair {
-    int kind;
-    cudaEvent_t a, b;
-};
-
 }  // namespace
 
-struct gmcs_ctx {
-    gmcs_config cfg;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int Pmax = 0, Kmax = 0, Nmax = 0;
-    size_t ld = 0;
-    int P = 0, K = 0;
-    uint32_t frame = 0;
-    bool have_particles = false;
-    int cur = 0;
-    float* pose[2] = {nullptr, nullptr};
-    float* kf[2] = {nullptr, nullptr};
-    double* logw = nullptr;
-    double* w = nullptr;             // normalised weights of the last frame
-    float* gbuf = nullptr;           // P x 6 gradients (differentiable log-likelihood)
-    float* ll = nullptr;
-    int* nbr = nullptr;
-    float* part = nullptr;
-    size_t part_floats = 0;
-    float4* scan = nullptr;
-    float* stage = nullptr;          // N x 3 points / P x 6 noise staging
-    size_t stage_floats = 0;
-    double* wpart = nullptr;
-    unsigned* counter = nullptr;
-    WeighResult* d_res = nullptr;
-    WeighResult* h_res = nullptr;    // pinned
-    unsigned long long* cl = nullptr;
-    unsigned long long* btot = nullptr;
-    int* anc = nullptr;
-    TableDesc* d_tables = nullptr;
-    std::vector<HostTable> tables;
-    std::vector<double> kf_path;     // odometry path length at each keyframe
-    double path_now = 0.0;           // and at the current frame
-    float* d_kf_path = nullptr;
-    unsigned* d2 = nullptr;
-    size_t d2_cap = 0;
-    size_t dev_bytes = 0;
-    // stats
-    uint64_t launches = 0, frames = 0;
-    uint64_t kind_launches[K_COUNT] = {0};
-    double kind_ms[K_COUNT] = {0};
-    bool profiling = false;
-    std::vector<EvPair> pending;
-    std::vector<cudaEvent_t> free_events;
-    gmcs_step_out last{};
-    bool last_valid = false;
-};
+namespace gmcs {
 
-namespace {
+// Chunking of the scan for the lookup pass: a CTA covers kPassTW particle tiles
+// x kPassCW point chunks; the number of chunk groups G gives several waves of
+// CTAs on 148 SMs, at most kMaxGroups (the partial-sum scratch), chunks >= 8 points.
+void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len) {
+    const int nt = (P + 31) / 32;
+    const int ntg = (nt + kPassTW - 1) / kPassTW;
+    const int target = 148 * 8 * 4;
+    int g = (target + ntg - 1) / ntg;
+    g = std::max(1, std::min(g, kMaxGroups));
+    const int max_chunks = std::max(1, (N + 7) / 8);
+    while (g > 1 && g * kPassCW > max_chunks) --g;
+    const int chunks = g * kPassCW;
+    *ntiles = nt;
+    *groups = g;
+    *chunk_len = std::max(1, (N + chunks - 1) / chunks);
+}
+
+// Device bytes gmcs_create allocates for these capacities (tables excluded).
+size_t ctx_device_bytes(int max_particles, int max_keyframes, int max_points) {
+    const size_t ld = ((size_t)max_particles + 31) / 32 * 32;
+    const size_t nb = (max_particles + kScanBlock - 1) / kScanBlock;
+    const size_t part = std::max((size_t)kMaxGroups * kAccGrad * ld, (size_t)12 * ld);
+    const size_t stage = std::max((size_t)3 * max_points, (size_t)6 * ld);
+    size_t b = 0;
+    b += 2 * (sizeof(float) * kPoseC * ld + sizeof(float) * kPoseC * ld * max_keyframes);
+    b += sizeof(double) * ld * 2 + sizeof(float) * ld + sizeof(float) * 6 * ld;   // logw, w, ll, gbuf
+    b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * max_points + sizeof(float) * stage;
+    b += sizeof(double) * 4 * 148 * 4 + sizeof(unsigned) + sizeof(WeighResult);
+    b += sizeof(unsigned long long) * (ld + nb + 1) + sizeof(int) * ld;
+    b += sizeof(TableDesc) * max_keyframes + sizeof(float) * max_keyframes;
+    return b;
+}
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return GMCS_OK;
@@ -97,6 +70,10 @@ int cuda_status(cudaError_t e) {
     }
     return GMCS_E_CUDA;
 }
+
+}  // namespace gmcs
+
+namespace {
 
 #define CK(expr)                                   \
     do {                                           \
@@ -179,23 +156,6 @@ void harvest(gmcs_ctx* c) {
     cudaGetLastError();
 }
 
-// Chunking of the scan for the lookup pass: a CTA covers kPassTW particle tiles
-// x kPassCW point chunks; the number of chunk groups G gives several waves of
-// CTAs on 148 SMs, at most kMaxGroups (the partial-sum scratch), chunks >= 8 points.
-void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len) {
-    const int nt = (P + 31) / 32;
-    const int ntg = (nt + kPassTW - 1) / kPassTW;
-    const int target = 148 * 8 * 4;
-    int g = (target + ntg - 1) / ntg;
-    g = std::max(1, std::min(g, kMaxGroups));
-    const int max_chunks = std::max(1, (N + 7) / 8);
-    while (g > 1 && g * kPassCW > max_chunks) --g;
-    const int chunks = g * kPassCW;
-    *ntiles = nt;
-    *groups = g;
-    *chunk_len = std::max(1, (N + chunks - 1) / chunks);
-}
-
 int upload_scan(gmcs_ctx* c, const float* scan, int N) {
     if (N < 0 || (N > 0 && !scan)) return GMCS_E_INVALID;
     if (N > c->Nmax) return GMCS_E_CAPACITY;
@@ -212,8 +172,13 @@ int upload_scan(gmcs_ctx* c, const float* scan, int N) {
     return check_launch();
 }
 
-int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw,
-             const float* pose_override = nullptr) {
+}  // namespace
+
+// ------------------------------------------------------------------ argument records
+namespace gmcs {
+
+void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw,
+               const float* pose_override, PassArgs* pa_out, FinishArgs* fa_out) {
     int nt, groups, chunk;
     pass_shape(c->P, N, &nt, &groups, &chunk);
     PassArgs pa;
@@ -231,12 +196,6 @@ int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out
     pa.groups = groups;
     pa.chunk_len = chunk;
     pa.eps = c->cfg.eps;
-    {
-        Launch L(c, grad ? K_PASS_GRAD : K_PASS_VALUE);
-        launch_pass(pa, c->cfg.table_dtype, grad, c->stream);
-    }
-    int rc = check_launch();
-    if (rc) return rc;
     FinishArgs fa;
     fa.part = c->part;
     fa.pose = c->pose[c->cur];
@@ -261,14 +220,11 @@ int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out
     fa.k_nb = std::min(c->cfg.k_nb, c->K);
     fa.propagate = c->cfg.propagate;
     fa.loop_recent = c->cfg.loop_recent;
-    {
-        Launch L(c, K_FINISH);
-        launch_finish(fa, grad, c->stream);
-    }
-    return check_launch();
+    *pa_out = pa;
+    *fa_out = fa;
 }
 
-int run_select(gmcs_ctx* c, int* nbr_out_dev) {
+SelectArgs select_args(gmcs_ctx* c, int* nbr_out) {
     SelectArgs sa;
     sa.pose = c->pose[c->cur];
     sa.kf = c->kf[c->cur];
@@ -277,7 +233,100 @@ int run_select(gmcs_ctx* c, int* nbr_out_dev) {
     sa.K = c->K;
     sa.k_nb = std::min(c->cfg.k_nb, std::max(c->K, 1));
     sa.nbr = c->nbr;
-    sa.nbr_out = nbr_out_dev;
+    sa.nbr_out = nbr_out;
+    return sa;
+}
+
+PredictArgs predict_args(gmcs_ctx* c, const double dT[12], const double cov[36], const float* z, uint32_t frame) {
+    PredictArgs a;
+    a.pose = c->pose[c->cur];
+    a.ld = c->ld;
+    a.P = c->P;
+    for (int e = 0; e < 12; ++e) a.dT[e] = (float)dT[e];
+    for (int e = 0; e < 36; ++e) a.cov[e] = (float)cov[e];
+    a.z = z;
+    a.seed = c->cfg.seed;
+    a.frame = frame;
+    return a;
+}
+
+WeighArgs weigh_args(gmcs_ctx* c, const float* ll, WeighResult* res) {
+    WeighArgs a;
+    a.logw = c->logw;
+    a.ll = ll;
+    a.P = c->P;
+    a.policy = c->cfg.resample;
+    a.part = c->wpart;
+    a.counter = c->counter;
+    a.res = res;
+    a.pose = c->pose[c->cur];
+    a.ld = c->ld;
+    return a;
+}
+
+void resample_args(gmcs_ctx* c, int P, const double* w, const WeighResult* res, double* w_out, double u,
+                   int u_from_philox, uint32_t frame, int* anc, ScanArgs* sa, TotalsArgs* ta, SearchArgs* se) {
+    const int nb = (P + kScanBlock - 1) / kScanBlock;
+    sa->logw = c->logw;
+    sa->w = w;
+    sa->res = res;
+    sa->w_out = w_out;
+    sa->P = P;
+    sa->cl = c->cl;
+    sa->btot = c->btot;
+    ta->btot = c->btot;
+    ta->nblocks = nb;
+    se->cl = c->cl;
+    se->boff = c->btot;
+    se->nblocks = nb;
+    se->P = P;
+    se->u = u;
+    se->u_from_philox = u_from_philox;
+    se->seed = c->cfg.seed;
+    se->frame = frame;
+    se->res = res;
+    se->anc = anc;
+}
+
+GatherArgs gather_args(gmcs_ctx* c, const WeighResult* res) {
+    GatherArgs g;
+    g.pose_src = c->pose[c->cur];
+    g.pose_dst = c->pose[1 - c->cur];
+    g.kf_src = c->kf[c->cur];
+    g.kf_dst = c->kf[1 - c->cur];
+    g.ld = c->ld;
+    g.P = c->P;
+    g.K = c->K;
+    g.anc = c->anc;
+    g.logw = c->logw;
+    g.res = res;
+    return g;
+}
+
+}  // namespace gmcs
+
+namespace {
+
+int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw,
+             const float* pose_override = nullptr) {
+    PassArgs pa;
+    FinishArgs fa;
+    pass_args(c, N, grad, move, out_ll, out_g, out_mom, logw, pose_override, &pa, &fa);
+    {
+        Launch L(c, grad ? K_PASS_GRAD : K_PASS_VALUE);
+        launch_pass(pa, c->cfg.table_dtype, grad, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    {
+        Launch L(c, K_FINISH);
+        launch_finish(fa, grad, c->stream);
+    }
+    return check_launch();
+}
+
+int run_select(gmcs_ctx* c, int* nbr_out_dev) {
+    const SelectArgs sa = select_args(c, nbr_out_dev);
     {
         Launch L(c, K_SELECT);
         launch_select(sa, c->stream);
@@ -290,15 +339,7 @@ int run_predict(gmcs_ctx* c, const double dT[12], const double cov[36], const fl
         if (!std::isfinite(dT[e])) return GMCS_E_INVALID;
     for (int e = 0; e < 36; ++e)
         if (!std::isfinite(cov[e])) return GMCS_E_INVALID;
-    PredictArgs a;
-    a.pose = c->pose[c->cur];
-    a.ld = c->ld;
-    a.P = c->P;
-    for (int e = 0; e < 12; ++e) a.dT[e] = (float)dT[e];
-    for (int e = 0; e < 36; ++e) a.cov[e] = (float)cov[e];
-    a.z = z_dev;
-    a.seed = c->cfg.seed;
-    a.frame = frame;
+    const PredictArgs a = predict_args(c, dT, cov, z_dev, frame);
     {
         Launch L(c, K_PREDICT);
         launch_predict(a, c->stream);
@@ -307,16 +348,7 @@ int run_predict(gmcs_ctx* c, const double dT[12], const double cov[36], const fl
 }
 
 int run_weigh(gmcs_ctx* c, const float* ll_dev) {
-    WeighArgs a;
-    a.logw = c->logw;
-    a.ll = ll_dev;
-    a.P = c->P;
-    a.policy = c->cfg.resample;
-    a.part = c->wpart;
-    a.counter = c->counter;
-    a.res = c->d_res;
-    a.pose = c->pose[c->cur];
-    a.ld = c->ld;
+    const WeighArgs a = weigh_args(c, ll_dev, c->d_res);
     {
         Launch L(c, K_WEIGH);
         launch_weigh(a, weigh_blocks(c->P), c->stream);
@@ -324,18 +356,13 @@ int run_weigh(gmcs_ctx* c, const float* ll_dev) {
     return check_launch();
 }
 
-// Quantise, scan, search (ancestors into c->anc). w_dev: given weights or null.
+// Quantise, scan, search (ancestors into anc_dev). w_dev: given weights or null.
 int run_resample_core(gmcs_ctx* c, int P, const double* w_dev, const WeighResult* res, double* w_out,
                       double u, int u_from_philox, uint32_t frame, int* anc_dev) {
-    const int nb = (P + kScanBlock - 1) / kScanBlock;
     ScanArgs sa;
-    sa.logw = c->logw;
-    sa.w = w_dev;
-    sa.res = res;
-    sa.w_out = w_out;
-    sa.P = P;
-    sa.cl = c->cl;
-    sa.btot = c->btot;
+    TotalsArgs ta;
+    SearchArgs se;
+    resample_args(c, P, w_dev, res, w_out, u, u_from_philox, frame, anc_dev, &sa, &ta, &se);
     {
         Launch L(c, K_RESAMPLE);
         launch_resample_scan(sa, c->stream);
@@ -344,21 +371,10 @@ int run_resample_core(gmcs_ctx* c, int P, const double* w_dev, const WeighResult
     if (rc) return rc;
     {
         Launch L(c, K_RESAMPLE);
-        launch_scan_totals(c->btot, nb, c->stream);
+        launch_scan_totals(ta.btot, ta.nblocks, c->stream);
     }
     rc = check_launch();
     if (rc) return rc;
-    SearchArgs se;
-    se.cl = c->cl;
-    se.boff = c->btot;
-    se.nblocks = nb;
-    se.P = P;
-    se.u = u;
-    se.u_from_philox = u_from_philox;
-    se.seed = c->cfg.seed;
-    se.frame = frame;
-    se.res = res;
-    se.anc = anc_dev;
     {
         Launch L(c, K_RESAMPLE);
         launch_resample_search(se, c->stream);
@@ -367,17 +383,7 @@ int run_resample_core(gmcs_ctx* c, int P, const double* w_dev, const WeighResult
 }
 
 int run_gather(gmcs_ctx* c, const WeighResult* res) {
-    GatherArgs g;
-    g.pose_src = c->pose[c->cur];
-    g.pose_dst = c->pose[1 - c->cur];
-    g.kf_src = c->kf[c->cur];
-    g.kf_dst = c->kf[1 - c->cur];
-    g.ld = c->ld;
-    g.P = c->P;
-    g.K = c->K;
-    g.anc = c->anc;
-    g.logw = c->logw;
-    g.res = res;
+    const GatherArgs g = gather_args(c, res);
     {
         Launch L(c, K_GATHER);
         launch_gather(g, c->stream);
@@ -386,6 +392,10 @@ int run_gather(gmcs_ctx* c, const WeighResult* res) {
     if (rc == GMCS_OK) c->cur = 1 - c->cur;
     return rc;
 }
+
+}  // namespace
+
+namespace gmcs {
 
 void fill_out(const WeighResult& r, uint32_t frame, gmcs_step_out* o) {
     for (int e = 0; e < 12; ++e) o->estimate[e] = r.est[e];
@@ -397,6 +407,10 @@ void fill_out(const WeighResult& r, uint32_t frame, gmcs_step_out* o) {
     o->frame = frame;
     o->status = r.nonfinite ? GMCS_E_NONFINITE : GMCS_OK;
 }
+
+}  // namespace gmcs
+
+namespace {
 
 // Copy n bytes from device src to dst (host or device); host destinations synchronise.
 int copy_out(gmcs_ctx* c, void* dst, const void* src, size_t n) {
@@ -437,6 +451,8 @@ const char* gmcs_strerror(int code) {
         case GMCS_E_CAPACITY: return "capacity exceeded";
         case GMCS_E_STATE: return "call out of order";
         case GMCS_E_NONFINITE: return "weights degenerated (reset to uniform)";
+        case GMCS_E_BUDGET: return "session does not fit the serving budget";
+        case GMCS_PENDING: return "pending";
         default: return "unknown error";
     }
 }

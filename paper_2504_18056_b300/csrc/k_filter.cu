@@ -26,10 +26,12 @@ namespace gmcs {
 
 // ------------------------------------------------------------------ layout helpers
 
-__global__ void k_scan_pack(const float* __restrict__ xyz, int n, float4* __restrict__ out) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        out[j] = make_float4(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], 0.f);
+__device__ __forceinline__ void scan_pack_body(const ScanPackArgs& a, int vb, int vg) {
+    for (int j = vb * blockDim.x + threadIdx.x; j < a.n; j += vg * blockDim.x)
+        a.out[j] = make_float4(a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], 0.f);
 }
+
+__global__ void k_scan_pack(ScanPackArgs a) { scan_pack_body(a, blockIdx.x, gridDim.x); }
 
 __global__ void k_aos_to_soa(const float* __restrict__ aos, int P, int C, float* __restrict__ soa, size_t ld) {
     const size_t n = (size_t)P * C;
@@ -74,11 +76,11 @@ __device__ __forceinline__ void chol6_psd(const float* A, float* L) {
     }
 }
 
-__global__ void __launch_bounds__(128) k_predict(PredictArgs a) {
+__device__ __forceinline__ void predict_body(const PredictArgs& a, int vb, int vg) {
     __shared__ float sL[36];
     if (threadIdx.x == 0) chol6_psd(a.cov, sL);
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = vb * blockDim.x + threadIdx.x;
     if (i >= a.P) return;
     float z[6];
     if (a.z) {
@@ -103,12 +105,14 @@ __global__ void __launch_bounds__(128) k_predict(PredictArgs a) {
     store_pose(a.pose, a.ld, i, out);
 }
 
+__global__ void __launch_bounds__(128) k_predict(PredictArgs a) { predict_body(a, blockIdx.x, gridDim.x); }
+
 // ------------------------------------------------------------------ neighbour keyframes
 
 // The k_nb smallest squared translation distances, formed as (dx*dx + dy*dy) + dz*dz
 // with separate round-to-nearest operations; ties keep the lower keyframe index.
-__global__ void __launch_bounds__(128) k_select(SelectArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void select_body(const SelectArgs& a, int vb, int vg) {
+    const int i = vb * blockDim.x + threadIdx.x;
     if (i >= a.P) return;
     const float tx = a.pose[3 * a.ld + i], ty = a.pose[7 * a.ld + i], tz = a.pose[11 * a.ld + i];
     float bd[kMaxNb];
@@ -143,6 +147,8 @@ __global__ void __launch_bounds__(128) k_select(SelectArgs a) {
         }
     }
 }
+
+__global__ void __launch_bounds__(128) k_select(SelectArgs a) { select_body(a, blockIdx.x, gridDim.x); }
 
 // ------------------------------------------------------------------ the lookup pass
 
@@ -301,12 +307,12 @@ struct WarpWork {
     int i, j0, j1, tg, cg;
 };
 
-__device__ __forceinline__ WarpWork warp_work(const PassArgs& a) {
+__device__ __forceinline__ WarpWork warp_work(const PassArgs& a, int vb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ntg = (a.ntiles + kPassTW - 1) / kPassTW;
     WarpWork w;
-    w.tg = blockIdx.x % ntg;
-    w.cg = blockIdx.x / ntg;
+    w.tg = vb % ntg;
+    w.cg = vb / ntg;
     const int tile = w.tg * kPassTW + warp % kPassTW;
     const int chunk = w.cg * kPassCW + warp / kPassTW;
     w.i = tile * 32 + lane;
@@ -345,7 +351,7 @@ __device__ __forceinline__ void store_partials(const PassArgs& a, const float* a
 template <int DT, bool GRAD>
 __global__ void __launch_bounds__(kPassThreads, GMCS_PASS_MINBLOCKS) k_pass(PassArgs a) {
     constexpr int NACC = GRAD ? kAccGrad : 1;
-    const WarpWork ww = warp_work(a);
+    const WarpWork ww = warp_work(a, blockIdx.x);
     const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
 
     float acc[NACC];
@@ -390,9 +396,9 @@ __global__ void __launch_bounds__(kPassThreads, GMCS_PASS_MINBLOCKS) k_pass(Pass
 // moments are accumulated once for all three lookups, which are independent
 // and keep three cell loads in flight.
 template <int DT, bool GRAD, int UNROLL>
-__global__ void __launch_bounds__(kPassThreads, GMCS_PASS3_MINBLOCKS) k_pass3(PassArgs a) {
+__device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
     constexpr int NACC = GRAD ? kAccGrad : 1;
-    const WarpWork ww = warp_work(a);
+    const WarpWork ww = warp_work(a, vb);
     const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
 
     float acc[NACC];
@@ -450,12 +456,20 @@ __global__ void __launch_bounds__(kPassThreads, GMCS_PASS3_MINBLOCKS) k_pass3(Pa
     store_partials<NACC>(a, acc, ww);
 }
 
+template <int DT, bool GRAD, int UNROLL>
+__global__ void __launch_bounds__(kPassThreads, GMCS_PASS3_MINBLOCKS) k_pass3(PassArgs a) {
+    pass3_body<DT, GRAD, UNROLL>(a, blockIdx.x);
+}
+
 // ------------------------------------------------------------------ finish: sums, move (Eq. 5-7)
 
-__device__ __forceinline__ void finish_sum(const FinishArgs& a, int i, int nacc, float* acc) {
-    for (int e = 0; e < nacc; ++e) acc[e] = 0.f;
+template <int NACC>
+__device__ __forceinline__ void finish_sum(const FinishArgs& a, int i, float* acc) {
+#pragma unroll
+    for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
     for (int g = 0; g < a.groups; ++g)
-        for (int e = 0; e < nacc; ++e) acc[e] += a.part[((size_t)g * nacc + e) * a.ld + i];
+#pragma unroll
+        for (int e = 0; e < NACC; ++e) acc[e] += a.part[((size_t)g * NACC + e) * a.ld + i];
 }
 
 // psi = (H + lambda diag H)^-1 g with H = sigma^-2 [[tr Q I - Q, [S]x], [[S]x^T, W I]],
@@ -535,12 +549,12 @@ __device__ bool gn_step(const float* g, const float* mom, const FinishArgs& a, f
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(128) k_finish(FinishArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void finish_body(const FinishArgs& a, int vb, int vg) {
+    const int i = vb * blockDim.x + threadIdx.x;
     if (i >= a.P) return;
     constexpr int NACC = GRAD ? kAccGrad : 1;
     float acc[NACC];
-    finish_sum(a, i, NACC, acc);
+    finish_sum<NACC>(a, i, acc);
     if (a.out_ll) a.out_ll[i] = acc[0];
     if (!GRAD) {
         if (a.logw) a.logw[i] += (double)acc[0];
@@ -588,6 +602,11 @@ __global__ void __launch_bounds__(128) k_finish(FinishArgs a) {
     }
 }
 
+template <bool GRAD>
+__global__ void __launch_bounds__(128) k_finish(FinishArgs a) {
+    finish_body<GRAD>(a, blockIdx.x, gridDim.x);
+}
+
 // ------------------------------------------------------------------ differentiable log-likelihood
 
 // dst_i = T0_i exp(xi_i)  (xi: P x 6, row-major)
@@ -626,6 +645,64 @@ __global__ void __launch_bounds__(128) k_chain(const float* __restrict__ xi, con
     }
 }
 
+// ------------------------------------------------------------------ batched launches
+
+// Walk the virtual blocks of every session in a BatchList; the trailing barrier
+// keeps a CTA's shared memory from being reused by the next virtual block while
+// slower threads still read it.
+#define GMCS_BATCH_LOOP(L, CALL)                                               \
+    for (int item = blockIdx.x; item < (L)->total; item += gridDim.x) {        \
+        int s = 0;                                                             \
+        while (s + 1 < (L)->count && (L)->offset[s + 1] <= item) ++s;          \
+        const int vb = item - (L)->offset[s], vg = (L)->vgrid[s];              \
+        (void)vg;                                                              \
+        CALL;                                                                  \
+        __syncthreads();                                                       \
+    }
+
+__global__ void __launch_bounds__(256) k_scan_pack_b(const BatchList<ScanPackArgs>* L) {
+    GMCS_BATCH_LOOP(L, scan_pack_body(L->args[s], vb, vg));
+}
+
+__global__ void __launch_bounds__(128) k_predict_b(const BatchList<PredictArgs>* L) {
+    GMCS_BATCH_LOOP(L, predict_body(L->args[s], vb, vg));
+}
+
+__global__ void __launch_bounds__(128) k_select_b(const BatchList<SelectArgs>* L) {
+    GMCS_BATCH_LOOP(L, select_body(L->args[s], vb, vg));
+}
+
+template <int DT, bool GRAD, int UNROLL>
+__global__ void __launch_bounds__(kPassThreads, GMCS_PASS3_MINBLOCKS) k_pass3_b(const BatchList<PassArgs>* L) {
+    GMCS_BATCH_LOOP(L, (pass3_body<DT, GRAD, UNROLL>(L->args[s], vb)));
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(128) k_finish_b(const BatchList<FinishArgs>* L) {
+    GMCS_BATCH_LOOP(L, finish_body<GRAD>(L->args[s], vb, vg));
+}
+
+void launch_scan_pack_b(const BatchList<ScanPackArgs>* L, cudaStream_t s) { k_scan_pack_b<<<148 * 4, 256, 0, s>>>(L); }
+void launch_predict_b(const BatchList<PredictArgs>* L, cudaStream_t s) { k_predict_b<<<148 * 8, 128, 0, s>>>(L); }
+void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s) { k_select_b<<<148 * 8, 128, 0, s>>>(L); }
+
+void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStream_t s) {
+    // persistent grid: the CTAs that fit at once (about 3 per SM for the gradient pass)
+    const int grid = 148 * (grad ? 3 : 4);
+#define GMCS_PASS_B(DT, G) k_pass3_b<DT, G, pass3_unroll<DT, G>()><<<grid, kPassThreads, 0, s>>>(L)
+    if (grad) {
+        if (dtype == 0) GMCS_PASS_B(0, true); else if (dtype == 1) GMCS_PASS_B(1, true); else GMCS_PASS_B(2, true);
+    } else {
+        if (dtype == 0) GMCS_PASS_B(0, false); else if (dtype == 1) GMCS_PASS_B(1, false); else GMCS_PASS_B(2, false);
+    }
+#undef GMCS_PASS_B
+}
+
+void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, cudaStream_t s) {
+    if (grad) k_finish_b<true><<<148 * 8, 128, 0, s>>>(L);
+    else k_finish_b<false><<<148 * 8, 128, 0, s>>>(L);
+}
+
 // ------------------------------------------------------------------ launchers
 
 void launch_perturb(const float* pose0, const float* xi, int P, size_t ld, float* dst, cudaStream_t s) {
@@ -642,8 +719,12 @@ static int blocks_for(size_t n, int threads, int cap = 148 * 16) {
     return (int)(b > 0 ? b : 1);
 }
 
+int grid_scan_pack(int n) { return blocks_for(n, 256); }
+int grid_per_particle(int P) { return (P + 127) / 128; }
+int grid_pass(const PassArgs& a) { return (a.ntiles + kPassTW - 1) / kPassTW * a.groups; }
+
 void launch_scan_pack(const float* xyz, int n, float4* out, cudaStream_t s) {
-    if (n > 0) k_scan_pack<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, out);
+    if (n > 0) k_scan_pack<<<grid_scan_pack(n), 256, 0, s>>>(ScanPackArgs{xyz, n, out});
 }
 
 void launch_aos_to_soa(const float* aos, int P, int C, float* soa, size_t ld, cudaStream_t s) {
@@ -663,7 +744,7 @@ void launch_select(const SelectArgs& a, cudaStream_t s) {
 }
 
 void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s) {
-    const int grid = (a.ntiles + kPassTW - 1) / kPassTW * a.groups;
+    const int grid = grid_pass(a);
     if (grid <= 0) return;
     // three neighbours (every particle then has all three slots filled): the fused kernel
     const bool three = GMCS_PASS3 && a.k_nb == 3;

@@ -69,9 +69,9 @@ constexpr int kWeighThreads = 256;
 
 }  // namespace
 
-__global__ void __launch_bounds__(kWeighThreads) k_weigh(WeighArgs a) {
+__device__ __forceinline__ void weigh_body(const WeighArgs& a, int vb, int vg) {
     Lse acc{-INFINITY, 0.0, 0.0, 0x7fffffff};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.P; i += gridDim.x * blockDim.x) {
+    for (int i = vb * blockDim.x + threadIdx.x; i < a.P; i += vg * blockDim.x) {
         double v = a.logw[i];
         if (a.ll) {
             v += (double)a.ll[i];
@@ -84,17 +84,17 @@ __global__ void __launch_bounds__(kWeighThreads) k_weigh(WeighArgs a) {
     acc = lse_block(acc);
     __shared__ int is_last;
     if (threadIdx.x == 0) {
-        double* p = a.part + 4 * (size_t)blockIdx.x;
+        double* p = a.part + 4 * (size_t)vb;
         p[0] = acc.m; p[1] = acc.s; p[2] = acc.s2; p[3] = (double)acc.im;
         __threadfence();
         const unsigned ticket = atomicAdd(a.counter, 1u);
-        is_last = (ticket == gridDim.x - 1);
+        is_last = (ticket == (unsigned)vg - 1);
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     Lse tot{-INFINITY, 0.0, 0.0, 0x7fffffff};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < vg; b += blockDim.x) {
         const double* p = a.part + 4 * (size_t)b;
         const Lse one{__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), (int)__ldcg(p + 3)};
         tot = lse_combine(tot, one);
@@ -117,10 +117,12 @@ __global__ void __launch_bounds__(kWeighThreads) k_weigh(WeighArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(kWeighThreads) k_weigh(WeighArgs a) { weigh_body(a, blockIdx.x, gridDim.x); }
+
 // q_i = rint(w_i 2^52) and the block-local inclusive prefix sums.
-__global__ void __launch_bounds__(kScanBlock) k_resample_scan(ScanArgs a) {
+__device__ __forceinline__ void resample_scan_body(const ScanArgs& a, int vb, int vg) {
     __shared__ unsigned long long wsum[32];
-    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    const int i = vb * kScanBlock + threadIdx.x;
     double w = 0.0;
     if (i < a.P) {
         if (a.w) {
@@ -152,11 +154,15 @@ __global__ void __launch_bounds__(kScanBlock) k_resample_scan(ScanArgs a) {
     __syncthreads();
     if (warp > 0) q += wsum[warp - 1];
     if (i < a.P) a.cl[i] = q;
-    if (threadIdx.x == kScanBlock - 1) a.btot[blockIdx.x] = q;
+    if (threadIdx.x == kScanBlock - 1) a.btot[vb] = q;
 }
 
+__global__ void __launch_bounds__(kScanBlock) k_resample_scan(ScanArgs a) { resample_scan_body(a, blockIdx.x, gridDim.x); }
+
 // Exclusive scan of the block totals in place; the grand total goes to btot[nblocks].
-__global__ void __launch_bounds__(1024) k_scan_totals(unsigned long long* btot, int nblocks) {
+__device__ __forceinline__ void scan_totals_body(const TotalsArgs& t, int vb, int vg) {
+    unsigned long long* btot = t.btot;
+    const int nblocks = t.nblocks;
     __shared__ unsigned long long wsum[32];
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0ull;
@@ -193,6 +199,8 @@ __global__ void __launch_bounds__(1024) k_scan_totals(unsigned long long* btot, 
     if (threadIdx.x == 0) btot[nblocks] = carry;
 }
 
+__global__ void __launch_bounds__(1024) k_scan_totals(TotalsArgs t) { scan_totals_body(t, blockIdx.x, gridDim.x); }
+
 __device__ __forceinline__ double systematic_u(uint64_t seed, uint32_t t) {
     const uint4 o = philox4x32_10(make_uint4(0xFFFFFFFFu, t, 0u, kTagResample),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
@@ -200,8 +208,8 @@ __device__ __forceinline__ double systematic_u(uint64_t seed, uint32_t t) {
     return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 1.0 / 9007199254740992.0);
 }
 
-__global__ void __launch_bounds__(256) k_resample_search(SearchArgs a) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void resample_search_body(const SearchArgs& a, int vb, int vg) {
+    const int m = vb * blockDim.x + threadIdx.x;
     if (m >= a.P) return;
     if (a.res && !a.res->do_resample) {
         a.anc[m] = m;
@@ -225,11 +233,13 @@ __global__ void __launch_bounds__(256) k_resample_search(SearchArgs a) {
     a.anc[m] = ((double)(base + a.cl[l]) > tau) ? l : a.P - 1;
 }
 
+__global__ void __launch_bounds__(256) k_resample_search(SearchArgs a) { resample_search_body(a, blockIdx.x, gridDim.x); }
+
 // State gather by ancestor: current pose and every keyframe pose, then log-weights.
-__global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
+__device__ __forceinline__ void gather_body(const GatherArgs& a, int vb, int vg) {
     const size_t per = (size_t)(1 + a.K) * kPoseC;
     const size_t n = per * a.P;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = vb * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)vg * blockDim.x) {
         const size_t row = e / a.P;
         const int m = (int)(e % a.P);
         const int src = a.anc[m];
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
         }
     }
     const double uni = -log((double)a.P);
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < a.P; m += gridDim.x * blockDim.x) {
+    for (int m = vb * blockDim.x + threadIdx.x; m < a.P; m += vg * blockDim.x) {
         if (!a.res) {
             a.logw[m] = uni;
         } else {
@@ -250,6 +260,8 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
         }
     }
 }
+
+__global__ void __launch_bounds__(256) k_gather(GatherArgs a) { gather_body(a, blockIdx.x, gridDim.x); }
 
 // No resampling: normalise the log-weights in place (w_out: weights, anc: identity).
 __global__ void __launch_bounds__(256) k_normalize(double* logw, int P, const WeighResult* res, double* w_out,
@@ -263,6 +275,54 @@ __global__ void __launch_bounds__(256) k_normalize(double* logw, int P, const We
     }
 }
 
+// ------------------------------------------------------------------ batched launches
+
+#define GMCS_BATCH_LOOP(L, CALL)                                               \
+    for (int item = blockIdx.x; item < (L)->total; item += gridDim.x) {        \
+        int s = 0;                                                             \
+        while (s + 1 < (L)->count && (L)->offset[s + 1] <= item) ++s;          \
+        const int vb = item - (L)->offset[s], vg = (L)->vgrid[s];              \
+        CALL;                                                                  \
+        __syncthreads();                                                       \
+    }
+
+__global__ void __launch_bounds__(kWeighThreads) k_weigh_b(const BatchList<WeighArgs>* L) {
+    GMCS_BATCH_LOOP(L, weigh_body(L->args[s], vb, vg));
+}
+__global__ void __launch_bounds__(kScanBlock) k_resample_scan_b(const BatchList<ScanArgs>* L) {
+    GMCS_BATCH_LOOP(L, resample_scan_body(L->args[s], vb, vg));
+}
+__global__ void __launch_bounds__(1024) k_scan_totals_b(const BatchList<TotalsArgs>* L) {
+    GMCS_BATCH_LOOP(L, scan_totals_body(L->args[s], vb, vg));
+}
+__global__ void __launch_bounds__(256) k_resample_search_b(const BatchList<SearchArgs>* L) {
+    GMCS_BATCH_LOOP(L, resample_search_body(L->args[s], vb, vg));
+}
+__global__ void __launch_bounds__(256) k_gather_b(const BatchList<GatherArgs>* L) {
+    GMCS_BATCH_LOOP(L, gather_body(L->args[s], vb, vg));
+}
+
+void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s) { k_weigh_b<<<148 * 4, kWeighThreads, 0, s>>>(L); }
+void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s) {
+    k_resample_scan_b<<<148 * 2, kScanBlock, 0, s>>>(L);
+}
+void launch_scan_totals_b(const BatchList<TotalsArgs>* L, cudaStream_t s) {
+    k_scan_totals_b<<<kMaxSlots, 1024, 0, s>>>(L);
+}
+void launch_resample_search_b(const BatchList<SearchArgs>* L, cudaStream_t s) {
+    k_resample_search_b<<<148 * 8, 256, 0, s>>>(L);
+}
+void launch_gather_b(const BatchList<GatherArgs>* L, cudaStream_t s) { k_gather_b<<<148 * 8, 256, 0, s>>>(L); }
+
+int grid_resample_scan(int P) { return (P + kScanBlock - 1) / kScanBlock; }
+int grid_resample_search(int P) { return (P + 255) / 256; }
+int grid_gather(const GatherArgs& a) {
+    const size_t n = (size_t)(1 + a.K) * kPoseC * a.P;
+    size_t b = (n + 255) / 256;
+    if (b > 148 * 16) b = 148 * 16;
+    return (int)(b > 0 ? b : 1);
+}
+
 int weigh_blocks(int P) {
     int b = (P + kWeighThreads * 4 - 1) / (kWeighThreads * 4);
     if (b > 148 * 4) b = 148 * 4;
@@ -274,23 +334,20 @@ void launch_weigh(const WeighArgs& a, int nblocks, cudaStream_t s) {
 }
 
 void launch_resample_scan(const ScanArgs& a, cudaStream_t s) {
-    const int nb = (a.P + kScanBlock - 1) / kScanBlock;
+    const int nb = grid_resample_scan(a.P);
     if (nb > 0) k_resample_scan<<<nb, kScanBlock, 0, s>>>(a);
 }
 
 void launch_scan_totals(unsigned long long* btot, int nblocks, cudaStream_t s) {
-    k_scan_totals<<<1, 1024, 0, s>>>(btot, nblocks);
+    k_scan_totals<<<1, 1024, 0, s>>>(TotalsArgs{btot, nblocks});
 }
 
 void launch_resample_search(const SearchArgs& a, cudaStream_t s) {
-    if (a.P > 0) k_resample_search<<<(a.P + 255) / 256, 256, 0, s>>>(a);
+    if (a.P > 0) k_resample_search<<<grid_resample_search(a.P), 256, 0, s>>>(a);
 }
 
 void launch_gather(const GatherArgs& a, cudaStream_t s) {
-    const size_t n = (size_t)(1 + a.K) * kPoseC * a.P;
-    size_t b = (n + 255) / 256;
-    if (b > 148 * 16) b = 148 * 16;
-    if (a.P > 0) k_gather<<<(int)b, 256, 0, s>>>(a);
+    if (a.P > 0) k_gather<<<grid_gather(a), 256, 0, s>>>(a);
 }
 
 void launch_normalize(double* logw, int P, const WeighResult* res, double* w_out, int* anc, cudaStream_t s) {

@@ -46,6 +46,12 @@ void launch_pack(const PackArgs& a, cudaStream_t s);
 void launch_unpack(const void* cells, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s);
 
 // ------------------------------------------------------------------ filter
+struct ScanPackArgs {
+    const float* xyz;       // n x 3
+    int n;
+    float4* out;
+};
+
 struct PredictArgs {
     float* pose;            // [12][ld], in/out
     size_t ld;
@@ -145,6 +151,11 @@ struct ScanArgs {
     unsigned long long* btot;   // per-block totals -> exclusive offsets
 };
 
+struct TotalsArgs {
+    unsigned long long* btot;   // block totals -> exclusive offsets, grand total at [nblocks]
+    int nblocks;
+};
+
 struct SearchArgs {
     const unsigned long long* cl;
     const unsigned long long* boff;   // exclusive block offsets, then total at [nblocks]
@@ -179,5 +190,40 @@ void launch_scan_totals(unsigned long long* btot, int nblocks, cudaStream_t s);
 void launch_resample_search(const SearchArgs& a, cudaStream_t s);
 void launch_gather(const GatherArgs& a, cudaStream_t s);
 void launch_normalize(double* logw, int P, const WeighResult* res, double* w_out, int* anc, cudaStream_t s);
+
+// ------------------------------------------------------------------ batched (serving) launches
+// One launch covers the work of up to kMaxSlots sessions: session s owns the
+// virtual blocks [offset[s], offset[s] + vgrid[s]) of a persistent grid that
+// walks them in order; each virtual block runs the same body as the
+// single-session kernel with blockIdx / gridDim replaced by (vb, vgrid[s]).
+constexpr int kMaxSlots = 32;
+
+template <typename A>
+struct BatchList {
+    int count;                 // sessions in this launch
+    int total;                 // sum of vgrid
+    int vgrid[kMaxSlots];
+    int offset[kMaxSlots];     // exclusive prefix of vgrid
+    A args[kMaxSlots];
+};
+
+void launch_scan_pack_b(const BatchList<ScanPackArgs>* L, cudaStream_t s);
+void launch_predict_b(const BatchList<PredictArgs>* L, cudaStream_t s);
+void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s);
+void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStream_t s);
+void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, cudaStream_t s);
+void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s);
+void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s);
+void launch_scan_totals_b(const BatchList<TotalsArgs>* L, cudaStream_t s);
+void launch_resample_search_b(const BatchList<SearchArgs>* L, cudaStream_t s);
+void launch_gather_b(const BatchList<GatherArgs>* L, cudaStream_t s);
+
+// Virtual grid sizes of the single-session launches (the batched launches use the same).
+int grid_scan_pack(int n);
+int grid_per_particle(int P);          // 128-thread blocks
+int grid_pass(const PassArgs& a);
+int grid_resample_scan(int P);
+int grid_resample_search(int P);
+int grid_gather(const GatherArgs& a);
 
 }  // namespace gmcs
