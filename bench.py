@@ -56,6 +56,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
+    ap.add_argument("--serve", action="store_true", help="serving benchmark (32 sessions, continuous batching)")
+    ap.add_argument("--sessions", type=int, default=32)
+    ap.add_argument("--session-frames", type=int, default=20)
+    ap.add_argument("--budget-gb", type=float, default=80.0)
+    ap.add_argument("--serve-range", type=float, default=20.0, help="lidar range of the serving scenes (m)")
+    ap.add_argument("--serve-pool", type=int, default=60, help="distinct keyframe clouds shared by the sessions")
+    ap.add_argument("--serve-rate", type=float, default=10.0, help="frames per second per session")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-at-a-time plain FP32 comparison")
     return ap.parse_args()
 
 
@@ -340,6 +348,180 @@ def run_native(a, world, rank, local):
     return line
 
 
+# ----------------------------------------------------------------------------- serving arm
+def _setup_session(f, pool, spec, dev):
+    """Particles from the host; keyframe clouds and per-particle keyframe poses
+    from device buffers (no host round trip per keyframe)."""
+    import torch
+    f.init_particles(synth_session_particles(pool, spec))
+    npool = len(pool["keyframes"])
+    kf_buf = torch.empty((spec["P"], 12), dtype=torch.float32, device="cuda")
+    for k in range(spec["K"]):
+        kf = pool["keyframes"][k % npool]
+        kf_buf.copy_(dev["kf_pose"][k % npool].expand(spec["P"], 12))
+        torch.cuda.current_stream().synchronize()
+        f.add_keyframe(dev["points"][k % npool], kf["grid"], kf_buf)
+
+
+def synth_session_particles(pool, spec):
+    import synth
+    return synth.session_particles(pool, spec)
+
+
+def _saturate(srv, sat_sids, a, pool, frame_idx):
+    for i in range(a.session_frames):
+        for sid, spec in sat_sids:
+            fi = frame_idx(spec, i)
+            srv.submit(sid, pool["scans"][fi][:spec["N"]], pool["odometry"][fi], pool["cov"])
+    srv.drain()
+    return srv.stats()
+
+
+def run_serve(a):
+    """Config 5: sessions with P ~ U[4096, 200000], N ~ U[1024, 8192], K ~ U[10, 300],
+    Poisson frames at 10 Hz per session, admission by a device-memory budget;
+    BF16 tables through the server, against the plain FP32 path serving the same
+    sessions one at a time."""
+    import torch
+    import paper_2504_18056_b300 as g
+    import synth
+
+    torch.cuda.init()
+    t0 = time.perf_counter()
+    pool = synth.serving_pool(seed=0, n_kf=a.serve_pool, rmax=a.serve_range)
+    specs = synth.serving_sessions(seed=0, n_sessions=a.sessions, n_frames=a.session_frames)
+    t_gen = time.perf_counter() - t0
+    nscan = len(pool["scans"])
+    frame_idx = lambda spec, i: (spec["frame0"] + i) % nscan
+    dev = {"points": [torch.from_numpy(kf["points"]).cuda() for kf in pool["keyframes"]],
+           "kf_pose": [torch.from_numpy(kf["pose"].astype(np.float32)).cuda() for kf in pool["keyframes"]]}
+    if a.serve_rate != 10.0:
+        for sp in specs:
+            sp["arrivals"] = sp["arrivals"] * (10.0 / a.serve_rate)
+
+    srv = g.Server(budget_bytes=int(a.budget_gb * (1 << 30)), max_sessions=a.sessions, background=True,
+                   table_dtype=1)
+    waiting = list(range(len(specs)))
+    active = {}
+    e2e_lat = []
+    done_sessions = 0
+    setup_s = 0.0
+    t_start = time.perf_counter()
+    while done_sessions < len(specs):
+        # admission: open sessions while the budget allows
+        while waiting:
+            spec = specs[waiting[0]]
+            P, K, N = spec["P"], spec["K"], spec["N"]
+            tb = K * (pool["keyframes"][0]["grid"]["dims"][0] * pool["keyframes"][0]["grid"]["dims"][1] *
+                      pool["keyframes"][0]["grid"]["dims"][2]) * 16
+            sid = srv.open(P, K, N, table_bytes=tb, seed=spec["seed"])
+            if sid is None:
+                break
+            ts = time.perf_counter()
+            f = srv.session(sid)
+            _setup_session(f, pool, spec, dev)
+            srv.ready(sid)
+            setup_s += time.perf_counter() - ts
+            active[sid] = {"spec": spec, "t0": time.perf_counter(), "next": 0, "tickets": [], "done": 0, "late": []}
+            waiting.pop(0)
+        now = time.perf_counter()
+        for sid, st in list(active.items()):
+            spec = st["spec"]
+            while st["next"] < len(spec["arrivals"]) and st["t0"] + spec["arrivals"][st["next"]] <= now:
+                fi = frame_idx(spec, st["next"])
+                t_sched = st["t0"] + spec["arrivals"][st["next"]]
+                st["tickets"].append(srv.submit(sid, pool["scans"][fi][:spec["N"]], pool["odometry"][fi], pool["cov"]))
+                st["late"].append(time.perf_counter() - t_sched)   # the request loop's own delay
+                st["next"] += 1
+            while st["done"] < len(st["tickets"]):
+                r = srv.poll(st["tickets"][st["done"]])
+                if r is None:
+                    break
+                e2e_lat.append(st["late"][st["done"]] + r[1])
+                st["done"] += 1
+            if st["done"] == len(spec["arrivals"]):
+                srv.close_session(sid)
+                del active[sid]
+                done_sessions += 1
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t_start
+    stats = srv.stats()
+
+    # saturation: the sessions that fit the budget at once, every frame submitted together
+    srv.reset_stats()
+    sat_sids = []
+    for spec in specs:
+        tb = spec["K"] * int(np.prod(pool["keyframes"][0]["grid"]["dims"])) * 16
+        sid = srv.open(spec["P"], spec["K"], spec["N"], table_bytes=tb, seed=spec["seed"])
+        if sid is None:
+            break
+        _setup_session(srv.session(sid), pool, spec, dev)
+        srv.ready(sid)
+        sat_sids.append((sid, spec))
+    sat = {}
+    for inflight in (2, 1):
+        srv.set_inflight(inflight)
+        srv.reset_stats()
+        sat[inflight] = _saturate(srv, sat_sids, a, pool, frame_idx)
+    srv.set_inflight(2)
+    for sid, _ in sat_sids:
+        srv.close_session(sid)
+    srv.close()
+
+    # the plain FP32 path, one session at a time, same frames
+    plain_s = 0.0
+    plain_evals = 0.0
+    lat_plain = [0.0]
+    plain_by_session = []
+    for spec in ([] if a.no_plain else specs):
+        f = g.Filter(spec["P"], spec["K"], spec["N"], seed=spec["seed"])
+        _setup_session(f, pool, spec, dev)
+        torch.cuda.synchronize()
+        for i in range(len(spec["arrivals"])):
+            fi = frame_idx(spec, i)
+            ts = time.perf_counter()
+            f.step(pool["scans"][fi][:spec["N"]], pool["odometry"][fi], pool["cov"])
+            dt = time.perf_counter() - ts
+            plain_s += dt
+            lat_plain.append(dt)
+            plain_evals += spec["P"] * spec["N"] * 3
+            plain_by_session.append((spec, dt))
+        f.close()
+    served_rate = stats["evals"] / stats["span_s"] if stats["span_s"] > 0 else 0.0
+    sat_ids = {sp["seed"] for _, sp in sat_sids}
+    sat_plain = [(spec, t) for spec, t in plain_by_session if spec["seed"] in sat_ids]
+    sat_plain_rate = (sum(sp["P"] * sp["N"] * 3 for sp, _ in sat_plain) / sum(t for _, t in sat_plain)
+                      if sat_plain else None)
+    return {
+        "metric": "serving: aggregate particle×point lik+grad evals/s and p50/p99 frame latency",
+        "value": served_rate, "unit": "evals/s", "n_gpus": 1, "higher_is_better": True,
+        "config": {"workload": f"{len(specs)} sessions, P~U[4096,200000], N~U[1024,8192], K~U[10,300], "
+                               f"{a.session_frames} Poisson frames at {a.serve_rate:g} Hz each, {a.budget_gb:.0f} GB budget, "
+                               f"BF16 tables, scenes to {a.serve_range:.0f} m",
+                   "sessions": len(specs), "frames": stats["frames"]},
+        "latency_ms": {"p50": stats["latency_p50_s"] * 1e3, "p99": stats["latency_p99_s"] * 1e3,
+                       "max": stats["latency_max_s"] * 1e3, "mean": stats["latency_mean_s"] * 1e3,
+                       "measured": "submission to completion (server clock)"},
+        "latency_from_arrival_ms": {"p50": float(np.percentile(e2e_lat, 50)) * 1e3,
+                                    "p99": float(np.percentile(e2e_lat, 99)) * 1e3,
+                                    "measured": "scheduled Poisson arrival to completion"},
+        "mean_sessions_per_tick": stats["mean_sessions_per_tick"], "ticks": stats["ticks"],
+        "gpu_busy_s": stats["busy_s"], "evals_per_gpu_busy_s": stats["evals"] / stats["busy_s"] if stats["busy_s"] else None,
+        "saturated": {"sessions": len(sat_sids),
+                      "two_ticks_in_flight_evals_per_s": sat[2]["evals"] / sat[2]["span_s"] if sat[2]["span_s"] else None,
+                      "one_tick_in_flight_evals_per_s": sat[1]["evals"] / sat[1]["span_s"] if sat[1]["span_s"] else None,
+                      "mean_sessions_per_tick": [sat[2]["mean_sessions_per_tick"], sat[1]["mean_sessions_per_tick"]],
+                      "plain_fp32_same_sessions_evals_per_s": sat_plain_rate},
+
+        "wall_s": wall, "session_setup_s": setup_s, "generation_s": t_gen,
+        "plain_fp32_one_at_a_time": {"evals_per_s": plain_evals / plain_s if plain_s else None,
+                                     "frame_ms_p50": float(np.percentile(lat_plain, 50)) * 1e3,
+                                     "frame_ms_p99": float(np.percentile(lat_plain, 99)) * 1e3, "busy_s": plain_s},
+        "offered_evals_per_s": float(np.mean([s["P"] * s["N"] * 3 for s in specs]) * a.serve_rate * len(specs)),
+        "rate_hz_per_session": a.serve_rate,
+    }
+
+
 # ----------------------------------------------------------------------------- reference arm (the oracle)
 def run_reference(a, world, rank):
     """The FP64 oracle as the reference implementation, on the host cores: each
@@ -373,6 +555,8 @@ def main():
     world, rank, local = dist_env()
     if a.impl == "reference":
         line = run_reference(a, world, rank)
+    elif a.serve:
+        line = run_serve(a) if rank == 0 else None
     else:
         line = run_native(a, world, rank, local)
     if rank == 0 and line is not None:

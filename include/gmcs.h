@@ -334,6 +334,7 @@ typedef struct {
     uint64_t used_bytes, budget_bytes;
     double evals;                 /* particle x point likelihood+gradient evaluations (P * N * steps) */
     double span_s;                /* first submission to last completion */
+    double busy_s;                /* time with at least one tick on the GPU (graph start to end) */
     double mean_sessions_per_tick;
     double latency_p50_s, latency_p99_s, latency_max_s, latency_mean_s;   /* submission to completion */
 } gmcs_server_stats;
@@ -348,6 +349,9 @@ int gmcs_server_destroy(gmcs_server* srv);
 int gmcs_server_start(gmcs_server* srv);
 int gmcs_server_stop(gmcs_server* srv);
 int gmcs_server_pump(gmcs_server* srv);
+/* Ticks allowed on the GPU at once: 2 (default; a tick starts while another runs)
+ * or 1 (one after another). */
+int gmcs_server_set_inflight(gmcs_server* srv, int ticks);
 /* Admission: open a session if its context (capacities) plus table_bytes fit the
  * remaining budget, else GMCS_E_BUDGET (retry after another session closes).
  * Then fill it through its context (gmcs_server_context: gmcs_init_particles,

@@ -62,7 +62,7 @@ class Stats(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("frames", C.c_uint64), ("ticks", C.c_uint64), ("sessions", C.c_int), ("pad", C.c_int),
                 ("used_bytes", C.c_uint64), ("budget_bytes", C.c_uint64), ("evals", C.c_double), ("span_s", C.c_double),
-                ("mean_sessions_per_tick", C.c_double), ("latency_p50_s", C.c_double), ("latency_p99_s", C.c_double),
+                ("busy_s", C.c_double), ("mean_sessions_per_tick", C.c_double), ("latency_p50_s", C.c_double), ("latency_p99_s", C.c_double),
                 ("latency_max_s", C.c_double), ("latency_mean_s", C.c_double)]
 
     def as_dict(self):
@@ -107,6 +107,7 @@ _SIGS = {
     "gmcs_server_start": (C.c_int, [C.c_void_p]),
     "gmcs_server_stop": (C.c_int, [C.c_void_p]),
     "gmcs_server_pump": (C.c_int, [C.c_void_p]),
+    "gmcs_server_set_inflight": (C.c_int, [C.c_void_p, C.c_int]),
     "gmcs_server_open": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_int)]),
     "gmcs_server_context": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "gmcs_server_ready": (C.c_int, [C.c_void_p, C.c_int]),
@@ -402,6 +403,9 @@ class Server:
 
     def pump(self):
         _check(lib().gmcs_server_pump(self.srv), "gmcs_server_pump")
+
+    def set_inflight(self, ticks):
+        _check(lib().gmcs_server_set_inflight(self.srv, int(ticks)), "gmcs_server_set_inflight")
 
     def drain(self):
         _check(lib().gmcs_server_drain(self.srv), "gmcs_server_drain")

@@ -661,46 +661,105 @@ __global__ void __launch_bounds__(128) k_chain(const float* __restrict__ xi, con
     }
 
 __global__ void __launch_bounds__(256) k_scan_pack_b(const BatchList<ScanPackArgs>* L) {
-    GMCS_BATCH_LOOP(L, scan_pack_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const ScanPackArgs a = L->args[s]; scan_pack_body(a, vb, vg));
 }
 
 __global__ void __launch_bounds__(128) k_predict_b(const BatchList<PredictArgs>* L) {
-    GMCS_BATCH_LOOP(L, predict_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const PredictArgs a = L->args[s]; predict_body(a, vb, vg));
 }
 
 __global__ void __launch_bounds__(128) k_select_b(const BatchList<SelectArgs>* L) {
-    GMCS_BATCH_LOOP(L, select_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const SelectArgs a = L->args[s]; select_body(a, vb, vg));
 }
 
 template <int DT, bool GRAD, int UNROLL>
-__global__ void __launch_bounds__(kPassThreads, GMCS_PASS3_MINBLOCKS) k_pass3_b(const BatchList<PassArgs>* L) {
-    GMCS_BATCH_LOOP(L, (pass3_body<DT, GRAD, UNROLL>(L->args[s], vb)));
+__global__ void __launch_bounds__(kPassThreads, 3) k_pass3_b(const BatchList<PassArgs>* L) {
+    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_body<DT, GRAD, UNROLL>(a, vb)));
 }
 
 template <bool GRAD>
 __global__ void __launch_bounds__(128) k_finish_b(const BatchList<FinishArgs>* L) {
-    GMCS_BATCH_LOOP(L, finish_body<GRAD>(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const FinishArgs a = L->args[s]; finish_body<GRAD>(a, vb, vg));
 }
 
-void launch_scan_pack_b(const BatchList<ScanPackArgs>* L, cudaStream_t s) { k_scan_pack_b<<<148 * 4, 256, 0, s>>>(L); }
-void launch_predict_b(const BatchList<PredictArgs>* L, cudaStream_t s) { k_predict_b<<<148 * 8, 128, 0, s>>>(L); }
-void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s) { k_select_b<<<148 * 8, 128, 0, s>>>(L); }
+// Persistent grids: every SM filled with as many CTAs as can be resident
+// (from the occupancy API, computed once per kernel before any graph capture).
+template <typename K>
+static int persistent_grid(K kernel, int threads) {
+    int per_sm = 0, dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * sms;
+}
+
+static int grid_scan_pack_b() {
+    static const int g = persistent_grid(k_scan_pack_b, 256);
+    return g;
+}
+static int grid_predict_b() {
+    static const int g = persistent_grid(k_predict_b, 128);
+    return g;
+}
+static int grid_select_b() {
+    static const int g = persistent_grid(k_select_b, 128);
+    return g;
+}
+template <int DT, bool G>
+static int grid_pass3_b() {
+    static const int g = persistent_grid(k_pass3_b<DT, G, pass3_unroll<DT, G>()>, kPassThreads);
+    return g;
+}
+template <bool G>
+static int grid_finish_b() {
+    static const int g = persistent_grid(k_finish_b<G>, 128);
+    return g;
+}
+
+void launch_scan_pack_b(const BatchList<ScanPackArgs>* L, cudaStream_t s) {
+    k_scan_pack_b<<<grid_scan_pack_b(), 256, 0, s>>>(L);
+}
+void launch_predict_b(const BatchList<PredictArgs>* L, cudaStream_t s) {
+    k_predict_b<<<grid_predict_b(), 128, 0, s>>>(L);
+}
+void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s) {
+    k_select_b<<<grid_select_b(), 128, 0, s>>>(L);
+}
+
+template <int DT, bool G>
+static void pass3_b(const BatchList<PassArgs>* L, cudaStream_t s) {
+    k_pass3_b<DT, G, pass3_unroll<DT, G>()><<<grid_pass3_b<DT, G>(), kPassThreads, 0, s>>>(L);
+}
 
 void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStream_t s) {
-    // persistent grid: the CTAs that fit at once (about 3 per SM for the gradient pass)
-    const int grid = 148 * (grad ? 3 : 4);
-#define GMCS_PASS_B(DT, G) k_pass3_b<DT, G, pass3_unroll<DT, G>()><<<grid, kPassThreads, 0, s>>>(L)
     if (grad) {
-        if (dtype == 0) GMCS_PASS_B(0, true); else if (dtype == 1) GMCS_PASS_B(1, true); else GMCS_PASS_B(2, true);
+        if (dtype == 0) pass3_b<0, true>(L, s); else if (dtype == 1) pass3_b<1, true>(L, s); else pass3_b<2, true>(L, s);
     } else {
-        if (dtype == 0) GMCS_PASS_B(0, false); else if (dtype == 1) GMCS_PASS_B(1, false); else GMCS_PASS_B(2, false);
+        if (dtype == 0) pass3_b<0, false>(L, s); else if (dtype == 1) pass3_b<1, false>(L, s); else pass3_b<2, false>(L, s);
     }
-#undef GMCS_PASS_B
 }
 
 void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, cudaStream_t s) {
-    if (grad) k_finish_b<true><<<148 * 8, 128, 0, s>>>(L);
-    else k_finish_b<false><<<148 * 8, 128, 0, s>>>(L);
+    if (grad) k_finish_b<true><<<grid_finish_b<true>(), 128, 0, s>>>(L);
+    else k_finish_b<false><<<grid_finish_b<false>(), 128, 0, s>>>(L);
+}
+
+void prepare_filter_batched() {
+    // evaluate every persistent grid size outside of any stream capture (no launch)
+    grid_scan_pack_b();
+    grid_predict_b();
+    grid_select_b();
+    grid_pass3_b<0, true>();
+    grid_pass3_b<1, true>();
+    grid_pass3_b<2, true>();
+    grid_pass3_b<0, false>();
+    grid_pass3_b<1, false>();
+    grid_pass3_b<2, false>();
+    grid_finish_b<true>();
+    grid_finish_b<false>();
 }
 
 // ------------------------------------------------------------------ launchers

@@ -287,32 +287,56 @@ __global__ void __launch_bounds__(256) k_normalize(double* logw, int P, const We
     }
 
 __global__ void __launch_bounds__(kWeighThreads) k_weigh_b(const BatchList<WeighArgs>* L) {
-    GMCS_BATCH_LOOP(L, weigh_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const WeighArgs a = L->args[s]; weigh_body(a, vb, vg));
 }
 __global__ void __launch_bounds__(kScanBlock) k_resample_scan_b(const BatchList<ScanArgs>* L) {
-    GMCS_BATCH_LOOP(L, resample_scan_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const ScanArgs a = L->args[s]; resample_scan_body(a, vb, vg));
 }
 __global__ void __launch_bounds__(1024) k_scan_totals_b(const BatchList<TotalsArgs>* L) {
-    GMCS_BATCH_LOOP(L, scan_totals_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const TotalsArgs a = L->args[s]; scan_totals_body(a, vb, vg));
 }
 __global__ void __launch_bounds__(256) k_resample_search_b(const BatchList<SearchArgs>* L) {
-    GMCS_BATCH_LOOP(L, resample_search_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const SearchArgs a = L->args[s]; resample_search_body(a, vb, vg));
 }
 __global__ void __launch_bounds__(256) k_gather_b(const BatchList<GatherArgs>* L) {
-    GMCS_BATCH_LOOP(L, gather_body(L->args[s], vb, vg));
+    GMCS_BATCH_LOOP(L, const GatherArgs a = L->args[s]; gather_body(a, vb, vg));
 }
 
-void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s) { k_weigh_b<<<148 * 4, kWeighThreads, 0, s>>>(L); }
+template <typename K>
+static int persistent_grid_w(K kernel, int threads) {
+    int per_sm = 0, dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * sms;
+}
+
+static int grid_weigh_b() { static const int g = persistent_grid_w(k_weigh_b, kWeighThreads); return g; }
+static int grid_scan_b() { static const int g = persistent_grid_w(k_resample_scan_b, kScanBlock); return g; }
+static int grid_search_b() { static const int g = persistent_grid_w(k_resample_search_b, 256); return g; }
+static int grid_gather_b() { static const int g = persistent_grid_w(k_gather_b, 256); return g; }
+
+void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s) { k_weigh_b<<<grid_weigh_b(), kWeighThreads, 0, s>>>(L); }
 void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s) {
-    k_resample_scan_b<<<148 * 2, kScanBlock, 0, s>>>(L);
+    k_resample_scan_b<<<grid_scan_b(), kScanBlock, 0, s>>>(L);
 }
 void launch_scan_totals_b(const BatchList<TotalsArgs>* L, cudaStream_t s) {
     k_scan_totals_b<<<kMaxSlots, 1024, 0, s>>>(L);
 }
 void launch_resample_search_b(const BatchList<SearchArgs>* L, cudaStream_t s) {
-    k_resample_search_b<<<148 * 8, 256, 0, s>>>(L);
+    k_resample_search_b<<<grid_search_b(), 256, 0, s>>>(L);
 }
-void launch_gather_b(const BatchList<GatherArgs>* L, cudaStream_t s) { k_gather_b<<<148 * 8, 256, 0, s>>>(L); }
+void launch_gather_b(const BatchList<GatherArgs>* L, cudaStream_t s) { k_gather_b<<<grid_gather_b(), 256, 0, s>>>(L); }
+
+void prepare_weights_batched() {
+    grid_weigh_b();
+    grid_scan_b();
+    grid_search_b();
+    grid_gather_b();
+}
 
 int grid_resample_scan(int P) { return (P + kScanBlock - 1) / kScanBlock; }
 int grid_resample_search(int P) { return (P + 255) / 256; }

@@ -217,6 +217,9 @@ void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s);
 void launch_scan_totals_b(const BatchList<TotalsArgs>* L, cudaStream_t s);
 void launch_resample_search_b(const BatchList<SearchArgs>* L, cudaStream_t s);
 void launch_gather_b(const BatchList<GatherArgs>* L, cudaStream_t s);
+// Size every persistent grid (occupancy queries) before a graph capture records the launches.
+void prepare_filter_batched();
+void prepare_weights_batched();
 
 // Virtual grid sizes of the single-session launches (the batched launches use the same).
 int grid_scan_pack(int n);

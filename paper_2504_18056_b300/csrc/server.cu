@@ -105,6 +105,7 @@ struct TickSet {
     bool busy = false;
     std::vector<Frame> frames;
     std::vector<double> evals;
+    std::atomic<double> t_start{0.0};
     std::atomic<double> t_done{0.0};
 };
 
@@ -114,6 +115,7 @@ struct Result {
     int status;
 };
 
+void CUDART_CB stamp_start(void* p) { static_cast<TickSet*>(p)->t_start.store(now_s()); }
 void CUDART_CB stamp_done(void* p) { static_cast<TickSet*>(p)->t_done.store(now_s()); }
 
 constexpr int kRingSlots = 64;
@@ -134,8 +136,10 @@ struct gmcs_server {
     std::map<uint64_t, Result> results;
     TickSet sets[2];
     std::vector<double> latencies;
+    std::vector<std::pair<double, double>> busy;   // [start, done] of every tick, host clock
     uint64_t frames_done = 0, ticks = 0, slots_used = 0;
     double evals = 0.0, t_first = 0.0, t_last = 0.0;
+    int max_inflight = 2;            // ticks on the GPU at once (1: strictly one after another)
     std::thread worker;
     std::atomic<bool> running{false};
 };
@@ -146,6 +150,7 @@ int capture_graph(gmcs_server* s, TickSet& t) {
     cudaStream_t st = t.stream;
     TickDesc* d = t.d_desc;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GMCS_E_CUDA;
+    cudaLaunchHostFunc(st, stamp_start, &t);
     cudaMemcpyAsync(d, t.h_desc, sizeof(TickDesc), cudaMemcpyHostToDevice, st);
     launch_scan_pack_b(&d->pack, st);
     launch_predict_b(&d->pred, st);
@@ -202,6 +207,7 @@ void collect(gmcs_server* s) {
         }
         s->frames_done += t.frames.size();
         s->t_last = std::max(s->t_last, t_done);
+        s->busy.emplace_back(t.t_start.load(), t_done);
         t.frames.clear();
         t.evals.clear();
         t.busy = false;
@@ -212,6 +218,9 @@ void collect(gmcs_server* s) {
 // (caller holds the lock). Returns the number of sessions in the tick.
 int launch_tick(gmcs_server* s) {
     TickSet* t = nullptr;
+    int busy = 0;
+    for (TickSet& c : s->sets) busy += c.busy ? 1 : 0;
+    if (busy >= s->max_inflight) return 0;
     for (TickSet& c : s->sets)
         if (!c.busy) { t = &c; break; }
     if (!t) return 0;
@@ -310,6 +319,8 @@ int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_se
     s->budget = budget_bytes;
     s->max_sessions = max_sessions;
     cudaGetDevice(&s->device);
+    prepare_filter_batched();
+    prepare_weights_batched();
     int rc = GMCS_OK;
     if (cudaStreamCreateWithFlags(&s->setup_stream, cudaStreamNonBlocking) != cudaSuccess) rc = GMCS_E_CUDA;
     for (TickSet& t : s->sets) {
@@ -335,6 +346,13 @@ int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_se
         return rc;
     }
     *out = s;
+    return GMCS_OK;
+}
+
+int gmcs_server_set_inflight(gmcs_server* s, int ticks) {
+    if (!s || ticks < 1 || ticks > 2) return GMCS_E_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->max_inflight = ticks;
     return GMCS_OK;
 }
 
@@ -534,6 +552,22 @@ int gmcs_server_get_stats(gmcs_server* s, gmcs_server_stats* out) {
     out->evals = s->evals;
     out->span_s = (s->t_last > s->t_first) ? s->t_last - s->t_first : 0.0;
     out->mean_sessions_per_tick = s->ticks ? (double)s->slots_used / s->ticks : 0.0;
+    {   // union of the tick intervals: time with at least one tick on the GPU
+        std::vector<std::pair<double, double>> b = s->busy;
+        std::sort(b.begin(), b.end());
+        double total = 0.0, cs = 0.0, ce = -1.0;
+        for (auto& iv : b) {
+            if (iv.first > ce) {
+                if (ce > cs) total += ce - cs;
+                cs = iv.first;
+                ce = iv.second;
+            } else {
+                ce = std::max(ce, iv.second);
+            }
+        }
+        if (ce > cs) total += ce - cs;
+        out->busy_s = total;
+    }
     if (!s->latencies.empty()) {
         std::vector<double> l = s->latencies;
         std::sort(l.begin(), l.end());
@@ -556,6 +590,7 @@ int gmcs_server_reset_stats(gmcs_server* s) {
     if (!s) return GMCS_E_INVALID;
     std::lock_guard<std::mutex> lock(s->mu);
     s->latencies.clear();
+    s->busy.clear();
     s->frames_done = s->ticks = s->slots_used = 0;
     s->evals = 0.0;
     s->t_first = s->t_last = 0.0;

@@ -397,3 +397,42 @@ def forest_workload(seed=0, n_particles=100_000, n_points=2048, n_keyframes=20,
     return {"scene": scene, "truth": frames, "keyframes": keyframes, "scans": scans,
             "odometry": odom, "cov": cov, "particles": particles.astype(np.float32),
             "kf_particle_poses": kf_particle_poses, "h": h, "sigma": 0.2}
+
+
+def serving_pool(seed=0, n_kf=300, kf_points=2048, n_scans=40, scan_points=8192, rmax=25.0, h=0.2, radius=6.0):
+    """Shared material for many serving sessions: n_kf keyframe clouds placed
+    around a loop in the corridor-and-trunk scene (ranges up to rmax), n_scans
+    scans of scan_points along the same loop, and their odometry."""
+    rng = np.random.default_rng(seed)
+    scene = corridor_forest(seed)
+    dirs = lidar_dirs(64, 1024, -22.5, 22.5)
+    kf_traj = loop_walk(seed + 1, n_kf, radius=radius, step=2.0 * np.pi * radius / n_kf)
+    keyframes = []
+    for k in range(n_kf):
+        pts = cast_scan(scene, kf_traj[k], dirs, rng, n_out=kf_points, rmax=rmax)
+        keyframes.append({"points": pts, "pose": kf_traj[k], "grid": grid_for_points(pts, h, 1.0)})
+    frames = loop_walk(seed + 2, n_scans + 1, radius=radius, step=0.4, phase0=0.05)
+    scans = [cast_scan(scene, frames[i], dirs, rng, n_out=scan_points, rmax=rmax) for i in range(1, n_scans + 1)]
+    return {"keyframes": keyframes, "truth": frames, "scans": scans, "odometry": _odometry(frames),
+            "cov": np.diag([np.deg2rad(0.3) ** 2] * 3 + [0.02 ** 2] * 3), "h": h}
+
+
+def serving_sessions(seed, n_sessions=32, p_range=(4096, 200_000), n_range=(1024, 8192), k_range=(10, 300),
+                     n_frames=20, rate_hz=10.0):
+    """Session specs: particle count, scan size and keyframe count drawn uniformly,
+    Poisson frame arrivals (offsets in seconds from admission)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n_sessions):
+        arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_frames))
+        out.append({"P": int(rng.integers(p_range[0], p_range[1] + 1)), "N": int(rng.integers(n_range[0], n_range[1] + 1)),
+                    "K": int(rng.integers(k_range[0], k_range[1] + 1)), "arrivals": arrivals, "seed": 1000 + s,
+                    "frame0": int(rng.integers(0, 8))})
+    return out
+
+
+def session_particles(pool, spec, init_trans=0.3, init_rot_deg=5.0):
+    """Initial particles of a serving session around its first frame's true pose."""
+    rng = np.random.default_rng(spec["seed"])
+    return perturb_poses(pool["truth"][spec["frame0"]], spec["P"], init_trans, np.deg2rad(init_rot_deg),
+                         rng).astype(np.float32)
