@@ -59,6 +59,7 @@ extern "C" {
 #define GMCS_RESAMPLE_ALWAYS 0
 #define GMCS_RESAMPLE_ESS_HALF 1
 #define GMCS_RESAMPLE_NEVER 2
+#define GMCS_RESAMPLE_PRUNE 3 /* dead-particle pruning (Sec. III-F): refill only the dead slots */
 
 #define GMCS_MAX_NB 8         /* upper bound on k_nb */
 
@@ -79,7 +80,11 @@ typedef struct {
     int loop_recent;   /* > 0: a particle moves only when its oldest neighbour keyframe is not
                           among the loop_recent newest keyframes (the loop condition of
                           Sec. III-C2); 0: every particle moves every frame */
-    int reserved;
+    float prune_w;     /* GMCS_RESAMPLE_PRUNE: a particle whose normalised weight is below
+                          prune_w is dead (the posterior criterion of Sec. III-F; 1e-8) */
+    float prune_lr;    /* GMCS_RESAMPLE_PRUNE: a particle whose frame likelihood is below
+                          prune_lr times the best particle's is dead (the likelihood criterion
+                          of Sec. III-F, relative to the frame's best; 1e-16); 0: off */
     uint64_t seed;     /* key of the Philox4x32-10 draws (motion noise, resampling offset) */
 } gmcs_config;
 
@@ -100,6 +105,8 @@ typedef struct {
     int resampled;        /* 1 if systematic resampling ran this frame */
     uint32_t frame;       /* frame counter used for this frame's draws */
     int status;           /* GMCS_OK or GMCS_E_NONFINITE */
+    int pruned;           /* GMCS_RESAMPLE_PRUNE: dead particles refilled this frame */
+    int reserved;
 } gmcs_step_out;
 
 typedef struct {
@@ -116,7 +123,7 @@ typedef struct gmcs_ctx gmcs_ctx;
 
 /* Defaults: sigma 0.2 m, r_t 1.0 m, eps 1e-3, lambda 1e-3, theta_max 2 deg,
  * t_max 0.1 m, w_min 1e-6, k_nb 3, steps 3, FP32 tables, resample always,
- * no propagation, no loop condition, seed 0. */
+ * no propagation, no loop condition, prune_w 1e-8, prune_lr 1e-16, seed 0. */
 void gmcs_config_default(gmcs_config* cfg);
 
 /*
@@ -167,7 +174,9 @@ int gmcs_add_keyframe(gmcs_ctx* ctx, const float* pts, int n, const gmcs_grid* g
  *   value pass at the moved poses, log-weight update (Eq. 11) with log-sum-exp
  *   normalisation in FP64, argmax estimate,
  *   systematic resampling per cfg.resample (FP64 offsets on 2^-52-quantised
- *   weights, exact integer prefix sums), and the gather of all particle state.
+ *   weights, exact integer prefix sums), and the gather of all particle state;
+ *   under GMCS_RESAMPLE_PRUNE instead only the dead slots are refilled in place
+ *   from the survivors (as gmcs_prune, with the value-pass log-likelihoods).
  * scan: N points (N x 3 floats, host or device) in the sensor frame.
  * delta_T: odometry increment (T^o_{t-1})^-1 T^o_t as 12 doubles (host).
  * cov: 6 x 6 motion covariance in the tangent space (36 doubles, host, row-major).
@@ -255,6 +264,27 @@ int gmcs_weigh(gmcs_ctx* ctx, const float* ll, double* w_out, gmcs_step_out* res
  * P may exceed max_particles only up to the context's scratch (same bound).
  */
 int gmcs_resample(gmcs_ctx* ctx, const double* w, int P, double u, int* anc);
+
+/*
+ * Dead-particle pruning (Sec. III-F) of arbitrary weights, on the kernels the
+ * step runs under GMCS_RESAMPLE_PRUNE; the context's particles are not touched.
+ *   x       P normalised log-weights (doubles)
+ *   w       P normalised weights, w = exp(x) as the caller computed it (doubles)
+ *   ll      P frame log-likelihoods (floats) for the likelihood criterion, or NULL
+ *   argmax  index of the largest weight: never pruned
+ *   u       systematic offset in [0, 1)
+ * Particle i != argmax is dead when w_i is not >= cfg.prune_w, or, with ll and
+ * cfg.prune_lr > 0, when ll_i - max_j ll_j is not >= log(prune_lr). With the
+ * survivors' weights quantised to q_i = rint(w_i 2^52) (q = 0 when dead),
+ * C_i = q_0 + ... + q_i and S = C_{P-1}, the r-th dead slot (index order,
+ * r = 0..D-1) takes ancestor a_r = min{ i : C_i > min(((u + r) / D) * S, S - 1) }.
+ * Outputs (host or device): anc (P ints: i for survivors, a_r for dead slots),
+ * logw (P doubles: x_a - log1p(c_a) for a survivor a with c_a copies and for
+ * each of its copies, x_i for survivors without copies), n_dead (host int, may
+ * be NULL) = D. All arrays may be host or device memory.
+ */
+int gmcs_prune(gmcs_ctx* ctx, const double* x, const double* w, const float* ll, int P, int argmax, double u,
+               int* anc, double* logw, int* n_dead);
 
 /*
  * The paper has no counterpart of this call: it is systematic resampling, with

@@ -39,16 +39,18 @@ class StepParams(C.Structure):
     _fields_ = [("sigma", C.c_double), ("eps", C.c_double), ("lambda_", C.c_double),
                 ("theta_max", C.c_double), ("t_max", C.c_double), ("w_min", C.c_double),
                 ("face_delta", C.c_double), ("k_nb", C.c_int), ("steps", C.c_int),
-                ("resample", C.c_int), ("propagate", C.c_int), ("loop_recent", C.c_int), ("seed", C.c_uint64)]
+                ("resample", C.c_int), ("propagate", C.c_int), ("loop_recent", C.c_int),
+                ("prune_w", C.c_double), ("ll_cut", C.c_double), ("seed", C.c_uint64)]
 
 
 class StepOut(C.Structure):
     _fields_ = [("estimate", C.c_double * 12), ("ess", C.c_double), ("max_w", C.c_double),
-                ("argmax", C.c_int), ("resampled", C.c_int)]
+                ("argmax", C.c_int), ("resampled", C.c_int), ("pruned", C.c_int), ("pad", C.c_int)]
 
 
 DEFAULTS = dict(sigma=0.2, eps=1e-3, lambda_=1e-3, theta_max=np.deg2rad(2.0), t_max=0.1,
-                w_min=1e-6, face_delta=1e-3, k_nb=3, steps=3, resample=0, propagate=0, loop_recent=0, seed=0)
+                w_min=1e-6, face_delta=1e-3, k_nb=3, steps=3, resample=0, propagate=0, loop_recent=0,
+                prune_w=1e-8, ll_cut=float(np.log(1e-16)), seed=0)
 
 
 def lib():
@@ -300,6 +302,20 @@ def resample(w, u):
     return anc
 
 
+def prune(x, w, ll, argmax, prune_w=1e-8, ll_cut=float(np.log(1e-16)), u=0.5):
+    """Dead-particle pruning (Sec. III-F): returns (anc, new log-weights, D)."""
+    x, px = _d(x); w, pw = _d(w)
+    pll = None
+    if ll is not None:
+        ll, pll = _d(ll)
+    P = x.shape[0]
+    anc = np.zeros(P, np.int32)
+    lo = np.zeros(P)
+    D = lib().ora_prune(px, pw, pll, C.c_int(P), C.c_int(argmax), C.c_double(prune_w), C.c_double(ll_cut),
+                        C.c_double(u), anc.ctypes.data_as(_ip), lo.ctypes.data_as(_dp))
+    return anc, lo, int(D)
+
+
 class State:
     """Particle set held by the oracle in FP64: poses (P, 12), keyframe poses
     (K, P, 12), log-weights (P,), plus the shared keyframe tables."""
@@ -319,7 +335,7 @@ class State:
         prm.update(params)
         sp = StepParams(prm["sigma"], prm["eps"], prm["lambda_"], prm["theta_max"], prm["t_max"], prm["w_min"],
                         prm["face_delta"], prm["k_nb"], prm["steps"], prm["resample"], prm["propagate"],
-                        prm["loop_recent"], prm["seed"])
+                        prm["loop_recent"], prm["prune_w"], prm["ll_cut"], prm["seed"])
         # odometry path length of this frame (Eq. 9 along the odometry trajectory)
         self.path_now += float(np.linalg.norm(np.asarray(dT, np.float64).reshape(12)[[3, 7, 11]]))
         kp = None if self.kf_path is None else self.kf_path.ctypes.data_as(_dp)
@@ -346,5 +362,5 @@ class State:
                        C.byref(out), ll.ctypes.data_as(_dp),
                        w.ctypes.data_as(_dp), anc.ctypes.data_as(_ip), nbr.ctypes.data_as(_ip))
         return {"estimate": np.array(list(out.estimate)), "ess": out.ess, "max_w": out.max_w,
-                "argmax": out.argmax, "resampled": bool(out.resampled), "ll": ll, "w": w, "anc": anc,
+                "argmax": out.argmax, "resampled": bool(out.resampled), "pruned": out.pruned, "ll": ll, "w": w, "anc": anc,
                 "nbr": nbr[:, :k_nb]}

@@ -657,6 +657,53 @@ void ora_resample(const double* w, int P, double u, int* anc) {
     free(C);
 }
 
+int ora_prune(const double* x, const double* w, const double* ll, int P, int argmax, double prune_w,
+              double ll_cut, double u, int* anc, double* logw_out) {
+    /* 1. the dead set */
+    double ll_max = -INFINITY;
+    if (ll)
+        for (int i = 0; i < P; ++i)
+            if (ll[i] > ll_max) ll_max = ll[i];
+    int* dead = (int*)malloc(sizeof(int) * (P > 0 ? P : 1));
+    int D = 0;
+    for (int i = 0; i < P; ++i) {
+        int d = !(w[i] >= prune_w);
+        if (ll && ll_cut > -INFINITY && !(ll[i] - ll_max >= ll_cut)) d = 1;
+        if (i == argmax) d = 0;
+        dead[i] = d;
+        D += d;
+    }
+    /* 2. cumulative quantised weights of the survivors */
+    uint64_t* C = (uint64_t*)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+    uint64_t run = 0;
+    for (int i = 0; i < P; ++i) {
+        if (!dead[i] && w[i] > 0.0 && w[i] <= 1.0) run += (uint64_t)nearbyint(w[i] * 4503599627370496.0);
+        C[i] = run;
+    }
+    double S = (double)run;
+    /* 3. one systematic comb of D teeth over the survivors */
+    int* copies = (int*)calloc(P > 0 ? P : 1, sizeof(int));
+    for (int i = 0; i < P; ++i) anc[i] = i;
+    int r = 0;
+    for (int i = 0; i < P && S > 0.0; ++i) {
+        if (!dead[i]) continue;
+        double tau = ((u + (double)r) / (double)D) * S;
+        if (tau > S - 1.0) tau = S - 1.0;
+        int a = 0;
+        while (!((double)C[a] > tau)) ++a;
+        anc[i] = a;
+        copies[a] += 1;
+        ++r;
+    }
+    /* 4. weights: each survivor's weight split evenly over it and its copies */
+    for (int i = 0; i < P; ++i) {
+        int a = anc[i];
+        logw_out[i] = copies[a] ? x[a] - log1p((double)copies[a]) : x[a];
+    }
+    free(dead); free(C); free(copies);
+    return D;
+}
+
 /* ------------------------------------------------------------------------ */
 /* whole frame                                                               */
 /* ------------------------------------------------------------------------ */
@@ -741,7 +788,25 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
     if (nbr_out) memcpy(nbr_out, nbr, sizeof(int) * (size_t)P * k_nb);
     int do_rs = (sp->resample == 0) || (sp->resample == 1 && ess < 0.5 * P);
     out->resampled = do_rs;
-    if (do_rs) {
+    out->pruned = 0;
+    if (sp->resample == 3) {
+        /* dead-particle pruning, Sec. III-F: refill dead slots from the survivors */
+        int* anc = (int*)malloc(sizeof(int) * P);
+        double* x = (double*)malloc(sizeof(double) * P);
+        for (int i = 0; i < P; ++i) x[i] = lw[i] - M - logS;
+        double uu = u ? *u : ora_systematic_u(sp->seed, frame);
+        out->pruned = ora_prune(x, w, ll, P, am, sp->prune_w, sp->ll_cut, uu, anc, logw);
+        for (int m = 0; m < P; ++m) {
+            if (anc[m] == m) continue;
+            memcpy(poses + 12 * (size_t)m, poses + 12 * (size_t)anc[m], 12 * sizeof(double));
+            for (int k = 0; k < K; ++k) {
+                double* base = kf_poses + (size_t)k * P * 12;
+                memcpy(base + 12 * (size_t)m, base + 12 * (size_t)anc[m], 12 * sizeof(double));
+            }
+        }
+        if (anc_out) memcpy(anc_out, anc, sizeof(int) * P);
+        free(anc); free(x);
+    } else if (do_rs) {
         int* anc = (int*)malloc(sizeof(int) * P);
         double uu = u ? *u : ora_systematic_u(sp->seed, frame);
         ora_resample(w, P, uu, anc);

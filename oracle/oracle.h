@@ -135,13 +135,32 @@ void ora_lse(const double* logw, const double* ll, int P, double* logw_out, doub
 /* ---- systematic resampling on weights quantised to the 2^-52 grid. */
 void ora_resample(const double* w, int P, double u, int* anc);
 
+/* ---- dead-particle pruning (Sec. III-F) as a resampling policy.
+ * Particle i (i != argmax, the largest weight, which always survives) is dead
+ * when its normalised weight is not >= prune_w (the posterior criterion; NaN is
+ * dead), or, when ll is given and ll_cut > -inf, when ll_i - max_j ll_j is not
+ * >= ll_cut (the likelihood criterion, relative to the frame's best particle;
+ * ll_cut = log of the likelihood ratio). The D dead slots, taken in index order
+ * r = 0..D-1, are refilled by systematic sampling over the survivors' weights
+ * quantised as q_i = rint(w_i 2^52) (q = 0 for dead slots), C_i = q_0+...+q_i,
+ * S = C_{P-1}:
+ *     tau_r = min(((u + r) / D) * S, S - 1),   a_r = min{ i : C_i > tau_r }.
+ * A survivor a drawn c_a times shares its weight with its copies: the survivor
+ * and each copy get x_a - log1p(c_a), x the normalised log-weights; survivors
+ * with no copy keep x. anc: i for survivors, a_r for the r-th dead slot.
+ * Returns D. */
+int ora_prune(const double* x, const double* w, const double* ll, int P, int argmax, double prune_w,
+              double ll_cut, double u, int* anc, double* logw_out);
+
 /* ---- whole frame over a particle set (the hot path, all steps in order). */
 typedef struct {
     double sigma, eps, lambda, theta_max, t_max, w_min, face_delta;
     int k_nb, steps;
-    int resample;        /* 0 always, 1 when ESS < P/2, 2 never */
+    int resample;        /* 0 always, 1 when ESS < P/2, 2 never, 3 prune dead particles */
     int propagate;       /* 1: keyframe pose propagation after every move (Eq. 8-10) */
     int loop_recent;     /* > 0: move only particles whose oldest neighbour is not among the newest loop_recent */
+    double prune_w;      /* resample 3: posterior threshold */
+    double ll_cut;       /* resample 3: log likelihood-ratio threshold (-inf: off) */
     uint64_t seed;
 } ora_step_params;
 
@@ -149,6 +168,7 @@ typedef struct {
     double estimate[12];
     double ess, max_w;
     int argmax, resampled;
+    int pruned, pad;
 } ora_step_out;
 
 /*

@@ -22,7 +22,7 @@ OK = 0
 E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE, E_BUDGET = -1, -2, -3, -4, -5, -6, -7
 PENDING = 1
 TABLE_F32, TABLE_BF16, TABLE_F16 = 0, 1, 2
-RESAMPLE_ALWAYS, RESAMPLE_ESS_HALF, RESAMPLE_NEVER = 0, 1, 2
+RESAMPLE_ALWAYS, RESAMPLE_ESS_HALF, RESAMPLE_NEVER, RESAMPLE_PRUNE = 0, 1, 2, 3
 MAX_NB = 8
 
 
@@ -36,7 +36,7 @@ class Config(C.Structure):
     _fields_ = [("sigma", C.c_float), ("r_t", C.c_float), ("eps", C.c_float), ("lambda_", C.c_float),
                 ("theta_max", C.c_float), ("t_max", C.c_float), ("w_min", C.c_float), ("k_nb", C.c_int),
                 ("steps", C.c_int), ("table_dtype", C.c_int), ("resample", C.c_int), ("propagate", C.c_int),
-                ("loop_recent", C.c_int), ("reserved", C.c_int), ("seed", C.c_uint64)]
+                ("loop_recent", C.c_int), ("prune_w", C.c_float), ("prune_lr", C.c_float), ("seed", C.c_uint64)]
 
 
 class Grid(C.Structure):
@@ -46,12 +46,12 @@ class Grid(C.Structure):
 class StepOut(C.Structure):
     _fields_ = [("estimate", C.c_double * 12), ("ess", C.c_double), ("max_w", C.c_double),
                 ("log_norm", C.c_double), ("argmax", C.c_int), ("resampled", C.c_int),
-                ("frame", C.c_uint32), ("status", C.c_int)]
+                ("frame", C.c_uint32), ("status", C.c_int), ("pruned", C.c_int), ("reserved", C.c_int)]
 
     def as_dict(self):
         return {"estimate": np.array(list(self.estimate)), "ess": self.ess, "max_w": self.max_w,
                 "log_norm": self.log_norm, "argmax": self.argmax, "resampled": bool(self.resampled),
-                "frame": self.frame, "status": self.status}
+                "frame": self.frame, "status": self.status, "pruned": self.pruned}
 
 
 class Stats(C.Structure):
@@ -90,6 +90,8 @@ _SIGS = {
     "gmcs_loglik_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "gmcs_weigh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(StepOut)]),
     "gmcs_resample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
+    "gmcs_prune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                             C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     "gmcs_get_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmcs_get_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_get_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -300,6 +302,13 @@ class Filter:
     def resample(self, w, u, anc):
         _check(lib().gmcs_resample(self.ctx, _ptr(w), int(w.shape[0]), float(u), _ptr(anc)), "gmcs_resample")
         return anc
+
+    def prune(self, x, w, ll, argmax, u, anc, logw):
+        """Dead-particle pruning of given weights (gmcs_prune); returns the dead count."""
+        d = C.c_int()
+        _check(lib().gmcs_prune(self.ctx, _ptr(x), _ptr(w), _ptr(ll), int(x.shape[0]), int(argmax), float(u),
+                                _ptr(anc), _ptr(logw), C.byref(d)), "gmcs_prune")
+        return d.value
 
     # --- readback
     def get_particles(self, poses=None, logw=None):

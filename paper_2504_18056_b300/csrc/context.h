@@ -53,6 +53,7 @@ struct gmcs_ctx {
     gmcs::WeighResult* h_res = nullptr;    // pinned
     unsigned long long* cl = nullptr;
     unsigned long long* btot = nullptr;
+    unsigned long long* dtot = nullptr;   // pruning: dead counts per scan block
     int* anc = nullptr;
     gmcs::TableDesc* d_tables = nullptr;
     std::vector<gmcs::HostTable> tables;
@@ -87,6 +88,8 @@ WeighArgs weigh_args(gmcs_ctx* c, const float* ll, WeighResult* res);
 void resample_args(gmcs_ctx* c, int P, const double* w, const WeighResult* res, double* w_out, double u,
                    int u_from_philox, uint32_t frame, int* anc, ScanArgs* sa, TotalsArgs* ta, SearchArgs* se);
 GatherArgs gather_args(gmcs_ctx* c, const WeighResult* res);
+PruneArgs prune_args(gmcs_ctx* c, int P, WeighResult* res, const double* w, const float* ll, double u,
+                     int u_from_philox, uint32_t frame, bool refill);
 void fill_out(const WeighResult& r, uint32_t frame, gmcs_step_out* o);
 void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len);
 

@@ -20,6 +20,10 @@
 
 using namespace gmcs;
 
+static_assert(sizeof(gmcs_config) == 72, "gmcs_config layout is part of the ABI");
+static_assert(sizeof(gmcs_step_out) == 144, "gmcs_step_out layout is part of the ABI");
+static_assert(sizeof(gmcs_grid) == 48, "gmcs_grid layout is part of the ABI");
+
 namespace {
 
 const char* kKindName[K_COUNT] = {"predict", "select", "pass_grad", "pass_value", "finish",
@@ -56,8 +60,8 @@ size_t ctx_device_bytes(int max_particles, int max_keyframes, int max_points) {
     b += 2 * (sizeof(float) * kPoseC * ld + sizeof(float) * kPoseC * ld * max_keyframes);
     b += sizeof(double) * ld * 2 + sizeof(float) * ld + sizeof(float) * 6 * ld;   // logw, w, ll, gbuf
     b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * max_points + sizeof(float) * stage;
-    b += sizeof(double) * 4 * 148 * 4 + sizeof(unsigned) + sizeof(WeighResult);
-    b += sizeof(unsigned long long) * (ld + nb + 1) + sizeof(int) * ld;
+    b += sizeof(double) * kWeighPart * 148 * 4 + sizeof(unsigned) + sizeof(WeighResult);
+    b += sizeof(unsigned long long) * (ld + 2 * (nb + 1)) + sizeof(int) * ld;
     b += sizeof(TableDesc) * max_keyframes + sizeof(float) * max_keyframes;
     return b;
 }
@@ -256,6 +260,7 @@ WeighArgs weigh_args(gmcs_ctx* c, const float* ll, WeighResult* res) {
     a.ll = ll;
     a.P = c->P;
     a.policy = c->cfg.resample;
+    a.llm = (c->cfg.resample == GMCS_RESAMPLE_PRUNE && c->cfg.prune_lr > 0.f) ? c->ll : nullptr;
     a.part = c->wpart;
     a.counter = c->counter;
     a.res = res;
@@ -286,6 +291,33 @@ void resample_args(gmcs_ctx* c, int P, const double* w, const WeighResult* res, 
     se->frame = frame;
     se->res = res;
     se->anc = anc;
+}
+
+PruneArgs prune_args(gmcs_ctx* c, int P, WeighResult* res, const double* w, const float* ll, double u,
+                     int u_from_philox, uint32_t frame, bool refill) {
+    PruneArgs a;
+    a.logw = c->logw;
+    a.w = w;
+    a.w_out = c->w;
+    a.ll = ll;
+    a.res = res;
+    a.pose = refill ? c->pose[c->cur] : nullptr;
+    a.kf = refill ? c->kf[c->cur] : nullptr;
+    a.ld = c->ld;
+    a.P = P;
+    a.K = c->K;
+    a.nblocks = (P + kScanBlock - 1) / kScanBlock;
+    a.cl = c->cl;
+    a.btot = c->btot;
+    a.dtot = c->dtot;
+    a.anc = c->anc;
+    a.prune_w = (double)c->cfg.prune_w;
+    a.ll_cut = c->cfg.prune_lr > 0.f ? std::log((double)c->cfg.prune_lr) : -INFINITY;
+    a.u = u;
+    a.u_from_philox = u_from_philox;
+    a.frame = frame;
+    a.seed = c->cfg.seed;
+    return a;
 }
 
 GatherArgs gather_args(gmcs_ctx* c, const WeighResult* res) {
@@ -382,6 +414,31 @@ int run_resample_core(gmcs_ctx* c, int P, const double* w_dev, const WeighResult
     return check_launch();
 }
 
+// Dead-particle pruning: mark + scans, totals, refill of dead slots, weight split.
+int run_prune(gmcs_ctx* c, const PruneArgs& a) {
+    {
+        Launch L(c, K_RESAMPLE);
+        launch_prune_mark(a, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    {
+        Launch L(c, K_RESAMPLE);
+        launch_prune_totals(a, c->stream);
+    }
+    if ((rc = check_launch())) return rc;
+    {
+        Launch L(c, K_GATHER);
+        launch_prune_spawn(a, c->stream);
+    }
+    if ((rc = check_launch())) return rc;
+    {
+        Launch L(c, K_RESAMPLE);
+        launch_prune_reweigh(a, c->stream);
+    }
+    return check_launch();
+}
+
 int run_gather(gmcs_ctx* c, const WeighResult* res) {
     const GatherArgs g = gather_args(c, res);
     {
@@ -406,6 +463,8 @@ void fill_out(const WeighResult& r, uint32_t frame, gmcs_step_out* o) {
     o->resampled = r.do_resample;
     o->frame = frame;
     o->status = r.nonfinite ? GMCS_E_NONFINITE : GMCS_OK;
+    o->pruned = r.pruned;
+    o->reserved = 0;
 }
 
 }  // namespace gmcs
@@ -439,6 +498,8 @@ void gmcs_config_default(gmcs_config* cfg) {
     cfg->steps = 3;
     cfg->table_dtype = GMCS_TABLE_F32;
     cfg->resample = GMCS_RESAMPLE_ALWAYS;
+    cfg->prune_w = 1e-8f;
+    cfg->prune_lr = 1e-16f;
     cfg->seed = 0;
 }
 
@@ -461,7 +522,8 @@ static bool config_ok(const gmcs_config* c) {
     return c && c->sigma > 0.f && c->r_t > 0.f && c->eps > 0.f && c->lambda >= 0.f && c->theta_max > 0.f &&
            (c->propagate == 0 || c->propagate == 1) && c->loop_recent >= 0 &&
            c->t_max > 0.f && c->w_min >= 0.f && c->k_nb >= 1 && c->k_nb <= GMCS_MAX_NB && c->steps >= 0 &&
-           c->steps <= 64 && c->table_dtype >= 0 && c->table_dtype <= 2 && c->resample >= 0 && c->resample <= 2;
+           c->steps <= 64 && c->table_dtype >= 0 && c->table_dtype <= 2 && c->resample >= 0 && c->resample <= 3 &&
+           c->prune_w >= 0.f && c->prune_w < 1.f && c->prune_lr >= 0.f && c->prune_lr < 1.f;
 }
 
 int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, int max_points, void* cuda_stream,
@@ -496,11 +558,12 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     if (!rc) rc = dalloc(c, &c->part, c->part_floats);
     if (!rc) rc = dalloc(c, &c->scan, (size_t)max_points);
     if (!rc) rc = dalloc(c, &c->stage, c->stage_floats);
-    if (!rc) rc = dalloc(c, &c->wpart, (size_t)4 * 148 * 4);
+    if (!rc) rc = dalloc(c, &c->wpart, (size_t)kWeighPart * 148 * 4);
     if (!rc) rc = dalloc(c, &c->counter, 1);
     if (!rc) rc = dalloc(c, &c->d_res, 1);
     if (!rc) rc = dalloc(c, &c->cl, ld);
     if (!rc) rc = dalloc(c, &c->btot, (size_t)nb + 1);
+    if (!rc) rc = dalloc(c, &c->dtot, (size_t)nb + 1);
     if (!rc) rc = dalloc(c, &c->anc, ld);
     if (!rc) rc = dalloc(c, &c->d_tables, (size_t)max_keyframes);
     if (!rc) rc = dalloc(c, &c->d_kf_path, (size_t)max_keyframes);
@@ -527,7 +590,7 @@ int gmcs_destroy(gmcs_ctx* c) {
     for (auto e : c->free_events) cudaEventDestroy(e);
     for (auto& t : c->tables) cudaFree(t.cells);
     void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->gbuf, c->ll, c->nbr, c->part, c->scan,
-                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->anc, c->d_tables, c->d2,
+                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->dtot, c->anc, c->d_tables, c->d2,
                     c->d_kf_path};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -732,6 +795,10 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
             launch_normalize(c->logw, c->P, c->d_res, c->w, c->anc, c->stream);
         }
         if ((rc = check_launch())) return rc;
+    } else if (c->cfg.resample == GMCS_RESAMPLE_PRUNE) {
+        const double u = u_override ? *u_override : 0.0;
+        const PruneArgs pa = prune_args(c, c->P, c->d_res, nullptr, c->ll, u, u_override ? 0 : 1, frame, true);
+        if ((rc = run_prune(c, pa))) return rc;
     } else {
         const double u = u_override ? *u_override : 0.0;
         if ((rc = run_resample_core(c, c->P, nullptr, c->d_res, c->w, u, u_override ? 0 : 1, frame, c->anc)))
@@ -942,6 +1009,46 @@ int gmcs_resample(gmcs_ctx* c, const double* w, int P, double u, int* anc) {
     int rc = run_resample_core(c, P, dw, nullptr, nullptr, u, 0, 0, dev ? anc : c->anc);
     if (rc) return rc;
     if (!dev) return copy_out(c, anc, c->anc, sizeof(int) * P);
+    return GMCS_OK;
+}
+
+int gmcs_prune(gmcs_ctx* c, const double* x, const double* w, const float* ll, int P, int argmax, double u,
+               int* anc, double* logw, int* n_dead) {
+    if (!c || !x || !w || !anc || !logw || P <= 0) return GMCS_E_INVALID;
+    if (P > c->Pmax) return GMCS_E_CAPACITY;
+    if (argmax < 0 || argmax >= P || !(u >= 0.0 && u < 1.0)) return GMCS_E_INVALID;
+    // inputs into scratch (the context's particles and diagnostics stay as they are):
+    // w and x as doubles in the partial-sum buffer, ll in the staging buffer
+    double* dw = reinterpret_cast<double*>(c->part);
+    double* dx = dw + c->ld;
+    float* dll = ll ? c->stage : nullptr;
+    CK(cudaMemcpyAsync(dx, x, sizeof(double) * P, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(dw, w, sizeof(double) * P, cudaMemcpyDefault, c->stream));
+    WeighResult* hr = c->h_res;
+    CK(cudaStreamSynchronize(c->stream));   // h_res may still be the target of an earlier copy
+    std::memset(hr, 0, sizeof(WeighResult));
+    hr->M = 0.0;                             // x is normalised: x - 0 - 0 = x exactly
+    hr->logS = 0.0;
+    hr->argmax = argmax;
+    hr->ll_max = -INFINITY;
+    if (ll) {
+        std::vector<float> h(P);
+        CK(cudaMemcpy(h.data(), ll, sizeof(float) * P, cudaMemcpyDefault));
+        CK(cudaMemcpyAsync(dll, ll, sizeof(float) * P, cudaMemcpyDefault, c->stream));
+        for (int i = 0; i < P; ++i)
+            if ((double)h[i] > hr->ll_max) hr->ll_max = (double)h[i];
+    }
+    CK(cudaMemcpyAsync(c->d_res, hr, sizeof(WeighResult), cudaMemcpyHostToDevice, c->stream));
+    PruneArgs pa = prune_args(c, P, c->d_res, dw, dll, u, 0, 0, false);
+    pa.logw = dx;
+    pa.w_out = nullptr;
+    int rc = run_prune(c, pa);
+    if (rc) return rc;
+    if ((rc = copy_out(c, anc, c->anc, sizeof(int) * P))) return rc;
+    if ((rc = copy_out(c, logw, dx, sizeof(double) * P))) return rc;
+    CK(cudaMemcpyAsync(hr, c->d_res, sizeof(WeighResult), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_dead) *n_dead = hr->pruned;
     return GMCS_OK;
 }
 

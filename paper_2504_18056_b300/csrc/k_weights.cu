@@ -24,6 +24,7 @@ namespace {
 
 struct Lse {
     double m, s, s2;
+    double lm;    // max frame log-likelihood (pruning's likelihood criterion)
     int im;
 };
 
@@ -31,6 +32,7 @@ __device__ __forceinline__ Lse lse_combine(Lse a, Lse b) {
     const bool b_first = (b.m > a.m) || (b.m == a.m && b.im < a.im);
     Lse hi = b_first ? b : a;
     const Lse lo = b_first ? a : b;
+    hi.lm = fmax(a.lm, b.lm);
     if (lo.m == -INFINITY) return hi;
     const double e = exp(lo.m - hi.m);
     hi.s += lo.s * e;
@@ -43,6 +45,7 @@ __device__ __forceinline__ Lse lse_shfl(Lse v, int off) {
     o.m = __shfl_down_sync(0xffffffffu, v.m, off);
     o.s = __shfl_down_sync(0xffffffffu, v.s, off);
     o.s2 = __shfl_down_sync(0xffffffffu, v.s2, off);
+    o.lm = __shfl_down_sync(0xffffffffu, v.lm, off);
     o.im = __shfl_down_sync(0xffffffffu, v.im, off);
     return o;
 }
@@ -57,7 +60,7 @@ __device__ Lse lse_block(Lse v) {
     __syncthreads();
     const int nw = (blockDim.x + 31) >> 5;
     if (warp == 0) {
-        v = (lane < nw) ? sh[lane] : Lse{-INFINITY, 0.0, 0.0, 0x7fffffff};
+        v = (lane < nw) ? sh[lane] : Lse{-INFINITY, 0.0, 0.0, -INFINITY, 0x7fffffff};
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v = lse_combine(v, lse_shfl(v, off));
     }
@@ -70,7 +73,7 @@ constexpr int kWeighThreads = 256;
 }  // namespace
 
 __device__ __forceinline__ void weigh_body(const WeighArgs& a, int vb, int vg) {
-    Lse acc{-INFINITY, 0.0, 0.0, 0x7fffffff};
+    Lse acc{-INFINITY, 0.0, 0.0, -INFINITY, 0x7fffffff};
     for (int i = vb * blockDim.x + threadIdx.x; i < a.P; i += vg * blockDim.x) {
         double v = a.logw[i];
         if (a.ll) {
@@ -78,14 +81,16 @@ __device__ __forceinline__ void weigh_body(const WeighArgs& a, int vb, int vg) {
             a.logw[i] = v;
         }
         if (isnan(v)) v = -INFINITY;
-        const Lse one{v, v == -INFINITY ? 0.0 : 1.0, v == -INFINITY ? 0.0 : 1.0, i};
+        double l = a.llm ? (double)a.llm[i] : -INFINITY;
+        if (isnan(l)) l = -INFINITY;
+        const Lse one{v, v == -INFINITY ? 0.0 : 1.0, v == -INFINITY ? 0.0 : 1.0, l, i};
         acc = lse_combine(acc, one);
     }
     acc = lse_block(acc);
     __shared__ int is_last;
     if (threadIdx.x == 0) {
-        double* p = a.part + 4 * (size_t)vb;
-        p[0] = acc.m; p[1] = acc.s; p[2] = acc.s2; p[3] = (double)acc.im;
+        double* p = a.part + kWeighPart * (size_t)vb;
+        p[0] = acc.m; p[1] = acc.s; p[2] = acc.s2; p[3] = (double)acc.im; p[4] = acc.lm;
         __threadfence();
         const unsigned ticket = atomicAdd(a.counter, 1u);
         is_last = (ticket == (unsigned)vg - 1);
@@ -93,10 +98,10 @@ __device__ __forceinline__ void weigh_body(const WeighArgs& a, int vb, int vg) {
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    Lse tot{-INFINITY, 0.0, 0.0, 0x7fffffff};
+    Lse tot{-INFINITY, 0.0, 0.0, -INFINITY, 0x7fffffff};
     for (int b = threadIdx.x; b < vg; b += blockDim.x) {
-        const double* p = a.part + 4 * (size_t)b;
-        const Lse one{__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), (int)__ldcg(p + 3)};
+        const double* p = a.part + kWeighPart * (size_t)b;
+        const Lse one{__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 4), (int)__ldcg(p + 3)};
         tot = lse_combine(tot, one);
     }
     tot = lse_block(tot);
@@ -108,7 +113,8 @@ __device__ __forceinline__ void weigh_body(const WeighArgs& a, int vb, int vg) {
         r.ess = r.nonfinite ? 0.0 : (tot.s * tot.s) / tot.s2;
         r.max_w = r.nonfinite ? 0.0 : 1.0 / tot.s;
         r.argmax = r.nonfinite ? 0 : tot.im;
-        r.pad = 0;
+        r.ll_max = tot.lm;
+        r.pruned = 0;
         int doit = (a.policy == 0) || (a.policy == 1 && r.ess < 0.5 * (double)a.P);
         r.do_resample = r.nonfinite ? 0 : doit;
         for (int c = 0; c < 12; ++c) r.est[c] = a.pose[(size_t)c * a.ld + r.argmax];
@@ -119,21 +125,9 @@ __device__ __forceinline__ void weigh_body(const WeighArgs& a, int vb, int vg) {
 
 __global__ void __launch_bounds__(kWeighThreads) k_weigh(WeighArgs a) { weigh_body(a, blockIdx.x, gridDim.x); }
 
-// q_i = rint(w_i 2^52) and the block-local inclusive prefix sums.
-__device__ __forceinline__ void resample_scan_body(const ScanArgs& a, int vb, int vg) {
+// Inclusive prefix sum over a kScanBlock-thread block (every thread calls it).
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long q) {
     __shared__ unsigned long long wsum[32];
-    const int i = vb * kScanBlock + threadIdx.x;
-    double w = 0.0;
-    if (i < a.P) {
-        if (a.w) {
-            w = a.w[i];
-        } else {
-            const WeighResult r = *a.res;
-            w = r.nonfinite ? 1.0 / (double)a.P : exp(a.logw[i] - r.M - r.logS);
-        }
-        if (a.w_out) a.w_out[i] = w;
-    }
-    unsigned long long q = (w > 0.0 && w <= 1.0) ? __double2ull_rn(w * 4503599627370496.0) : 0ull;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -153,6 +147,25 @@ __device__ __forceinline__ void resample_scan_body(const ScanArgs& a, int vb, in
     }
     __syncthreads();
     if (warp > 0) q += wsum[warp - 1];
+    __syncthreads();      // wsum is reused by the next call
+    return q;
+}
+
+// q_i = rint(w_i 2^52) and the block-local inclusive prefix sums.
+__device__ __forceinline__ void resample_scan_body(const ScanArgs& a, int vb, int vg) {
+    const int i = vb * kScanBlock + threadIdx.x;
+    double w = 0.0;
+    if (i < a.P) {
+        if (a.w) {
+            w = a.w[i];
+        } else {
+            const WeighResult r = *a.res;
+            w = r.nonfinite ? 1.0 / (double)a.P : exp(a.logw[i] - r.M - r.logS);
+        }
+        if (a.w_out) a.w_out[i] = w;
+    }
+    unsigned long long q = (w > 0.0 && w <= 1.0) ? __double2ull_rn(w * 4503599627370496.0) : 0ull;
+    q = block_scan_u64(q);
     if (i < a.P) a.cl[i] = q;
     if (threadIdx.x == kScanBlock - 1) a.btot[vb] = q;
 }
@@ -275,6 +288,146 @@ __global__ void __launch_bounds__(256) k_normalize(double* logw, int P, const We
     }
 }
 
+// ------------------------------------------------------------------ dead-particle pruning
+//
+// Sec. III-F: particles whose weight (or frame likelihood relative to the best
+// particle) has collapsed are dead; only their slots are refilled, by one
+// systematic comb of D teeth over the survivors' quantised weights, and each
+// survivor's weight is split evenly over it and its copies, so the weighted
+// particle measure of the survivors is unchanged. Survivors never move: the
+// refill reads survivors' state and writes dead slots' state in place.
+//   mark     dead flags, q_i (0 when dead), block scans of q and of the flags;
+//            anc[i] = i for survivors, -(local dead rank + 1) for dead slots
+//   totals   exclusive offsets of both block totals (CTA 0: q, CTA 1: dead)
+//   spawn    dead slot r: ancestor a_r, its copy count, new log-weight, state
+//   reweigh  survivors: x - log1p(copies)
+
+__device__ __forceinline__ double prune_tooth(double u, int r, int D, double S) {
+    const double t = __dmul_rn(__ddiv_rn(__dadd_rn(u, (double)r), (double)D), S);
+    return fmin(t, S - 1.0);
+}
+
+// Number of teeth r in [0, D) below X (the teeth are non-decreasing in r).
+__device__ __forceinline__ int prune_below(double u, int D, double S, double X) {
+    int lo = 0, hi = D;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (prune_tooth(u, mid, D, S) < X) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Teeth that land in survivor i's interval [C_{i-1}, C_i).
+__device__ __forceinline__ int prune_copies(const PruneArgs& a, int i, double u, int D, double S) {
+    const unsigned long long base = a.btot[i / kScanBlock];
+    const double hi = (double)(base + a.cl[i]);
+    const double lo = (double)((i % kScanBlock) ? base + a.cl[i - 1] : base);
+    if (!(hi > lo)) return 0;
+    return prune_below(u, D, S, hi) - prune_below(u, D, S, lo);
+}
+
+// min{ i : C_i > tau } for tau < S.
+__device__ __forceinline__ int prune_find(const PruneArgs& a, double tau) {
+    int lo = 0, hi = a.nblocks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((double)a.btot[mid + 1] > tau) hi = mid; else lo = mid + 1;
+    }
+    const unsigned long long base = a.btot[lo];
+    int l = lo * kScanBlock, h = min(a.P, (lo + 1) * kScanBlock) - 1;
+    while (l < h) {
+        const int mid = (l + h) >> 1;
+        if ((double)(base + a.cl[mid]) > tau) h = mid; else l = mid + 1;
+    }
+    return l;
+}
+
+__device__ __forceinline__ double prune_u(const PruneArgs& a) {
+    return a.u_from_philox ? systematic_u(a.seed, a.frame) : a.u;
+}
+
+__device__ __forceinline__ void prune_mark_body(const PruneArgs& a, int vb, int vg) {
+    const int i = vb * kScanBlock + threadIdx.x;
+    const WeighResult* R = a.res;
+    unsigned long long q = 0ull, d = 0ull;
+    if (i < a.P) {
+        const int nonfinite = R->nonfinite;
+        const double x = (a.logw[i] - R->M) - R->logS;
+        double w = a.w ? a.w[i] : exp(x);
+        if (nonfinite) w = 1.0 / (double)a.P;
+        if (a.w_out) a.w_out[i] = w;
+        bool dead = !(w >= a.prune_w);
+        if (a.ll && a.ll_cut > -INFINITY && !((double)a.ll[i] - R->ll_max >= a.ll_cut)) dead = true;
+        if (i == R->argmax || nonfinite) dead = false;
+        q = (!dead && w > 0.0 && w <= 1.0) ? __double2ull_rn(w * 4503599627370496.0) : 0ull;
+        d = dead ? 1ull : 0ull;
+    }
+    q = block_scan_u64(q);
+    const unsigned long long dl = block_scan_u64(d);
+    if (i < a.P) {
+        a.cl[i] = q;
+        a.anc[i] = d ? -(int)dl : i;
+    }
+    if (threadIdx.x == kScanBlock - 1) {
+        a.btot[vb] = q;
+        a.dtot[vb] = dl;
+    }
+}
+
+__device__ __forceinline__ void prune_totals_body(const PruneArgs& a, int vb, int vg) {
+    scan_totals_body(TotalsArgs{vb == 0 ? a.btot : a.dtot, a.nblocks}, 0, 1);
+}
+
+__device__ __forceinline__ void prune_spawn_body(const PruneArgs& a, int vb, int vg) {
+    const int m = vb * blockDim.x + threadIdx.x;
+    if (m >= a.P) return;
+    const WeighResult* R = a.res;
+    if (R->nonfinite) return;
+    const int tag = a.anc[m];
+    if (tag >= 0) return;                       // survivor
+    const int D = (int)a.dtot[a.nblocks];
+    const double S = (double)a.btot[a.nblocks];
+    if (!(S > 0.0)) {                           // nothing carries weight: leave the slot
+        a.anc[m] = m;
+        return;
+    }
+    const int r = (int)a.dtot[m / kScanBlock] - tag - 1;
+    const double u = prune_u(a);
+    const int src = prune_find(a, prune_tooth(u, r, D, S));
+    const int c = prune_copies(a, src, u, D, S);
+    a.anc[m] = src;
+    a.logw[m] = ((a.logw[src] - R->M) - R->logS) - log1p((double)c);
+    if (a.pose) {
+#pragma unroll
+        for (int e = 0; e < kPoseC; ++e) a.pose[(size_t)e * a.ld + m] = a.pose[(size_t)e * a.ld + src];
+        const size_t rows = (size_t)a.K * kPoseC;
+        for (size_t e = 0; e < rows; ++e) a.kf[e * a.ld + m] = a.kf[e * a.ld + src];
+    }
+}
+
+__device__ __forceinline__ void prune_reweigh_body(const PruneArgs& a, int vb, int vg) {
+    const int m = vb * blockDim.x + threadIdx.x;
+    if (m >= a.P) return;
+    WeighResult* R = a.res;
+    const int D = (int)a.dtot[a.nblocks];
+    const double S = (double)a.btot[a.nblocks];
+    if (R->nonfinite) {
+        a.logw[m] = -log((double)a.P);
+        a.anc[m] = m;
+        return;
+    }
+    if (m == 0) R->pruned = (S > 0.0) ? D : 0;
+    if (a.anc[m] != m) return;                  // refilled by the spawn kernel
+    const double x = (a.logw[m] - R->M) - R->logS;
+    const int c = (D > 0 && S > 0.0) ? prune_copies(a, m, prune_u(a), D, S) : 0;
+    a.logw[m] = c ? x - log1p((double)c) : x;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_prune_mark(PruneArgs a) { prune_mark_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(1024) k_prune_totals(PruneArgs a) { prune_totals_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256) k_prune_spawn(PruneArgs a) { prune_spawn_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256) k_prune_reweigh(PruneArgs a) { prune_reweigh_body(a, blockIdx.x, gridDim.x); }
+
 // ------------------------------------------------------------------ batched launches
 
 #define GMCS_BATCH_LOOP(L, CALL)                                               \
@@ -301,6 +454,18 @@ __global__ void __launch_bounds__(256) k_resample_search_b(const BatchList<Searc
 __global__ void __launch_bounds__(256) k_gather_b(const BatchList<GatherArgs>* L) {
     GMCS_BATCH_LOOP(L, const GatherArgs a = L->args[s]; gather_body(a, vb, vg));
 }
+__global__ void __launch_bounds__(kScanBlock) k_prune_mark_b(const BatchList<PruneArgs>* L) {
+    GMCS_BATCH_LOOP(L, const PruneArgs a = L->args[s]; prune_mark_body(a, vb, vg));
+}
+__global__ void __launch_bounds__(1024) k_prune_totals_b(const BatchList<PruneArgs>* L) {
+    GMCS_BATCH_LOOP(L, const PruneArgs a = L->args[s]; prune_totals_body(a, vb, vg));
+}
+__global__ void __launch_bounds__(256) k_prune_spawn_b(const BatchList<PruneArgs>* L) {
+    GMCS_BATCH_LOOP(L, const PruneArgs a = L->args[s]; prune_spawn_body(a, vb, vg));
+}
+__global__ void __launch_bounds__(256) k_prune_reweigh_b(const BatchList<PruneArgs>* L) {
+    GMCS_BATCH_LOOP(L, const PruneArgs a = L->args[s]; prune_reweigh_body(a, vb, vg));
+}
 
 template <typename K>
 static int persistent_grid_w(K kernel, int threads) {
@@ -318,6 +483,9 @@ static int grid_weigh_b() { static const int g = persistent_grid_w(k_weigh_b, kW
 static int grid_scan_b() { static const int g = persistent_grid_w(k_resample_scan_b, kScanBlock); return g; }
 static int grid_search_b() { static const int g = persistent_grid_w(k_resample_search_b, 256); return g; }
 static int grid_gather_b() { static const int g = persistent_grid_w(k_gather_b, 256); return g; }
+static int grid_pmark_b() { static const int g = persistent_grid_w(k_prune_mark_b, kScanBlock); return g; }
+static int grid_pspawn_b() { static const int g = persistent_grid_w(k_prune_spawn_b, 256); return g; }
+static int grid_preweigh_b() { static const int g = persistent_grid_w(k_prune_reweigh_b, 256); return g; }
 
 void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s) { k_weigh_b<<<grid_weigh_b(), kWeighThreads, 0, s>>>(L); }
 void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s) {
@@ -330,12 +498,27 @@ void launch_resample_search_b(const BatchList<SearchArgs>* L, cudaStream_t s) {
     k_resample_search_b<<<grid_search_b(), 256, 0, s>>>(L);
 }
 void launch_gather_b(const BatchList<GatherArgs>* L, cudaStream_t s) { k_gather_b<<<grid_gather_b(), 256, 0, s>>>(L); }
+void launch_prune_mark_b(const BatchList<PruneArgs>* L, cudaStream_t s) {
+    k_prune_mark_b<<<grid_pmark_b(), kScanBlock, 0, s>>>(L);
+}
+void launch_prune_totals_b(const BatchList<PruneArgs>* L, cudaStream_t s) {
+    k_prune_totals_b<<<2 * kMaxSlots, 1024, 0, s>>>(L);
+}
+void launch_prune_spawn_b(const BatchList<PruneArgs>* L, cudaStream_t s) {
+    k_prune_spawn_b<<<grid_pspawn_b(), 256, 0, s>>>(L);
+}
+void launch_prune_reweigh_b(const BatchList<PruneArgs>* L, cudaStream_t s) {
+    k_prune_reweigh_b<<<grid_preweigh_b(), 256, 0, s>>>(L);
+}
 
 void prepare_weights_batched() {
     grid_weigh_b();
     grid_scan_b();
     grid_search_b();
     grid_gather_b();
+    grid_pmark_b();
+    grid_pspawn_b();
+    grid_preweigh_b();
 }
 
 int grid_resample_scan(int P) { return (P + kScanBlock - 1) / kScanBlock; }
@@ -376,6 +559,21 @@ void launch_gather(const GatherArgs& a, cudaStream_t s) {
 
 void launch_normalize(double* logw, int P, const WeighResult* res, double* w_out, int* anc, cudaStream_t s) {
     if (P > 0) k_normalize<<<(P + 255) / 256, 256, 0, s>>>(logw, P, res, w_out, anc);
+}
+
+int grid_prune_slots(int P) { return (P + 255) / 256; }
+
+void launch_prune_mark(const PruneArgs& a, cudaStream_t s) {
+    if (a.P > 0) k_prune_mark<<<a.nblocks, kScanBlock, 0, s>>>(a);
+}
+void launch_prune_totals(const PruneArgs& a, cudaStream_t s) {
+    if (a.P > 0) k_prune_totals<<<2, 1024, 0, s>>>(a);
+}
+void launch_prune_spawn(const PruneArgs& a, cudaStream_t s) {
+    if (a.P > 0) k_prune_spawn<<<grid_prune_slots(a.P), 256, 0, s>>>(a);
+}
+void launch_prune_reweigh(const PruneArgs& a, cudaStream_t s) {
+    if (a.P > 0) k_prune_reweigh<<<grid_prune_slots(a.P), 256, 0, s>>>(a);
 }
 
 }  // namespace gmcs

@@ -122,10 +122,11 @@ struct WeighResult {
     double logS;        // log sum exp(logw - M)
     double ess;         // S^2 / S2
     double max_w;
+    double ll_max;      // max of the frame log-likelihoods (WeighArgs::llm), -inf without
     int argmax;
     int nonfinite;      // 1 if every log-weight was -inf or NaN
     int do_resample;    // policy decision
-    int pad;
+    int pruned;         // dead particles refilled (pruning policy)
     float est[12];      // pose of argmax (before resampling)
 };
 
@@ -133,8 +134,9 @@ struct WeighArgs {
     double* logw;       // in/out
     const float* ll;    // added to logw first when non-null
     int P;
-    int policy;         // 0 always, 1 ESS < P/2, 2 never
-    double* part;       // 4 doubles + 1 index per block
+    int policy;         // 0 always, 1 ESS < P/2, 2 never, 3 prune
+    const float* llm;   // frame log-likelihoods whose max goes to res->ll_max, or null
+    double* part;       // kWeighPart doubles per block
     unsigned* counter;  // zero between launches
     WeighResult* res;
     const float* pose;  // current poses (for the estimate)
@@ -182,6 +184,32 @@ struct GatherArgs {
 };
 
 constexpr int kScanBlock = 1024;
+constexpr int kWeighPart = 5;   // doubles per weigh block partial (M, S, S2, argmax, ll max)
+
+// Dead-particle pruning (Sec. III-F): mark + block scans, scans of the block
+// totals, refill of the dead slots, weight split. State is refilled in place.
+struct PruneArgs {
+    double* logw;             // in: log-weights (x = logw - M - logS); out: new log-weights
+    const double* w;          // given normalised weights, or null (w = exp(x))
+    double* w_out;            // optional normalised weights
+    const float* ll;          // frame log-likelihoods (likelihood criterion), or null
+    WeighResult* res;         // M, logS, argmax, ll_max, nonfinite in; pruned out
+    float* pose;              // current poses [12][ld] (null: no state refill)
+    float* kf;                // keyframe poses [K][12][ld]
+    size_t ld;
+    int P, K;
+    int nblocks;              // scan blocks of kScanBlock particles
+    unsigned long long* cl;   // block-local inclusive prefix of q
+    unsigned long long* btot; // q block totals -> exclusive offsets, total at [nblocks]
+    unsigned long long* dtot; // dead counts per block -> exclusive offsets, total at [nblocks]
+    int* anc;                 // i for survivors, ancestor for dead slots
+    double prune_w;           // posterior threshold
+    double ll_cut;            // log likelihood-ratio threshold (-inf: off)
+    double u;                 // systematic offset when u_from_philox == 0
+    int u_from_philox;
+    uint32_t frame;
+    uint64_t seed;
+};
 
 void launch_weigh(const WeighArgs& a, int nblocks, cudaStream_t s);
 int weigh_blocks(int P);
@@ -190,6 +218,10 @@ void launch_scan_totals(unsigned long long* btot, int nblocks, cudaStream_t s);
 void launch_resample_search(const SearchArgs& a, cudaStream_t s);
 void launch_gather(const GatherArgs& a, cudaStream_t s);
 void launch_normalize(double* logw, int P, const WeighResult* res, double* w_out, int* anc, cudaStream_t s);
+void launch_prune_mark(const PruneArgs& a, cudaStream_t s);
+void launch_prune_totals(const PruneArgs& a, cudaStream_t s);
+void launch_prune_spawn(const PruneArgs& a, cudaStream_t s);
+void launch_prune_reweigh(const PruneArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------ batched (serving) launches
 // One launch covers the work of up to kMaxSlots sessions: session s owns the
@@ -217,6 +249,10 @@ void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s);
 void launch_scan_totals_b(const BatchList<TotalsArgs>* L, cudaStream_t s);
 void launch_resample_search_b(const BatchList<SearchArgs>* L, cudaStream_t s);
 void launch_gather_b(const BatchList<GatherArgs>* L, cudaStream_t s);
+void launch_prune_mark_b(const BatchList<PruneArgs>* L, cudaStream_t s);
+void launch_prune_totals_b(const BatchList<PruneArgs>* L, cudaStream_t s);
+void launch_prune_spawn_b(const BatchList<PruneArgs>* L, cudaStream_t s);
+void launch_prune_reweigh_b(const BatchList<PruneArgs>* L, cudaStream_t s);
 // Size every persistent grid (occupancy queries) before a graph capture records the launches.
 void prepare_filter_batched();
 void prepare_weights_batched();
@@ -228,5 +264,6 @@ int grid_pass(const PassArgs& a);
 int grid_resample_scan(int P);
 int grid_resample_search(int P);
 int grid_gather(const GatherArgs& a);
+int grid_prune_slots(int P);           // spawn / reweigh: 256-thread blocks over the slots
 
 }  // namespace gmcs

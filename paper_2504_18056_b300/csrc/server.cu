@@ -55,6 +55,9 @@ struct TickDesc {
     BatchList<TotalsArgs> tot;
     BatchList<SearchArgs> search;
     BatchList<GatherArgs> gather;
+    BatchList<PruneArgs> prune;      // pruning policy: mark (scan blocks),
+    BatchList<PruneArgs> ptot;       // totals (2 CTAs per session),
+    BatchList<PruneArgs> pslot;      // spawn and reweigh (slot blocks)
 };
 
 template <typename A>
@@ -162,10 +165,17 @@ int capture_graph(gmcs_server* s, TickSet& t) {
     launch_pass3_b(&d->pval, s->cfg.table_dtype, false, st);
     launch_finish_b(&d->fval, false, st);
     launch_weigh_b(&d->weigh, st);
-    launch_resample_scan_b(&d->scan, st);
-    launch_scan_totals_b(&d->tot, st);
-    launch_resample_search_b(&d->search, st);
-    launch_gather_b(&d->gather, st);
+    if (s->cfg.resample == GMCS_RESAMPLE_PRUNE) {
+        launch_prune_mark_b(&d->prune, st);
+        launch_prune_totals_b(&d->ptot, st);
+        launch_prune_spawn_b(&d->pslot, st);
+        launch_prune_reweigh_b(&d->pslot, st);
+    } else {
+        launch_resample_scan_b(&d->scan, st);
+        launch_scan_totals_b(&d->tot, st);
+        launch_resample_search_b(&d->search, st);
+        launch_gather_b(&d->gather, st);
+    }
     cudaMemcpyAsync(t.h_res, t.d_res, sizeof(WeighResult) * kMaxSlots, cudaMemcpyDeviceToHost, st);
     cudaLaunchHostFunc(st, stamp_done, &t);
     cudaGraph_t g = nullptr;
@@ -236,7 +246,7 @@ int launch_tick(gmcs_server* s) {
     TickDesc& D = *t->h_desc;
     list_clear(D.pack); list_clear(D.pred); list_clear(D.sel); list_clear(D.pgrad); list_clear(D.fgrad);
     list_clear(D.pval); list_clear(D.fval); list_clear(D.weigh); list_clear(D.scan); list_clear(D.tot);
-    list_clear(D.search); list_clear(D.gather);
+    list_clear(D.search); list_clear(D.gather); list_clear(D.prune); list_clear(D.ptot); list_clear(D.pslot);
     for (size_t k = 0; k < cand.size(); ++k) {
         Session* ss = cand[k];
         gmcs_ctx* c = ss->ctx;
@@ -260,17 +270,25 @@ int launch_tick(gmcs_server* s) {
         list_add(D.fval, fa, grid_per_particle(c->P));
         WeighResult* res = t->d_res + k;
         list_add(D.weigh, weigh_args(c, nullptr, res), weigh_blocks(c->P));
-        ScanArgs sa;
-        TotalsArgs ta;
-        SearchArgs se;
-        resample_args(c, c->P, nullptr, res, c->w, 0.0, 1, frame, c->anc, &sa, &ta, &se);
-        list_add(D.scan, sa, grid_resample_scan(c->P));
-        list_add(D.tot, ta, 1);
-        list_add(D.search, se, grid_resample_search(c->P));
-        const GatherArgs g = gather_args(c, res);
-        list_add(D.gather, g, grid_gather(g));
-        // the gather writes the other buffer of the pair: it is current from the next frame on
-        c->cur = 1 - c->cur;
+        if (s->cfg.resample == GMCS_RESAMPLE_PRUNE) {
+            // dead slots are refilled in place: the state buffer stays current
+            const PruneArgs pa = prune_args(c, c->P, res, nullptr, c->ll, 0.0, 1, frame, true);
+            list_add(D.prune, pa, pa.nblocks);
+            list_add(D.ptot, pa, 2);
+            list_add(D.pslot, pa, grid_prune_slots(c->P));
+        } else {
+            ScanArgs sa;
+            TotalsArgs ta;
+            SearchArgs se;
+            resample_args(c, c->P, nullptr, res, c->w, 0.0, 1, frame, c->anc, &sa, &ta, &se);
+            list_add(D.scan, sa, grid_resample_scan(c->P));
+            list_add(D.tot, ta, 1);
+            list_add(D.search, se, grid_resample_search(c->P));
+            const GatherArgs g = gather_args(c, res);
+            list_add(D.gather, g, grid_gather(g));
+            // the gather writes the other buffer of the pair: it is current from the next frame on
+            c->cur = 1 - c->cur;
+        }
         c->frame = frame + 1;
         c->frames++;
         c->last_valid = true;
