@@ -39,8 +39,8 @@ class StepParams(C.Structure):
     _fields_ = [("sigma", C.c_double), ("eps", C.c_double), ("lambda_", C.c_double),
                 ("theta_max", C.c_double), ("t_max", C.c_double), ("w_min", C.c_double),
                 ("face_delta", C.c_double), ("k_nb", C.c_int), ("steps", C.c_int),
-                ("resample", C.c_int), ("propagate", C.c_int), ("loop_recent", C.c_int),
-                ("prune_w", C.c_double), ("ll_cut", C.c_double), ("seed", C.c_uint64)]
+                ("resample", C.c_int), ("propagate", C.c_int), ("loop_recent", C.c_int), ("model", C.c_int),
+                ("gicp_tau", C.c_double), ("prune_w", C.c_double), ("ll_cut", C.c_double), ("seed", C.c_uint64)]
 
 
 class StepOut(C.Structure):
@@ -49,8 +49,8 @@ class StepOut(C.Structure):
 
 
 DEFAULTS = dict(sigma=0.2, eps=1e-3, lambda_=1e-3, theta_max=np.deg2rad(2.0), t_max=0.1,
-                w_min=1e-6, face_delta=1e-3, k_nb=3, steps=3, resample=0, propagate=0, loop_recent=0,
-                prune_w=1e-8, ll_cut=float(np.log(1e-16)), seed=0)
+                w_min=1e-6, face_delta=1e-3, k_nb=3, steps=3, resample=0, propagate=0, loop_recent=0, model=0,
+                gicp_tau=20.0, prune_w=1e-8, ll_cut=float(np.log(1e-16)), seed=0)
 
 
 def lib():
@@ -316,6 +316,82 @@ def prune(x, w, ll, argmax, prune_w=1e-8, ll_cut=float(np.log(1e-16)), u=0.5):
     return anc, lo, int(D)
 
 
+def knn_cov(points, k=10, eps=1e-3):
+    """Per-point covariances for GICP (Eq. 4's Sigma_j, Sigma'_j): the k nearest
+    points of the same cloud (the point itself included) by squared distance
+    formed in float32 as ((dx*dx + dy*dy) + dz*dz), each operation rounded,
+    ties to the lower index; their FP64 covariance (1/k); then the plane
+    regularisation of generalised ICP (Segal et al., RSS 2009): eigenvalues
+    replaced by (eps, 1, 1) in ascending order. Returns (n, 6): xx xy xz yy yz zz."""
+    P = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+    n = P.shape[0]
+    kk = min(k, n)
+    out = np.zeros((n, 6))
+    for i in range(n):
+        d = P - P[i]
+        d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        nb = np.argsort(d2, kind="stable")[:kk]
+        Q = P[nb].astype(np.float64)
+        m = Q.sum(0) / kk
+        D = Q - m
+        Cv = D.T @ D / kk
+        lam, V = np.linalg.eigh(Cv)
+        S = V @ np.diag([eps, 1.0, 1.0]) @ V.T
+        out[i] = [S[0, 0], S[0, 1], S[0, 2], S[1, 1], S[1, 2], S[2, 2]]
+    return out
+
+
+def gicp_voxel_map(points, covs, grid):
+    """Dense GICP voxel map (the voxel-based correspondence of Sec. III-C1):
+    voxel floor((p - origin) / h) in FP64; per non-empty voxel the mean of its
+    points and the mean of their covariances. Returns (n2*n1*n0, 10):
+    mean (3), count, covariance (6); x fastest."""
+    P = np.asarray(points, np.float32).reshape(-1, 3).astype(np.float64)
+    o = np.asarray(grid["origin"], np.float64)
+    h = float(grid["h"])
+    n = [int(v) for v in grid["dims"]]
+    v = np.floor((P - o) / h).astype(np.int64)
+    inside = np.all((v >= 0) & (v < np.array(n)), axis=1)
+    rec = np.zeros((n[0] * n[1] * n[2], 10))
+    for i in np.flatnonzero(inside):
+        f = (v[i, 2] * n[1] + v[i, 1]) * n[0] + v[i, 0]
+        rec[f, :3] += P[i]
+        rec[f, 3] += 1.0
+        rec[f, 4:] += covs[i]
+    occ = rec[:, 3] > 0
+    rec[occ, :3] /= rec[occ, 3:4]
+    rec[occ, 4:] /= rec[occ, 3:4]
+    return rec
+
+
+def gicp_eval(T, kf_poses, maps, grids, scan, scov, tau=20.0, face_delta=1e-3):
+    """ora_gicp_eval_particle: ll, b (6), H (6 x 6), slack (3), valid lookups."""
+    n_nb = len(kf_poses)
+    Tk = np.ascontiguousarray(np.asarray(kf_poses, np.float64).reshape(n_nb, 12))
+    mps = [np.ascontiguousarray(m, np.float64) for m in maps]
+    mp = (_dp * max(n_nb, 1))(*[m.ctypes.data_as(_dp) for m in mps])
+    grs = (Grid * max(n_nb, 1))(*[make_grid(g) for g in grids])
+    scan, ps = _f(scan)
+    sc, psc = _d(np.asarray(scov).reshape(-1, 6))
+    T, pT = _d(np.asarray(T).reshape(12))
+    ll = C.c_double(); b = np.zeros(6); H = np.zeros(36); sl = np.zeros(3); nv = C.c_int()
+    lib().ora_gicp_eval_particle(pT, C.c_int(n_nb), Tk.ctypes.data_as(_dp), mp, grs, ps, psc,
+                                 C.c_int(scan.shape[0]), C.c_double(tau), C.c_double(face_delta), C.byref(ll),
+                                 b.ctypes.data_as(_dp), H.ctypes.data_as(_dp), sl.ctypes.data_as(_dp), C.byref(nv))
+    return {"ll": ll.value, "b": b, "H": H.reshape(6, 6), "slack": sl, "nvalid": nv.value}
+
+
+def move_h(T, b, H, sigma=0.2, lambda_=1e-3, theta_max=np.deg2rad(2.0), t_max=0.1):
+    """ora_move_h: (new pose, psi)."""
+    T, pT = _d(np.asarray(T).reshape(12))
+    b, pb = _d(b)
+    H, pH = _d(np.asarray(H).reshape(36))
+    mp = MoveParams(sigma, lambda_, theta_max, t_max, 0.0)
+    out = np.zeros(12); psi = np.zeros(6)
+    lib().ora_move_h(pT, pb, pH, C.byref(mp), out.ctypes.data_as(_dp), psi.ctypes.data_as(_dp))
+    return out, psi
+
+
 class State:
     """Particle set held by the oracle in FP64: poses (P, 12), keyframe poses
     (K, P, 12), log-weights (P,), plus the shared keyframe tables."""
@@ -330,12 +406,14 @@ class State:
         self.tables = [np.ascontiguousarray(t, np.float64) for t in tables]
         self.grids = list(grids)
 
-    def step(self, scan, dT, cov, frame, z=None, u=None, **params):
+    def step(self, scan, dT, cov, frame, z=None, u=None, scov=None, **params):
+        """One frame (ora_step). For the GICP model (model=1) the tables are voxel
+        maps (gicp_voxel_map) and scov the scan's point covariances (knn_cov)."""
         prm = dict(DEFAULTS)
         prm.update(params)
         sp = StepParams(prm["sigma"], prm["eps"], prm["lambda_"], prm["theta_max"], prm["t_max"], prm["w_min"],
                         prm["face_delta"], prm["k_nb"], prm["steps"], prm["resample"], prm["propagate"],
-                        prm["loop_recent"], prm["prune_w"], prm["ll_cut"], prm["seed"])
+                        prm["loop_recent"], prm["model"], prm["gicp_tau"], prm["prune_w"], prm["ll_cut"], prm["seed"])
         # odometry path length of this frame (Eq. 9 along the odometry trajectory)
         self.path_now += float(np.linalg.norm(np.asarray(dT, np.float64).reshape(12)[[3, 7, 11]]))
         kp = None if self.kf_path is None else self.kf_path.ctypes.data_as(_dp)
@@ -344,6 +422,9 @@ class State:
         tab_ptrs = (_dp * max(K, 1))(*[t.ctypes.data_as(_dp) for t in self.tables])
         grs = (Grid * max(K, 1))(*[make_grid(g) for g in self.grids])
         scan, ps = _f(scan)
+        psc = None
+        if scov is not None:
+            scov, psc = _d(np.asarray(scov).reshape(-1, 6))
         dT, pd = _d(dT)
         cov, pc = _d(np.asarray(cov).reshape(36))
         zp = None
@@ -357,7 +438,7 @@ class State:
         k_nb = min(prm["k_nb"], K)
         ll = np.zeros(P); w = np.zeros(P); anc = np.zeros(P, np.int32); nbr = np.zeros((P, max(k_nb, 1)), np.int32)
         lib().ora_step(C.c_int(P), C.c_int(K), self.poses.ctypes.data_as(_dp), self.kf_poses.ctypes.data_as(_dp),
-                       self.logw.ctypes.data_as(_dp), tab_ptrs, grs, ps, C.c_int(scan.shape[0]), pd, pc,
+                       self.logw.ctypes.data_as(_dp), tab_ptrs, grs, ps, psc, C.c_int(scan.shape[0]), pd, pc,
                        C.c_uint32(frame), zp, up, C.byref(sp), kp, C.c_double(self.path_now),
                        C.byref(out), ll.ctypes.data_as(_dp),
                        w.ctypes.data_as(_dp), anc.ctypes.data_as(_ip), nbr.ctypes.data_as(_ip))

@@ -490,34 +490,179 @@ static int cholesky(const double* A, int n, double* L) {
     return 0;
 }
 
+/* psi = (H + lambda diag H)^-1 g by Cholesky, then the clamps (psi = 0 when the
+ * damped matrix is not positive definite). H is modified. */
+static void damped_step(double H[36], const double g[6], const ora_move_params* mp, double psi[6]) {
+    double L[36];
+    for (int d = 0; d < 6; ++d) H[d * 6 + d] *= (1.0 + mp->lambda);
+    if (cholesky(H, 6, L) != 0) return;
+    double y[6];
+    for (int i = 0; i < 6; ++i) {        /* L y = g */
+        double s = g[i];
+        for (int k = 0; k < i; ++k) s -= L[i * 6 + k] * y[k];
+        y[i] = s / L[i * 6 + i];
+    }
+    for (int i = 5; i >= 0; --i) {       /* L^T psi = y */
+        double s = y[i];
+        for (int k = i + 1; k < 6; ++k) s -= L[k * 6 + i] * psi[k];
+        psi[i] = s / L[i * 6 + i];
+    }
+    double nw = sqrt(psi[0] * psi[0] + psi[1] * psi[1] + psi[2] * psi[2]);
+    double nv = sqrt(psi[3] * psi[3] + psi[4] * psi[4] + psi[5] * psi[5]);
+    if (nw > mp->theta_max) for (int d = 0; d < 3; ++d) psi[d] *= mp->theta_max / nw;
+    if (nv > mp->t_max) for (int d = 3; d < 6; ++d) psi[d] *= mp->t_max / nv;
+}
+
 void ora_move(const double Tt[12], const double g[6], const double mom[10], const ora_move_params* mp,
               double Tout[12], double psi[6]) {
     for (int d = 0; d < 6; ++d) psi[d] = 0.0;
     if (mom[0] >= mp->w_min) {
-        double H[36], L[36];
+        double H[36];
         ora_h_from_moments(mom, mp->sigma, H);
-        for (int d = 0; d < 6; ++d) H[d * 6 + d] *= (1.0 + mp->lambda);
-        if (cholesky(H, 6, L) == 0) {
-            double y[6];
-            for (int i = 0; i < 6; ++i) {        /* L y = g */
-                double s = g[i];
-                for (int k = 0; k < i; ++k) s -= L[i * 6 + k] * y[k];
-                y[i] = s / L[i * 6 + i];
-            }
-            for (int i = 5; i >= 0; --i) {       /* L^T psi = y */
-                double s = y[i];
-                for (int k = i + 1; k < 6; ++k) s -= L[k * 6 + i] * psi[k];
-                psi[i] = s / L[i * 6 + i];
-            }
-            double nw = sqrt(psi[0] * psi[0] + psi[1] * psi[1] + psi[2] * psi[2]);
-            double nv = sqrt(psi[3] * psi[3] + psi[4] * psi[4] + psi[5] * psi[5]);
-            if (nw > mp->theta_max) for (int d = 0; d < 3; ++d) psi[d] *= mp->theta_max / nw;
-            if (nv > mp->t_max) for (int d = 3; d < 6; ++d) psi[d] *= mp->t_max / nv;
-        }
+        damped_step(H, g, mp, psi);
     }
     double E[12];
     ora_se3_exp(psi, E);
     ora_pose_mul(Tt, E, Tout);
+}
+
+void ora_move_h(const double Tt[12], const double b[6], const double H[36], const ora_move_params* mp,
+                double Tout[12], double psi[6]) {
+    for (int d = 0; d < 6; ++d) psi[d] = 0.0;
+    double Hc[36];
+    memcpy(Hc, H, sizeof(Hc));
+    damped_step(Hc, b, mp, psi);
+    double E[12];
+    ora_se3_exp(psi, E);
+    ora_pose_mul(Tt, E, Tout);
+}
+
+/* ------------------------------------------------------------------------ */
+/* GICP distribution-to-distribution likelihood, Eq. 2-6                     */
+/* ------------------------------------------------------------------------ */
+
+/* Inverse of a 3x3 matrix by cofactors; 0 when singular. */
+static int inv3(const double A[9], double B[9]) {
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(fabs(det) > 0.0)) return 0;
+    B[0] = c00 / det;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    B[3] = c01 / det;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    B[6] = c02 / det;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    return 1;
+}
+
+/* One correspondence: voxel record vox (mean, count, covariance), scan point mu
+ * with covariance S (6), relative pose rel. Returns 0 when the voxel is empty. */
+static int gicp_term(const double* vox, const double rel[12], const double mu[3], const double* S, double tau,
+                     double* l, double bj[6], double Hj[36]) {
+    *l = -tau;
+    for (int d = 0; d < 6; ++d) bj[d] = 0.0;
+    for (int d = 0; d < 36; ++d) Hj[d] = 0.0;
+    if (!vox || !(vox[3] > 0.0)) return 0;
+    double R[9] = {rel[0], rel[1], rel[2], rel[4], rel[5], rel[6], rel[8], rel[9], rel[10]};
+    double x[3], e[3];
+    for (int r = 0; r < 3; ++r) {
+        x[r] = R[r * 3] * mu[0] + R[r * 3 + 1] * mu[1] + R[r * 3 + 2] * mu[2] + rel[r * 4 + 3];
+        e[r] = vox[r] - x[r];                       /* e = mu' - kT_t mu  (Eq. 4) */
+    }
+    double Sj[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+    double Sv[9] = {vox[4], vox[5], vox[6], vox[5], vox[7], vox[8], vox[6], vox[8], vox[9]};
+    double RS[9], C[9], Om[9];
+    mat3_mul(R, Sj, RS);
+    for (int r = 0; r < 3; ++r)                      /* Sigma' + R Sigma R^T */
+        for (int c = 0; c < 3; ++c)
+            C[r * 3 + c] = Sv[r * 3 + c] + RS[r * 3] * R[c * 3] + RS[r * 3 + 1] * R[c * 3 + 1] + RS[r * 3 + 2] * R[c * 3 + 2];
+    if (!inv3(C, Om)) return 0;
+    double Oe[3];
+    for (int r = 0; r < 3; ++r) Oe[r] = Om[r * 3] * e[0] + Om[r * 3 + 1] * e[1] + Om[r * 3 + 2] * e[2];
+    double d2 = e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
+    if (!(d2 < tau)) return 0;                      /* outlier: the capped term, no gradient */
+    *l = -d2;                                       /* Eq. 3 */
+    /* J = d(kT_t exp(xi) mu)/d xi = R [-[mu]x | I]  (3 x 6) */
+    double M[9], J[18];
+    hat(mu, M);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            J[r * 6 + c] = -(R[r * 3] * M[c] + R[r * 3 + 1] * M[3 + c] + R[r * 3 + 2] * M[6 + c]);
+            J[r * 6 + 3 + c] = R[r * 3 + c];
+        }
+    for (int a = 0; a < 6; ++a) {                   /* b = J^T Omega e, H = J^T Omega J (Eq. 6) */
+        bj[a] = J[a] * Oe[0] + J[6 + a] * Oe[1] + J[12 + a] * Oe[2];
+        double OJ[3];
+        for (int r = 0; r < 3; ++r) OJ[r] = Om[r * 3] * J[a] + Om[r * 3 + 1] * J[6 + a] + Om[r * 3 + 2] * J[12 + a];
+        for (int c = 0; c < 6; ++c) Hj[c * 6 + a] = J[c] * OJ[0] + J[6 + c] * OJ[1] + J[12 + c] * OJ[2];
+    }
+    return 1;
+}
+
+void ora_gicp_eval_particle(const double Tt[12], int n_nb, const double* Tk, const double* const* maps,
+                            const ora_grid* grids, const float* scan, const double* scov, int N, double tau,
+                            double face_delta, double* ll, double b[6], double H[36], double slack[3], int* nvalid) {
+    double acc_l = 0.0, acc_b[6] = {0}, acc_H[36] = {0}, sl[3] = {0, 0, 0};
+    int nv = 0;
+    for (int s = 0; s < n_nb; ++s) {
+        double inv[12], rel[12];
+        ora_pose_inv(Tk + 12 * s, inv);
+        ora_pose_mul(inv, Tt, rel);                 /* kT_t = (T_k)^-1 T_t */
+        const ora_grid* g = &grids[s];
+        const double* map = maps[s];
+        for (int j = 0; j < N; ++j) {
+            double mu[3] = {scan[3 * j], scan[3 * j + 1], scan[3 * j + 2]};
+            double u[3];
+            int c[3], inside = 1;
+            for (int r = 0; r < 3; ++r) {
+                double x = rel[r * 4] * mu[0] + rel[r * 4 + 1] * mu[1] + rel[r * 4 + 2] * mu[2] + rel[r * 4 + 3];
+                u[r] = (x - g->origin[r]) / g->h;
+                c[r] = (int)floor(u[r]);
+                if (c[r] < 0 || c[r] >= g->n[r]) inside = 0;
+            }
+            double l, bj[6], Hj[36];
+            int ok = gicp_term(inside ? map + 10 * vidx(g, c[0], c[1], c[2]) : NULL, rel, mu, scov + 6 * (size_t)j,
+                               tau, &l, bj, Hj);
+            nv += ok;
+            acc_l += l;
+            for (int d = 0; d < 6; ++d) acc_b[d] += bj[d];
+            for (int d = 0; d < 36; ++d) acc_H[d] += Hj[d];
+            if (slack) {
+                /* the voxel across the nearest face, when u is within face_delta of it */
+                int ax = -1, dir = 0;
+                double best = face_delta;
+                for (int r = 0; r < 3; ++r) {
+                    double f = u[r] - floor(u[r]);
+                    if (f < best) { best = f; ax = r; dir = -1; }
+                    if (1.0 - f < best) { best = 1.0 - f; ax = r; dir = +1; }
+                }
+                if (ax >= 0) {
+                    int c2[3] = {c[0], c[1], c[2]};
+                    c2[ax] += dir;
+                    int in2 = 1;
+                    for (int r = 0; r < 3; ++r)
+                        if (c2[r] < 0 || c2[r] >= g->n[r]) in2 = 0;
+                    double l2, b2[6], H2[36];
+                    gicp_term(in2 ? map + 10 * vidx(g, c2[0], c2[1], c2[2]) : NULL, rel, mu, scov + 6 * (size_t)j,
+                              tau, &l2, b2, H2);
+                    double db = 0.0, dH = 0.0;
+                    for (int d = 0; d < 6; ++d) db += (b2[d] - bj[d]) * (b2[d] - bj[d]);
+                    for (int d = 0; d < 36; ++d) dH += (H2[d] - Hj[d]) * (H2[d] - Hj[d]);
+                    sl[0] += fabs(l2 - l);
+                    sl[1] += sqrt(db);
+                    sl[2] += sqrt(dH);
+                }
+            }
+        }
+    }
+    if (ll) *ll = acc_l;
+    if (b) for (int d = 0; d < 6; ++d) b[d] = acc_b[d];
+    if (H) for (int d = 0; d < 36; ++d) H[d] = acc_H[d];
+    if (slack) for (int d = 0; d < 3; ++d) slack[d] = sl[d];
+    if (nvalid) *nvalid = nv;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -710,7 +855,7 @@ int ora_prune(const double* x, const double* w, const double* ll, int P, int arg
 
 void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
               const double* const* tables, const ora_grid* grids,
-              const float* scan, int N, const double dT[12], const double cov[36],
+              const float* scan, const double* scov, int N, const double dT[12], const double cov[36],
               uint32_t frame, const double* z, const double* u, const ora_step_params* sp,
               const double* kf_path, double path_now,
               ora_step_out* out, double* ll_out, double* w_out, int* anc_out, int* nbr_out) {
@@ -756,9 +901,16 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
                 const int* nb = nbr + (size_t)i * k_nb;
                 if (!ora_loop(nb, k_nb, K, sp->loop_recent)) continue;   /* Sec. III-C2 */
                 double psi[6];
-                ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
-                                  NULL, g, mom, NULL, NULL, NULL, 0);
-                ora_move(poses + 12 * (size_t)i, g, mom, &mp, poses + 12 * (size_t)i, psi);
+                if (sp->model == 1) {
+                    double Hg[36];
+                    ora_gicp_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, scov, N, sp->gicp_tau,
+                                           sp->face_delta, NULL, g, Hg, NULL, NULL);
+                    ora_move_h(poses + 12 * (size_t)i, g, Hg, &mp, poses + 12 * (size_t)i, psi);
+                } else {
+                    ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
+                                      NULL, g, mom, NULL, NULL, NULL, 0);
+                    ora_move(poses + 12 * (size_t)i, g, mom, &mp, poses + 12 * (size_t)i, psi);
+                }
                 if (sp->propagate && kf_path) {
                     double* kfi = (double*)malloc(sizeof(double) * 12 * (size_t)K);
                     for (int k = 0; k < K; ++k)
@@ -768,6 +920,9 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
                         memcpy(kf_poses + ((size_t)k * P + i) * 12, kfi + 12 * (size_t)k, 12 * sizeof(double));
                     free(kfi);
                 }
+            } else if (sp->model == 1) {
+                ora_gicp_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, scov, N, sp->gicp_tau,
+                                       sp->face_delta, ll + i, NULL, NULL, NULL, NULL);
             } else {
                 ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
                                   ll + i, NULL, NULL, NULL, NULL, NULL, 0);

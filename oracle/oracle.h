@@ -108,6 +108,31 @@ typedef struct {
 void ora_move(const double Tt[12], const double g[6], const double mom[10], const ora_move_params* mp,
               double Tout[12], double psi[6]);
 
+/* Eq. 5-7 with a given Gauss-Newton matrix: psi = (H + lambda diag H)^-1 b,
+ * clamped, Tout = Tt exp(psi) (no move when the damped H is not positive definite). */
+void ora_move_h(const double Tt[12], const double b[6], const double H[36], const ora_move_params* mp,
+                double Tout[12], double psi[6]);
+
+/* ---- GICP distribution-to-distribution likelihood (Eq. 2-6) on voxel maps.
+ * A map is a dense lattice of n[0] x n[1] x n[2] voxels of edge h from origin
+ * (voxel (ix,iy,iz) covers origin + h [ix, ix+1) x [iy, iy+1) x [iz, iz+1)),
+ * 10 doubles each, x fastest: mean (3), point count (1), covariance (6: xx xy
+ * xz yy yz zz); a voxel with count 0 has no distribution. scov: N x 6 scan point
+ * covariances. Every (neighbour s, scan point mu_j) pair adds one term. When the
+ * transformed point lies in a non-empty voxel,
+ *   e = mu' - kT_t mu_j, Omega = (Sigma' + R Sigma_j R^T)^-1,  d2 = e^T Omega e,
+ * and d2 < tau (an inlier):
+ *   ll += -d2,  J = d(kT_t exp(xi) mu_j)/d xi = R [-[mu_j]x | I],
+ *   b += J^T Omega e,  H += J^T Omega J;
+ * otherwise (no voxel, empty voxel, or d2 >= tau) ll += -tau and nothing else
+ * (the step psi = H^-1 b ascends ll). slack[3]: summed over lookups whose
+ * coordinate lies within face_delta voxels of a face, |change| of the term's
+ * ll, b (norm) and H (Frobenius) when the voxel across that face is used.
+ * nvalid: inlier lookups. Any output may be NULL. */
+void ora_gicp_eval_particle(const double Tt[12], int n_nb, const double* Tk, const double* const* maps,
+                            const ora_grid* grids, const float* scan, const double* scov, int N, double tau,
+                            double face_delta, double* ll, double b[6], double H[36], double slack[3], int* nvalid);
+
 /* ---- keyframe pose propagation, Eq. 8-10: with o the oldest (lowest-index)
  * neighbour keyframe, every keyframe k > o moves by T_k exp(r_k psi),
  * r_k = (D_k - D_o) / (Dt - D_o), D the odometry path length at each keyframe
@@ -159,6 +184,8 @@ typedef struct {
     int resample;        /* 0 always, 1 when ESS < P/2, 2 never, 3 prune dead particles */
     int propagate;       /* 1: keyframe pose propagation after every move (Eq. 8-10) */
     int loop_recent;     /* > 0: move only particles whose oldest neighbour is not among the newest loop_recent */
+    int model;           /* 0 voxel likelihood field, 1 GICP (tables are voxel maps, scov required) */
+    double gicp_tau;     /* model 1: cap of a term's e^T Omega e (outliers and points without a voxel) */
     double prune_w;      /* resample 3: posterior threshold */
     double ll_cut;       /* resample 3: log likelihood-ratio threshold (-inf: off) */
     uint64_t seed;
@@ -172,6 +199,8 @@ typedef struct {
 } ora_step_out;
 
 /*
+ * tables    K likelihood tables (model 0) or K GICP voxel maps (model 1), with grids
+ * scov      model 1: N x 6 scan point covariances (else may be NULL)
  * poses     P x 12 current poses (in/out)
  * kf_poses  K x P x 12 per-particle keyframe poses (in/out; gathered on resample)
  * logw      P log-weights (in/out)
@@ -184,7 +213,7 @@ typedef struct {
  */
 void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
               const double* const* tables, const ora_grid* grids,
-              const float* scan, int N, const double dT[12], const double cov[36],
+              const float* scan, const double* scov, int N, const double dT[12], const double cov[36],
               uint32_t frame, const double* z, const double* u, const ora_step_params* sp,
               const double* kf_path, double path_now,
               ora_step_out* out, double* ll_out, double* w_out, int* anc_out, int* nbr_out);
