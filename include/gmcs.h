@@ -63,6 +63,10 @@ extern "C" {
 
 #define GMCS_MAX_NB 8         /* upper bound on k_nb */
 
+#define GMCS_MODEL_FIELD 0    /* voxel likelihood field exp(-d^2 / 2 sigma^2), trilinear */
+#define GMCS_MODEL_GICP 1     /* GICP distribution-to-distribution terms on voxel maps (Eq. 2-6) */
+#define GMCS_KNN_MAX 32       /* upper bound on knn */
+
 typedef struct {
     float sigma;       /* field width (m): vertex value exp(-d^2 / 2 sigma^2) */
     float r_t;         /* truncation radius (m): value 0 where d > r_t */
@@ -85,6 +89,11 @@ typedef struct {
     float prune_lr;    /* GMCS_RESAMPLE_PRUNE: a particle whose frame likelihood is below
                           prune_lr times the best particle's is dead (the likelihood criterion
                           of Sec. III-F, relative to the frame's best; 1e-16); 0: off */
+    int model;         /* GMCS_MODEL_* likelihood of the context (its keyframes' map type) */
+    int knn;           /* GICP: neighbours per point covariance (the point included; 10) */
+    float cov_eps;     /* GICP: plane regularisation, covariance eigenvalues (cov_eps, 1, 1) */
+    float gicp_tau;    /* GICP: cap of a term's e^T Omega e; points without a voxel or with
+                          e^T Omega e >= gicp_tau add -gicp_tau and no gradient (20) */
     uint64_t seed;     /* key of the Philox4x32-10 draws (motion noise, resampling offset) */
 } gmcs_config;
 
@@ -123,7 +132,8 @@ typedef struct gmcs_ctx gmcs_ctx;
 
 /* Defaults: sigma 0.2 m, r_t 1.0 m, eps 1e-3, lambda 1e-3, theta_max 2 deg,
  * t_max 0.1 m, w_min 1e-6, k_nb 3, steps 3, FP32 tables, resample always,
- * no propagation, no loop condition, prune_w 1e-8, prune_lr 1e-16, seed 0. */
+ * no propagation, no loop condition, prune_w 1e-8, prune_lr 1e-16, voxel field
+ * model (GICP settings knn 10, cov_eps 1e-3, gicp_tau 20), seed 0. */
 void gmcs_config_default(gmcs_config* cfg);
 
 /*
@@ -155,6 +165,11 @@ int gmcs_init_particles(gmcs_ctx* ctx, const float* poses, int P, const double* 
  * grid: the table lattice in that frame. The library builds the table on the
  * device (K8: splat of d^2 within r_t, then exp) and stores it packed per cell
  * (8 corner values contiguous) in cfg.table_dtype.
+ * GICP model: grid is the voxel lattice (n = voxels per axis, voxel (ix,iy,iz)
+ * covering origin + h [ix, ix+1) x ...); the library computes every point's
+ * plane-regularised covariance from its cfg.knn nearest keyframe points (FP64)
+ * and stores per voxel the mean of its points and of their covariances (48 B,
+ * FP32). Points outside the lattice are dropped.
  * kf_poses: P x 12 floats (host or device), the keyframe pose held by each
  * particle, or NULL to copy every particle's current pose (the paper's
  * insertion of the current frame as a keyframe). Needs particles to exist.
@@ -221,6 +236,10 @@ int gmcs_select(gmcs_ctx* ctx, int* nbr_out);
  *   g   = d ll / d xi for T_t exp(xi) at xi = 0             (P x 6 floats)
  *   mom = [W, Sx, Sy, Sz, Qxx, Qxy, Qxz, Qyy, Qyz, Qzz], w = L/(L+eps),
  *         W = sum w, S = sum w p, Q = sum w p p^T            (P x 10 floats)
+ * GICP model (Eq. 3-6): ll = sum_{j,k} -min(e^T Omega e, gicp_tau) (gicp_tau for
+ * points without a voxel), g = 2 b with b = sum J^T Omega e over the inliers
+ * (the gradient of ll where Omega does not move with the pose), and mom = the
+ * upper triangle of H = sum J^T Omega J, row-major (P x 21 floats).
  * Any output may be NULL; outputs are host or device (host: synchronises).
  */
 int gmcs_eval(gmcs_ctx* ctx, const float* scan, int N, float* ll, float* g, float* mom);
@@ -326,7 +345,17 @@ int gmcs_set_kf_poses(gmcs_ctx* ctx, int k, const float* poses);
  * frame did not resample), nbr = neighbour keyframes (P x k_nb ints).
  */
 int gmcs_get_frame_diag(gmcs_ctx* ctx, float* ll, double* w, int* anc, int* nbr);
-/* Copy table k as float vertex values [n2][n1][n0] (unpacked from its cells). */
+/* GICP point covariances of a cloud, as the context computes them for scans and
+ * keyframes: for each of the n points (n x 3 floats, host or device) the
+ * cfg.knn nearest points of the cloud (the point included; squared distances
+ * in float as ((dx*dx + dy*dy) + dz*dz), ties to the lower index), their FP64
+ * covariance (1/k), plane-regularised to eigenvalues (cfg.cov_eps, 1, 1).
+ * cov: n x 6 doubles (xx xy xz yy yz zz), host or device. Any model. */
+int gmcs_point_covariances(gmcs_ctx* ctx, const float* pts, int n, double* cov);
+
+/* Copy table k as float vertex values [n2][n1][n0] (unpacked from its cells).
+ * GICP model: the voxel records, 12 floats per voxel [n2][n1][n0]: mean (3),
+ * 1 or 0 (voxel holds points), covariance xx xy xz yy yz zz, 0, 0. */
 int gmcs_get_table(gmcs_ctx* ctx, int k, float* vals);
 /* Current sizes. Any pointer may be NULL. */
 int gmcs_get_sizes(gmcs_ctx* ctx, int* P, int* K, uint32_t* frame);
@@ -369,7 +398,7 @@ typedef struct {
     double latency_p50_s, latency_p99_s, latency_max_s, latency_mean_s;   /* submission to completion */
 } gmcs_server_stats;
 
-/* cfg: shared by all sessions (k_nb must be 3); budget_bytes: device memory the
+/* cfg: shared by all sessions (k_nb must be 3, voxel field model); budget_bytes: device memory the
  * sessions may hold; max_sessions: open-session limit. Errors: GMCS_E_INVALID,
  * GMCS_E_OOM, GMCS_E_CUDA. */
 int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_sessions, gmcs_server** out);

@@ -24,6 +24,8 @@ PENDING = 1
 TABLE_F32, TABLE_BF16, TABLE_F16 = 0, 1, 2
 RESAMPLE_ALWAYS, RESAMPLE_ESS_HALF, RESAMPLE_NEVER, RESAMPLE_PRUNE = 0, 1, 2, 3
 MAX_NB = 8
+MODEL_FIELD, MODEL_GICP = 0, 1
+KNN_MAX = 32
 
 
 class GmcsError(RuntimeError):
@@ -36,7 +38,8 @@ class Config(C.Structure):
     _fields_ = [("sigma", C.c_float), ("r_t", C.c_float), ("eps", C.c_float), ("lambda_", C.c_float),
                 ("theta_max", C.c_float), ("t_max", C.c_float), ("w_min", C.c_float), ("k_nb", C.c_int),
                 ("steps", C.c_int), ("table_dtype", C.c_int), ("resample", C.c_int), ("propagate", C.c_int),
-                ("loop_recent", C.c_int), ("prune_w", C.c_float), ("prune_lr", C.c_float), ("seed", C.c_uint64)]
+                ("loop_recent", C.c_int), ("prune_w", C.c_float), ("prune_lr", C.c_float), ("model", C.c_int),
+                ("knn", C.c_int), ("cov_eps", C.c_float), ("gicp_tau", C.c_float), ("seed", C.c_uint64)]
 
 
 class Grid(C.Structure):
@@ -95,6 +98,7 @@ _SIGS = {
     "gmcs_get_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmcs_get_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_get_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_point_covariances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_set_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_get_frame_diag": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmcs_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_uint32)]),
@@ -322,6 +326,14 @@ class Filter:
 
     def frame_diag(self, ll=None, w=None, anc=None, nbr=None):
         _check(lib().gmcs_get_frame_diag(self.ctx, _ptr(ll), _ptr(w), _ptr(anc), _ptr(nbr)), "gmcs_get_frame_diag")
+
+    def point_covariances(self, pts, cov=None):
+        """GICP point covariances of a cloud (gmcs_point_covariances): n x 6 doubles."""
+        if cov is None:
+            cov = np.zeros((pts.shape[0], 6))
+        _check(lib().gmcs_point_covariances(self.ctx, _ptr(pts), int(pts.shape[0]), _ptr(cov)),
+               "gmcs_point_covariances")
+        return cov
 
     def get_table(self, k, vals):
         _check(lib().gmcs_get_table(self.ctx, int(k), _ptr(vals)), "gmcs_get_table")

@@ -45,6 +45,7 @@ struct gmcs_ctx {
     float* part = nullptr;
     size_t part_floats = 0;
     float4* scan = nullptr;
+    float4* scov = nullptr;          // GICP: scan point covariances, 2 float4 per point
     float* stage = nullptr;          // N x 3 points / P x 6 noise staging
     size_t stage_floats = 0;
     double* wpart = nullptr;
@@ -91,6 +92,6 @@ GatherArgs gather_args(gmcs_ctx* c, const WeighResult* res);
 PruneArgs prune_args(gmcs_ctx* c, int P, WeighResult* res, const double* w, const float* ll, double u,
                      int u_from_philox, uint32_t frame, bool refill);
 void fill_out(const WeighResult& r, uint32_t frame, gmcs_step_out* o);
-void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len);
+void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len, int max_groups = kMaxGroups);
 
 }  // namespace gmcs

@@ -20,7 +20,7 @@
 
 using namespace gmcs;
 
-static_assert(sizeof(gmcs_config) == 72, "gmcs_config layout is part of the ABI");
+static_assert(sizeof(gmcs_config) == 88, "gmcs_config layout is part of the ABI");
 static_assert(sizeof(gmcs_step_out) == 144, "gmcs_step_out layout is part of the ABI");
 static_assert(sizeof(gmcs_grid) == 48, "gmcs_grid layout is part of the ABI");
 
@@ -36,12 +36,12 @@ namespace gmcs {
 // Chunking of the scan for the lookup pass: a CTA covers kPassTW particle tiles
 // x kPassCW point chunks; the number of chunk groups G gives several waves of
 // CTAs on 148 SMs, at most kMaxGroups (the partial-sum scratch), chunks >= 8 points.
-void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len) {
+void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len, int max_groups) {
     const int nt = (P + 31) / 32;
     const int ntg = (nt + kPassTW - 1) / kPassTW;
     const int target = 148 * 8 * 4;
     int g = (target + ntg - 1) / ntg;
-    g = std::max(1, std::min(g, kMaxGroups));
+    g = std::max(1, std::min(g, max_groups));
     const int max_chunks = std::max(1, (N + 7) / 8);
     while (g > 1 && g * kPassCW > max_chunks) --g;
     const int chunks = g * kPassCW;
@@ -59,7 +59,7 @@ size_t ctx_device_bytes(int max_particles, int max_keyframes, int max_points) {
     size_t b = 0;
     b += 2 * (sizeof(float) * kPoseC * ld + sizeof(float) * kPoseC * ld * max_keyframes);
     b += sizeof(double) * ld * 2 + sizeof(float) * ld + sizeof(float) * 6 * ld;   // logw, w, ll, gbuf
-    b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * max_points + sizeof(float) * stage;
+    b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * 3 * max_points + sizeof(float) * stage;
     b += sizeof(double) * kWeighPart * 148 * 4 + sizeof(unsigned) + sizeof(WeighResult);
     b += sizeof(unsigned long long) * (ld + 2 * (nb + 1)) + sizeof(int) * ld;
     b += sizeof(TableDesc) * max_keyframes + sizeof(float) * max_keyframes;
@@ -173,6 +173,20 @@ int upload_scan(gmcs_ctx* c, const float* scan, int N) {
         Launch L(c, K_MISC);
         launch_scan_pack(src, N, c->scan, c->stream);
     }
+    int rc = check_launch();
+    if (rc || c->cfg.model != GMCS_MODEL_GICP) return rc;
+    // GICP: per-point covariances of the scan (k nearest points of the scan itself)
+    KnnCovArgs ka;
+    ka.pts = c->scan;
+    ka.n = N;
+    ka.k = c->cfg.knn;
+    ka.eps = (double)c->cfg.cov_eps;
+    ka.cov64 = nullptr;
+    ka.cov32 = c->scov;
+    {
+        Launch L(c, K_MISC);
+        launch_knn_cov(ka, c->stream);
+    }
     return check_launch();
 }
 
@@ -184,13 +198,18 @@ namespace gmcs {
 void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw,
                const float* pose_override, PassArgs* pa_out, FinishArgs* fa_out) {
     int nt, groups, chunk;
-    pass_shape(c->P, N, &nt, &groups, &chunk);
+    const bool gicp = c->cfg.model == GMCS_MODEL_GICP;
+    // the partial-sum scratch holds kMaxGroups x kAccGrad accumulators per particle
+    pass_shape(c->P, N, &nt, &groups, &chunk, gicp ? kMaxGroups * kAccGrad / kAccGicp : kMaxGroups);
     PassArgs pa;
     pa.pose = pose_override ? pose_override : c->pose[c->cur];
     pa.kf = c->kf[c->cur];
     pa.nbr = c->nbr;
     pa.tables = c->d_tables;
     pa.scan = c->scan;
+    pa.scov = c->scov;
+    pa.tau = c->cfg.gicp_tau;
+    pa.model = c->cfg.model;
     pa.part = c->part;
     pa.ld = c->ld;
     pa.P = c->P;
@@ -224,6 +243,7 @@ void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* o
     fa.k_nb = std::min(c->cfg.k_nb, c->K);
     fa.propagate = c->cfg.propagate;
     fa.loop_recent = c->cfg.loop_recent;
+    fa.model = c->cfg.model;
     *pa_out = pa;
     *fa_out = fa;
 }
@@ -346,7 +366,8 @@ int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out
     pass_args(c, N, grad, move, out_ll, out_g, out_mom, logw, pose_override, &pa, &fa);
     {
         Launch L(c, grad ? K_PASS_GRAD : K_PASS_VALUE);
-        launch_pass(pa, c->cfg.table_dtype, grad, c->stream);
+        if (pa.model == GMCS_MODEL_GICP) launch_gicp_pass(pa, grad, c->stream);
+        else launch_pass(pa, c->cfg.table_dtype, grad, c->stream);
     }
     int rc = check_launch();
     if (rc) return rc;
@@ -500,6 +521,10 @@ void gmcs_config_default(gmcs_config* cfg) {
     cfg->resample = GMCS_RESAMPLE_ALWAYS;
     cfg->prune_w = 1e-8f;
     cfg->prune_lr = 1e-16f;
+    cfg->model = GMCS_MODEL_FIELD;
+    cfg->knn = 10;
+    cfg->cov_eps = 1e-3f;
+    cfg->gicp_tau = 20.f;
     cfg->seed = 0;
 }
 
@@ -523,7 +548,9 @@ static bool config_ok(const gmcs_config* c) {
            (c->propagate == 0 || c->propagate == 1) && c->loop_recent >= 0 &&
            c->t_max > 0.f && c->w_min >= 0.f && c->k_nb >= 1 && c->k_nb <= GMCS_MAX_NB && c->steps >= 0 &&
            c->steps <= 64 && c->table_dtype >= 0 && c->table_dtype <= 2 && c->resample >= 0 && c->resample <= 3 &&
-           c->prune_w >= 0.f && c->prune_w < 1.f && c->prune_lr >= 0.f && c->prune_lr < 1.f;
+           c->prune_w >= 0.f && c->prune_w < 1.f && c->prune_lr >= 0.f && c->prune_lr < 1.f &&
+           (c->model == GMCS_MODEL_FIELD || c->model == GMCS_MODEL_GICP) && c->knn >= 1 && c->knn <= kKnnMax &&
+           c->cov_eps > 0.f && c->cov_eps <= 1.f && c->gicp_tau > 0.f;
 }
 
 int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, int max_points, void* cuda_stream,
@@ -557,6 +584,7 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     if (!rc) rc = dalloc(c, &c->nbr, (size_t)GMCS_MAX_NB * ld);
     if (!rc) rc = dalloc(c, &c->part, c->part_floats);
     if (!rc) rc = dalloc(c, &c->scan, (size_t)max_points);
+    if (!rc) rc = dalloc(c, &c->scov, (size_t)2 * max_points);
     if (!rc) rc = dalloc(c, &c->stage, c->stage_floats);
     if (!rc) rc = dalloc(c, &c->wpart, (size_t)kWeighPart * 148 * 4);
     if (!rc) rc = dalloc(c, &c->counter, 1);
@@ -590,7 +618,7 @@ int gmcs_destroy(gmcs_ctx* c) {
     for (auto e : c->free_events) cudaEventDestroy(e);
     for (auto& t : c->tables) cudaFree(t.cells);
     void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->gbuf, c->ll, c->nbr, c->part, c->scan,
-                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->dtot, c->anc, c->d_tables, c->d2,
+                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->dtot, c->anc, c->d_tables, c->d2, c->scov,
                     c->d_kf_path};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -625,10 +653,189 @@ int gmcs_init_particles(gmcs_ctx* c, const float* poses, int P, const double* lo
     return GMCS_OK;
 }
 
+namespace {
+
+// GICP keyframe: per-point covariances (k nearest keyframe points, FP64), then
+// per-voxel means of points and covariances into a dense record lattice.
+int build_gicp_map(gmcs_ctx* c, const float* dpts, int n, const gmcs_grid* grid, HostTable* t) {
+    const size_t nv = (size_t)grid->n[0] * grid->n[1] * grid->n[2];
+    t->bytes = nv * 3 * sizeof(float4);
+    if (cudaMalloc(&t->cells, t->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        t->cells = nullptr;
+        return GMCS_E_OOM;
+    }
+    float4* p4 = nullptr;
+    double* cov = nullptr;
+    double* sums = nullptr;
+    int rc = GMCS_OK;
+    if (cudaMalloc((void**)&p4, sizeof(float4) * (size_t)std::max(n, 1)) != cudaSuccess ||
+        cudaMalloc((void**)&cov, sizeof(double) * 6 * (size_t)std::max(n, 1)) != cudaSuccess ||
+        cudaMalloc((void**)&sums, sizeof(double) * 10 * nv) != cudaSuccess) {
+        cudaGetLastError();
+        rc = GMCS_E_OOM;
+    }
+    if (!rc) rc = cuda_status(cudaMemsetAsync(sums, 0, sizeof(double) * 10 * nv, c->stream));
+    if (!rc && n > 0) {
+        {
+            Launch L(c, K_TABLE);
+            launch_scan_pack(dpts, n, p4, c->stream);
+        }
+        KnnCovArgs ka;
+        ka.pts = p4;
+        ka.n = n;
+        ka.k = c->cfg.knn;
+        ka.eps = (double)c->cfg.cov_eps;
+        ka.cov64 = cov;
+        ka.cov32 = nullptr;
+        {
+            Launch L(c, K_TABLE);
+            launch_knn_cov(ka, c->stream);
+        }
+        rc = check_launch();
+    }
+    VoxelArgs va;
+    va.pts = p4;
+    va.cov = cov;
+    va.n = n;
+    va.ox = grid->origin[0];
+    va.oy = grid->origin[1];
+    va.oz = grid->origin[2];
+    va.h = grid->h;
+    va.nx = grid->n[0];
+    va.ny = grid->n[1];
+    va.nz = grid->n[2];
+    va.sums = sums;
+    va.rec = reinterpret_cast<float4*>(t->cells);
+    if (!rc) {
+        {
+            Launch L(c, K_TABLE);
+            launch_voxel_accum(va, c->stream);
+        }
+        rc = check_launch();
+    }
+    if (!rc) {
+        {
+            Launch L(c, K_TABLE);
+            launch_voxel_final(va, c->stream);
+        }
+        rc = check_launch();
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(p4);
+    cudaFree(cov);
+    cudaFree(sums);
+    if (rc) {
+        cudaFree(t->cells);
+        t->cells = nullptr;
+    }
+    return rc;
+}
+
+// Table descriptor, per-particle keyframe poses and path length of a new
+// keyframe whose table t is built; frees t on failure.
+int register_keyframe(gmcs_ctx* c, HostTable& t, const gmcs_grid* grid, int ncx, int ncy, int ncz,
+                      const float* kf_poses, int* kf_id) {
+    int rc = GMCS_OK;
+    TableDesc td;
+    std::memset(&td, 0, sizeof(td));
+    td.cells = t.cells;
+    td.ox = (float)grid->origin[0];
+    td.oy = (float)grid->origin[1];
+    td.oz = (float)grid->origin[2];
+    td.inv_h = (float)(1.0 / grid->h);
+    td.h = (float)grid->h;
+    td.ncx = ncx;
+    td.ncy = ncy;
+    td.ncz = ncz;
+    td.dtype = t.dtype;
+    const int k = c->K;
+    rc = cuda_status(cudaMemcpyAsync(c->d_tables + k, &td, sizeof(td), cudaMemcpyHostToDevice, c->stream));
+    if (!rc) {
+        float* dst = c->kf[c->cur] + (size_t)k * kPoseC * c->ld;
+        if (kf_poses) {
+            rc = cuda_status(cudaMemcpyAsync(c->part, kf_poses, sizeof(float) * 12 * (size_t)c->P, cudaMemcpyDefault,
+                                             c->stream));
+            if (!rc) {
+                Launch L(c, K_MISC);
+                launch_aos_to_soa(c->part, c->P, 12, dst, c->ld, c->stream);
+            }
+        } else {
+            rc = cuda_status(cudaMemcpy2DAsync(dst, c->ld * sizeof(float), c->pose[c->cur], c->ld * sizeof(float),
+                                               c->P * sizeof(float), kPoseC, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        if (!rc) rc = check_launch();
+    }
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));   // td lives on this stack frame
+    if (rc) {
+        cudaFree(t.cells);
+        return rc;
+    }
+    {
+        const float d = (float)c->path_now;
+        if (cudaMemcpy(c->d_kf_path + k, &d, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(t.cells);
+            return GMCS_E_CUDA;
+        }
+    }
+    c->kf_path.push_back(c->path_now);
+    c->dev_bytes += t.bytes;
+    c->tables.push_back(t);
+    c->K = k + 1;
+    if (kf_id) *kf_id = k;
+    return GMCS_OK;
+}
+
+// Stage host points on the device (device points are used in place).
+int stage_points(gmcs_ctx* c, const float* pts, int n, const float** dpts, float** tmp) {
+    *dpts = pts;
+    *tmp = nullptr;
+    if (n > 0 && !is_device_ptr(pts)) {
+        if (cudaMalloc((void**)tmp, sizeof(float) * 3 * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            *tmp = nullptr;
+            return GMCS_E_OOM;
+        }
+        if (cudaMemcpyAsync(*tmp, pts, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess) {
+            cudaFree(*tmp);
+            *tmp = nullptr;
+            return GMCS_E_CUDA;
+        }
+        *dpts = *tmp;
+    }
+    return GMCS_OK;
+}
+
+int add_keyframe_gicp(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* grid, const float* kf_poses, int* kf_id) {
+    for (int a = 0; a < 3; ++a)
+        if (grid->n[a] < 1 || !std::isfinite(grid->origin[a])) return GMCS_E_INVALID;
+    if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return GMCS_E_INVALID;
+    const size_t nv = (size_t)grid->n[0] * grid->n[1] * grid->n[2];
+    if (nv >= ((size_t)1 << 31)) return GMCS_E_INVALID;
+    const float* dpts = nullptr;
+    float* tmp = nullptr;
+    int rc = stage_points(c, pts, n, &dpts, &tmp);
+    if (rc) return rc;
+    HostTable t;
+    t.grid = *grid;
+    t.dtype = 3;
+    rc = build_gicp_map(c, dpts, n, grid, &t);
+    if (tmp) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+    }
+    if (rc) return rc;
+    return register_keyframe(c, t, grid, grid->n[0], grid->n[1], grid->n[2], kf_poses, kf_id);
+}
+
+}  // namespace
+
 int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* grid, const float* kf_poses, int* kf_id) {
     if (!c || !grid || n < 0 || (n > 0 && !pts)) return GMCS_E_INVALID;
     if (!c->have_particles) return GMCS_E_STATE;
     if (c->K >= c->Kmax) return GMCS_E_CAPACITY;
+    if (c->cfg.model == GMCS_MODEL_GICP) return add_keyframe_gicp(c, pts, n, grid, kf_poses, kf_id);
     for (int a = 0; a < 3; ++a)
         if (grid->n[a] < 2 || !std::isfinite(grid->origin[a])) return GMCS_E_INVALID;
     if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return GMCS_E_INVALID;
@@ -724,53 +931,7 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
         cudaFree(t.cells);
         return rc;
     }
-    TableDesc td;
-    std::memset(&td, 0, sizeof(td));
-    td.cells = t.cells;
-    td.ox = (float)grid->origin[0];
-    td.oy = (float)grid->origin[1];
-    td.oz = (float)grid->origin[2];
-    td.inv_h = (float)(1.0 / grid->h);
-    td.h = (float)grid->h;
-    td.ncx = (int)nx - 1;
-    td.ncy = (int)ny - 1;
-    td.ncz = (int)nz - 1;
-    td.dtype = dtype;
-    const int k = c->K;
-    rc = cuda_status(cudaMemcpyAsync(c->d_tables + k, &td, sizeof(td), cudaMemcpyHostToDevice, c->stream));
-    if (!rc) {
-        float* dst = c->kf[c->cur] + (size_t)k * kPoseC * c->ld;
-        if (kf_poses) {
-            rc = cuda_status(cudaMemcpyAsync(c->part, kf_poses, sizeof(float) * 12 * (size_t)c->P, cudaMemcpyDefault,
-                                             c->stream));
-            if (!rc) {
-                Launch L(c, K_MISC);
-                launch_aos_to_soa(c->part, c->P, 12, dst, c->ld, c->stream);
-            }
-        } else {
-            rc = cuda_status(cudaMemcpy2DAsync(dst, c->ld * sizeof(float), c->pose[c->cur], c->ld * sizeof(float),
-                                               c->P * sizeof(float), kPoseC, cudaMemcpyDeviceToDevice, c->stream));
-        }
-        if (!rc) rc = check_launch();
-    }
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));   // td lives on this stack frame
-    if (rc) {
-        cudaFree(t.cells);
-        return rc;
-    }
-    {
-        const float d = (float)c->path_now;
-        if (cudaMemcpy(c->d_kf_path + k, &d, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaFree(t.cells);
-            return GMCS_E_CUDA;
-        }
-    }
-    c->kf_path.push_back(c->path_now);
-    c->dev_bytes += t.bytes;
-    c->tables.push_back(t);
-    c->K = k + 1;
-    if (kf_id) *kf_id = k;
-    return GMCS_OK;
+    return register_keyframe(c, t, grid, (int)nx - 1, (int)ny - 1, (int)nz - 1, kf_poses, kf_id);
 }
 
 int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], const double cov[36],
@@ -878,7 +1039,7 @@ int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float*
     float* dm = mom ? (md ? mom : nullptr) : nullptr;
     float* tmp = nullptr;
     if ((g && !gd) || (mom && !md)) {
-        if (cudaMalloc((void**)&tmp, sizeof(float) * 16 * (size_t)c->P) != cudaSuccess) {
+        if (cudaMalloc((void**)&tmp, sizeof(float) * 27 * (size_t)c->P) != cudaSuccess) {
             cudaGetLastError();
             return GMCS_E_OOM;
         }
@@ -890,7 +1051,8 @@ int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float*
     rc = run_pass(c, N, grad, false, dl, dg, dm, nullptr);
     if (!rc && ll && !ld_) rc = copy_out(c, ll, c->ll, sizeof(float) * c->P);
     if (!rc && g && !gd) rc = copy_out(c, g, dg, sizeof(float) * 6 * (size_t)c->P);
-    if (!rc && mom && !md) rc = copy_out(c, mom, dm, sizeof(float) * 10 * (size_t)c->P);
+    const size_t nm = c->cfg.model == GMCS_MODEL_GICP ? 21 : 10;
+    if (!rc && mom && !md) rc = copy_out(c, mom, dm, sizeof(float) * nm * (size_t)c->P);
     if (tmp) {
         cudaStreamSynchronize(c->stream);
         cudaFree(tmp);
@@ -1110,9 +1272,52 @@ int gmcs_get_frame_diag(gmcs_ctx* c, float* ll, double* w, int* anc, int* nbr) {
     return GMCS_OK;
 }
 
+int gmcs_point_covariances(gmcs_ctx* c, const float* pts, int n, double* cov) {
+    if (!c || n < 0 || (n > 0 && (!pts || !cov))) return GMCS_E_INVALID;
+    if (n == 0) return GMCS_OK;
+    const float* dpts = nullptr;
+    float* tmp = nullptr;
+    int rc = stage_points(c, pts, n, &dpts, &tmp);
+    if (rc) return rc;
+    float4* p4 = nullptr;
+    double* dcov = is_device_ptr(cov) ? cov : nullptr;
+    double* tcov = nullptr;
+    if (cudaMalloc((void**)&p4, sizeof(float4) * (size_t)n) != cudaSuccess ||
+        (!dcov && cudaMalloc((void**)&tcov, sizeof(double) * 6 * (size_t)n) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = GMCS_E_OOM;
+    }
+    if (!rc) {
+        if (!dcov) dcov = tcov;
+        {
+            Launch L(c, K_MISC);
+            launch_scan_pack(dpts, n, p4, c->stream);
+        }
+        KnnCovArgs ka;
+        ka.pts = p4;
+        ka.n = n;
+        ka.k = c->cfg.knn;
+        ka.eps = (double)c->cfg.cov_eps;
+        ka.cov64 = dcov;
+        ka.cov32 = nullptr;
+        {
+            Launch L(c, K_MISC);
+            launch_knn_cov(ka, c->stream);
+        }
+        rc = check_launch();
+        if (!rc && tcov) rc = copy_out(c, cov, tcov, sizeof(double) * 6 * (size_t)n);
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(p4);
+    cudaFree(tcov);
+    cudaFree(tmp);
+    return rc ? rc : cuda_status(cudaGetLastError());
+}
+
 int gmcs_get_table(gmcs_ctx* c, int k, float* vals) {
     if (!c || !vals || k < 0 || k >= c->K) return GMCS_E_INVALID;
     const HostTable& t = c->tables[k];
+    if (t.dtype == 3) return copy_out(c, vals, t.cells, t.bytes);   // GICP voxel records as stored
     const size_t nv = (size_t)t.grid.n[0] * t.grid.n[1] * t.grid.n[2];
     const bool dev = is_device_ptr(vals);
     float* dst = dev ? vals : nullptr;

@@ -21,6 +21,7 @@
 //   sum_j d l/d omega = h A^T sum_j (r_j x gu_j)
 // which equals the per-point [p x q; q] summed, since R^T (R p x g) = p x R^T g.
 #include "kernels.h"
+#include "pass.cuh"
 
 namespace gmcs {
 
@@ -302,51 +303,6 @@ __device__ __forceinline__ void add_moments(float w, float4 p, float* acc) {
     acc[14] = fmaf(wy, p.y, acc[14]); acc[15] = fmaf(wy, p.z, acc[15]); acc[16] = fmaf(wz, p.z, acc[16]);
 }
 
-// Map a CTA warp to (particle index, point range, chunk group).
-struct WarpWork {
-    int i, j0, j1, tg, cg;
-};
-
-__device__ __forceinline__ WarpWork warp_work(const PassArgs& a, int vb) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ntg = (a.ntiles + kPassTW - 1) / kPassTW;
-    WarpWork w;
-    w.tg = vb % ntg;
-    w.cg = vb / ntg;
-    const int tile = w.tg * kPassTW + warp % kPassTW;
-    const int chunk = w.cg * kPassCW + warp / kPassTW;
-    w.i = tile * 32 + lane;
-    w.j0 = min(chunk * a.chunk_len, a.N);
-    w.j1 = min(w.j0 + a.chunk_len, a.N);
-    return w;
-}
-
-// CTA partial sums -> scratch [group][acc][particle]; warps sharing a tile add
-// their chunks in a fixed order.
-template <int NACC>
-__device__ __forceinline__ void store_partials(const PassArgs& a, const float* acc, const WarpWork& ww) {
-    if constexpr (kPassCW == 1) {
-        if (ww.i < a.P)
-#pragma unroll
-            for (int e = 0; e < NACC; ++e) a.part[((size_t)ww.cg * NACC + e) * a.ld + ww.i] = acc[e];
-    } else {
-        __shared__ float red[kPassCW][NACC][kPassTW * 32];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int col = (warp % kPassTW) * 32 + lane;
-#pragma unroll
-        for (int e = 0; e < NACC; ++e) red[warp / kPassTW][e][col] = acc[e];
-        __syncthreads();
-        const int base = ww.tg * kPassTW * 32;
-        for (int t = threadIdx.x; t < NACC * kPassTW * 32; t += kPassThreads) {
-            const int e = t / (kPassTW * 32), l = t % (kPassTW * 32);
-            float s = 0.f;
-#pragma unroll
-            for (int c = 0; c < kPassCW; ++c) s += red[c][e][l];
-            if (base + l < a.P) a.part[((size_t)ww.cg * NACC + e) * a.ld + base + l] = s;
-        }
-    }
-}
-
 // Generic pass: any number of neighbour slots, neighbour loop outside the point loop.
 template <int DT, bool GRAD>
 __global__ void __launch_bounds__(kPassThreads, GMCS_PASS_MINBLOCKS) k_pass(PassArgs a) {
@@ -472,24 +428,9 @@ __device__ __forceinline__ void finish_sum(const FinishArgs& a, int i, float* ac
         for (int e = 0; e < NACC; ++e) acc[e] += a.part[((size_t)g * NACC + e) * a.ld + i];
 }
 
-// psi = (H + lambda diag H)^-1 g with H = sigma^-2 [[tr Q I - Q, [S]x], [[S]x^T, W I]],
-// solved by Cholesky after symmetric Jacobi scaling; then clamped.
-__device__ bool gn_step(const float* g, const float* mom, const FinishArgs& a, float* psi) {
-#pragma unroll
-    for (int d = 0; d < 6; ++d) psi[d] = 0.f;
-    const float W = mom[0];
-    if (!(W >= a.w_min)) return false;
-    const float Sx = mom[1], Sy = mom[2], Sz = mom[3];
-    const float Qxx = mom[4], Qxy = mom[5], Qxz = mom[6], Qyy = mom[7], Qyz = mom[8], Qzz = mom[9];
-    const float tr = Qxx + Qyy + Qzz;
-    float H[36] = {
-        tr - Qxx, -Qxy,     -Qxz,     0.f, -Sz, Sy,
-        -Qxy,     tr - Qyy, -Qyz,     Sz,  0.f, -Sx,
-        -Qxz,     -Qyz,     tr - Qzz, -Sy, Sx,  0.f,
-        0.f,      Sz,       -Sy,      W,   0.f, 0.f,
-        -Sz,      0.f,      Sx,       0.f, W,   0.f,
-        Sy,       -Sx,      0.f,      0.f, 0.f, W};
-    const float k = 1.f / (a.sigma * a.sigma);
+// psi = (k H + lambda diag(k H))^-1 g, solved by Cholesky after symmetric
+// Jacobi scaling, then clamped. H is overwritten.
+__device__ bool damped_solve(float* H, float k, const float* g, const FinishArgs& a, float* psi) {
     float D[6], b[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
@@ -548,11 +489,51 @@ __device__ bool gn_step(const float* g, const float* mom, const FinishArgs& a, f
     return true;
 }
 
-template <bool GRAD>
+// Field model: psi = (H + lambda diag H)^-1 g with
+// H = sigma^-2 [[tr Q I - Q, [S]x], [[S]x^T, W I]] from the moments.
+__device__ bool gn_step(const float* g, const float* mom, const FinishArgs& a, float* psi) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) psi[d] = 0.f;
+    const float W = mom[0];
+    if (!(W >= a.w_min)) return false;
+    const float Sx = mom[1], Sy = mom[2], Sz = mom[3];
+    const float Qxx = mom[4], Qxy = mom[5], Qxz = mom[6], Qyy = mom[7], Qyz = mom[8], Qzz = mom[9];
+    const float tr = Qxx + Qyy + Qzz;
+    float H[36] = {
+        tr - Qxx, -Qxy,     -Qxz,     0.f, -Sz, Sy,
+        -Qxy,     tr - Qyy, -Qyz,     Sz,  0.f, -Sx,
+        -Qxz,     -Qyz,     tr - Qzz, -Sy, Sx,  0.f,
+        0.f,      Sz,       -Sy,      W,   0.f, 0.f,
+        -Sz,      0.f,      Sx,       0.f, W,   0.f,
+        Sy,       -Sx,      0.f,      0.f, 0.f, W};
+    return damped_solve(H, 1.f / (a.sigma * a.sigma), g, a, psi);
+}
+
+// GICP model (Eq. 5-6): psi = (H + lambda diag H)^-1 b with H given by its upper
+// triangle (21, row-major).
+__device__ bool gn_step_h(const float* b, const float* hu, const FinishArgs& a, float* psi) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) psi[d] = 0.f;
+    float H[36];
+    int e = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+            H[r * 6 + c] = hu[e];
+            H[c * 6 + r] = hu[e];
+            ++e;
+        }
+    return damped_solve(H, 1.f, b, a, psi);
+}
+
+// GICP: the accumulators are [l, b (6), H upper triangle (21)]; the gradient of
+// l is 2 b where the pose does not move Omega (Eq. 3 has no 1/2).
+template <bool GRAD, bool GICP>
 __device__ __forceinline__ void finish_body(const FinishArgs& a, int vb, int vg) {
     const int i = vb * blockDim.x + threadIdx.x;
     if (i >= a.P) return;
-    constexpr int NACC = GRAD ? kAccGrad : 1;
+    constexpr int NACC = GRAD ? (GICP ? kAccGicp : kAccGrad) : 1;
     float acc[NACC];
     finish_sum<NACC>(a, i, acc);
     if (a.out_ll) a.out_ll[i] = acc[0];
@@ -561,9 +542,11 @@ __device__ __forceinline__ void finish_body(const FinishArgs& a, int vb, int vg)
         return;
     } else {
         if (a.out_g)
-            for (int d = 0; d < 6; ++d) a.out_g[(size_t)i * 6 + d] = acc[1 + d];
-        if (a.out_mom)
-            for (int d = 0; d < 10; ++d) a.out_mom[(size_t)i * 10 + d] = acc[7 + d];
+            for (int d = 0; d < 6; ++d) a.out_g[(size_t)i * 6 + d] = GICP ? 2.f * acc[1 + d] : acc[1 + d];
+        if (a.out_mom) {
+            constexpr int NM = GICP ? 21 : 10;
+            for (int d = 0; d < NM; ++d) a.out_mom[(size_t)i * NM + d] = acc[7 + d];
+        }
         if (a.do_move) {
             // oldest (lowest-index) neighbour keyframe of this particle
             int o = -1;
@@ -573,7 +556,7 @@ __device__ __forceinline__ void finish_body(const FinishArgs& a, int vb, int vg)
             }
             const bool loop = a.loop_recent <= 0 || (o >= 0 && o < a.K - a.loop_recent);
             float psi[6];
-            if (loop && gn_step(acc + 1, acc + 7, a, psi)) {
+            if (loop && (GICP ? gn_step_h(acc + 1, acc + 7, a, psi) : gn_step(acc + 1, acc + 7, a, psi))) {
                 float T[12], E[12], out[12];
                 load_pose(a.pose, a.ld, i, T);
                 se3_exp(psi, E);
@@ -602,9 +585,9 @@ __device__ __forceinline__ void finish_body(const FinishArgs& a, int vb, int vg)
     }
 }
 
-template <bool GRAD>
+template <bool GRAD, bool GICP>
 __global__ void __launch_bounds__(128) k_finish(FinishArgs a) {
-    finish_body<GRAD>(a, blockIdx.x, gridDim.x);
+    finish_body<GRAD, GICP>(a, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ differentiable log-likelihood
@@ -677,9 +660,9 @@ __global__ void __launch_bounds__(kPassThreads, 3) k_pass3_b(const BatchList<Pas
     GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_body<DT, GRAD, UNROLL>(a, vb)));
 }
 
-template <bool GRAD>
+template <bool GRAD, bool GICP>
 __global__ void __launch_bounds__(128) k_finish_b(const BatchList<FinishArgs>* L) {
-    GMCS_BATCH_LOOP(L, const FinishArgs a = L->args[s]; finish_body<GRAD>(a, vb, vg));
+    GMCS_BATCH_LOOP(L, const FinishArgs a = L->args[s]; (finish_body<GRAD, GICP>(a, vb, vg)));
 }
 
 // Persistent grids: every SM filled with as many CTAs as can be resident
@@ -713,9 +696,9 @@ static int grid_pass3_b() {
     static const int g = persistent_grid(k_pass3_b<DT, G, pass3_unroll<DT, G>()>, kPassThreads);
     return g;
 }
-template <bool G>
+template <bool G, bool GICP>
 static int grid_finish_b() {
-    static const int g = persistent_grid(k_finish_b<G>, 128);
+    static const int g = persistent_grid(k_finish_b<G, GICP>, 128);
     return g;
 }
 
@@ -742,9 +725,14 @@ void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStre
     }
 }
 
-void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, cudaStream_t s) {
-    if (grad) k_finish_b<true><<<grid_finish_b<true>(), 128, 0, s>>>(L);
-    else k_finish_b<false><<<grid_finish_b<false>(), 128, 0, s>>>(L);
+void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, bool gicp, cudaStream_t s) {
+    if (gicp) {
+        if (grad) k_finish_b<true, true><<<grid_finish_b<true, true>(), 128, 0, s>>>(L);
+        else k_finish_b<false, true><<<grid_finish_b<false, true>(), 128, 0, s>>>(L);
+    } else {
+        if (grad) k_finish_b<true, false><<<grid_finish_b<true, false>(), 128, 0, s>>>(L);
+        else k_finish_b<false, false><<<grid_finish_b<false, false>(), 128, 0, s>>>(L);
+    }
 }
 
 void prepare_filter_batched() {
@@ -758,8 +746,10 @@ void prepare_filter_batched() {
     grid_pass3_b<0, false>();
     grid_pass3_b<1, false>();
     grid_pass3_b<2, false>();
-    grid_finish_b<true>();
-    grid_finish_b<false>();
+    grid_finish_b<true, false>();
+    grid_finish_b<false, false>();
+    grid_finish_b<true, true>();
+    grid_finish_b<false, true>();
 }
 
 // ------------------------------------------------------------------ launchers
@@ -820,8 +810,14 @@ void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s) {
 
 void launch_finish(const FinishArgs& a, bool grad, cudaStream_t s) {
     if (a.P <= 0) return;
-    if (grad) k_finish<true><<<(a.P + 127) / 128, 128, 0, s>>>(a);
-    else k_finish<false><<<(a.P + 127) / 128, 128, 0, s>>>(a);
+    const int g = (a.P + 127) / 128;
+    if (a.model == 1) {
+        if (grad) k_finish<true, true><<<g, 128, 0, s>>>(a);
+        else k_finish<false, true><<<g, 128, 0, s>>>(a);
+    } else {
+        if (grad) k_finish<true, false><<<g, 128, 0, s>>>(a);
+        else k_finish<false, false><<<g, 128, 0, s>>>(a);
+    }
 }
 
 }  // namespace gmcs

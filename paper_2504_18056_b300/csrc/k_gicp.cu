@@ -1,0 +1,353 @@
+// k_gicp.cu -- the GICP distribution-to-distribution likelihood (Eq. 2-6).
+//
+// Each point carries a Gaussian: its k nearest points of the same cloud give a
+// covariance, plane-regularised as in generalised ICP (eigenvalues replaced by
+// (eps, 1, 1), so only the direction of the smallest eigenvalue -- the surface
+// normal n -- survives: Sigma = I - (1 - eps) n n^T). A keyframe is a dense
+// voxel map: per voxel the mean of its points and the mean of their
+// covariances (the voxel-based correspondence of Sec. III-C1: a transformed
+// scan point corresponds to the voxel it falls in).
+//
+// The lookup pass works in the sensor frame of the particle's current pose:
+// with kT_t = [R | t] and x = R mu + t,
+//   e~ = R^T (mu' - x),  Omega~ = (R^T Sigma' R + Sigma_j)^-1 = R^T Omega R,
+//   d2 = e~^T Omega~ e~   (= e^T Omega e of Eq. 3-4),
+// and the Gauss-Newton terms of Eq. 5-6 for the right perturbation of the
+// current pose, J~ = [-[mu]x | I]:
+//   b += J~^T Omega~ e~ = [mu x q; q],  q = Omega~ e~,
+//   H += J~^T Omega~ J~ = [[-[mu]x Omega~ [mu]x, [mu]x Omega~], [.., Omega~]].
+// Every (point, neighbour) pair adds one term to the log-likelihood: -d2 for an
+// inlier (d2 < tau), -tau when the voxel is empty, outside the map, or d2 >= tau.
+#include <math.h>
+
+#include "kernels.h"
+#include "pass.cuh"
+
+namespace gmcs {
+
+// ------------------------------------------------------------------ covariances
+
+// One Jacobi rotation zeroing A[p][q] of a symmetric 3x3 matrix (r the third
+// index), accumulated into the eigenvector matrix V (Golub & Van Loan, the
+// symmetric Schur decomposition of a 2x2 block).
+template <int p, int q, int r>
+__device__ __forceinline__ void jacobi_rot(double (&A)[3][3], double (&V)[3][3]) {
+    const double apq = A[p][q];
+    if (apq == 0.0) return;
+    const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+    const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+    const double arp = A[r][p], arq = A[r][q];
+    A[r][p] = A[p][r] = c * arp - s * arq;
+    A[r][q] = A[q][r] = s * arp + c * arq;
+    A[p][p] -= t * apq;
+    A[q][q] += t * apq;
+    A[p][q] = A[q][p] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double vp = V[k][p], vq = V[k][q];
+        V[k][p] = c * vp - s * vq;
+        V[k][q] = s * vp + c * vq;
+    }
+}
+
+// Unit eigenvector of the smallest eigenvalue (lowest index on ties) by cyclic Jacobi.
+__device__ __forceinline__ void sym3_min_eigvec(double (&A)[3][3], double n[3]) {
+    double V[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        const double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+        if (!(off > 1e-36 * dia)) break;
+        jacobi_rot<0, 1, 2>(A, V);
+        jacobi_rot<0, 2, 1>(A, V);
+        jacobi_rot<1, 2, 0>(A, V);
+    }
+    int m = 0;
+    if (A[1][1] < A[m][m]) m = 1;
+    if (A[2][2] < A[m][m]) m = 2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n[k] = (m == 0) ? V[k][0] : (m == 1 ? V[k][1] : V[k][2]);
+}
+
+// One thread per point. Candidates stream through shared memory in index order;
+// the k best are kept sorted by squared distance, formed in float as
+// ((dx*dx + dy*dy) + dz*dz) with separate round-to-nearest operations; a
+// candidate replaces an entry only when strictly closer, so ties keep the lower
+// index. The covariance of the k points is taken in FP64 (1/k) and regularised.
+__global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
+    __shared__ float4 tile[128];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < a.n;
+    const float4 p = act ? a.pts[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int k = min(a.k, a.n);
+    float bd[kKnnMax];
+    int bi[kKnnMax];
+#pragma unroll
+    for (int s = 0; s < kKnnMax; ++s) { bd[s] = __int_as_float(0x7f800000); bi[s] = 0; }
+    float worst = __int_as_float(0x7f800000);
+    for (int base = 0; base < a.n; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        if (j < a.n) tile[threadIdx.x] = a.pts[j];
+        __syncthreads();
+        const int m = min((int)blockDim.x, a.n - base);
+        if (act) {
+            for (int t = 0; t < m; ++t) {
+                const float4 q = tile[t];
+                const float dx = __fsub_rn(q.x, p.x), dy = __fsub_rn(q.y, p.y), dz = __fsub_rn(q.z, p.z);
+                const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                if (d2 < worst) {
+                    bool done = false;
+#pragma unroll
+                    for (int s = kKnnMax - 1; s >= 0; --s) {
+                        if (s < k && !done) {
+                            if (s > 0 && bd[s - 1] > d2) {
+                                bd[s] = bd[s - 1];
+                                bi[s] = bi[s - 1];
+                            } else {
+                                bd[s] = d2;
+                                bi[s] = base + t;
+                                done = true;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < kKnnMax; ++s)
+                        if (s == k - 1) worst = bd[s];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!act || k <= 0) return;
+    double mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+    for (int s = 0; s < kKnnMax; ++s) {
+        if (s < k) {
+            const float4 q = a.pts[bi[s]];
+            mx += (double)q.x;
+            my += (double)q.y;
+            mz += (double)q.z;
+        }
+    }
+    mx /= (double)k;
+    my /= (double)k;
+    mz /= (double)k;
+    double C[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+#pragma unroll
+    for (int s = 0; s < kKnnMax; ++s) {
+        if (s < k) {
+            const float4 q = a.pts[bi[s]];
+            const double dx = (double)q.x - mx, dy = (double)q.y - my, dz = (double)q.z - mz;
+            C[0][0] += dx * dx; C[0][1] += dx * dy; C[0][2] += dx * dz;
+            C[1][1] += dy * dy; C[1][2] += dy * dz; C[2][2] += dz * dz;
+        }
+    }
+    const double ik = 1.0 / (double)k;
+    C[0][0] *= ik; C[0][1] *= ik; C[0][2] *= ik; C[1][1] *= ik; C[1][2] *= ik; C[2][2] *= ik;
+    C[1][0] = C[0][1]; C[2][0] = C[0][2]; C[2][1] = C[1][2];
+    double n[3];
+    sym3_min_eigvec(C, n);
+    const double w = 1.0 - a.eps;
+    const double sxx = 1.0 - w * n[0] * n[0], sxy = -w * n[0] * n[1], sxz = -w * n[0] * n[2];
+    const double syy = 1.0 - w * n[1] * n[1], syz = -w * n[1] * n[2], szz = 1.0 - w * n[2] * n[2];
+    if (a.cov64) {
+        double* o = a.cov64 + 6 * (size_t)i;
+        o[0] = sxx; o[1] = sxy; o[2] = sxz; o[3] = syy; o[4] = syz; o[5] = szz;
+    }
+    if (a.cov32) {
+        a.cov32[2 * (size_t)i] = make_float4((float)sxx, (float)sxy, (float)sxz, (float)syy);
+        a.cov32[2 * (size_t)i + 1] = make_float4((float)syz, (float)szz, 0.f, 0.f);
+    }
+}
+
+// ------------------------------------------------------------------ voxel maps
+
+__global__ void k_voxel_accum(VoxelArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float4 p = a.pts[i];
+    const double px = (double)p.x, py = (double)p.y, pz = (double)p.z;
+    const double fx = floor((px - a.ox) / a.h), fy = floor((py - a.oy) / a.h), fz = floor((pz - a.oz) / a.h);
+    if (!(fx >= 0.0 && fx < (double)a.nx && fy >= 0.0 && fy < (double)a.ny && fz >= 0.0 && fz < (double)a.nz))
+        return;
+    const size_t v = ((size_t)fz * a.ny + (size_t)fy) * a.nx + (size_t)fx;
+    double* s = a.sums + 10 * v;
+    atomicAdd(s + 0, px);
+    atomicAdd(s + 1, py);
+    atomicAdd(s + 2, pz);
+    atomicAdd(s + 3, 1.0);
+    const double* c = a.cov + 6 * (size_t)i;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) atomicAdd(s + 4 + e, c[e]);
+}
+
+__global__ void k_voxel_final(VoxelArgs a) {
+    const size_t nv = (size_t)a.nx * a.ny * a.nz;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        const double* s = a.sums + 10 * v;
+        const double cnt = s[3];
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        if (cnt > 0.0) {
+            r0 = make_float4((float)(s[0] / cnt), (float)(s[1] / cnt), (float)(s[2] / cnt), 1.f);
+            r1 = make_float4((float)(s[4] / cnt), (float)(s[5] / cnt), (float)(s[6] / cnt), (float)(s[7] / cnt));
+            r2 = make_float4((float)(s[8] / cnt), (float)(s[9] / cnt), 0.f, 0.f);
+        }
+        a.rec[3 * v] = r0;
+        a.rec[3 * v + 1] = r1;
+        a.rec[3 * v + 2] = r2;
+    }
+}
+
+// ------------------------------------------------------------------ the lookup pass
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
+    constexpr int NACC = GRAD ? kAccGicp : 1;
+    const WarpWork ww = warp_work(a, blockIdx.x);
+    const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
+    float acc[NACC];
+#pragma unroll
+    for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
+
+    if (i < a.P && j0 < j1) {
+        float Tt[12];
+        load_pose(a.pose, a.ld, i, Tt);
+        const float tau = a.tau;
+        float lsum = 0.f;
+        for (int s = 0; s < a.k_nb; ++s) {
+            const int k = a.nbr[(size_t)s * a.ld + i];
+            if (k < 0) continue;
+            const TableDesc td = a.tables[k];
+            float Tk[12], rel[12];
+            load_pose(a.kf + (size_t)k * kPoseC * a.ld, a.ld, i, Tk);
+            pose_rel(Tk, Tt, rel);
+            const float R00 = rel[0], R01 = rel[1], R02 = rel[2], t0 = rel[3];
+            const float R10 = rel[4], R11 = rel[5], R12 = rel[6], t1 = rel[7];
+            const float R20 = rel[8], R21 = rel[9], R22 = rel[10], t2 = rel[11];
+            const float4* __restrict__ recs = reinterpret_cast<const float4*>(td.cells);
+            const uint32_t ncx = (uint32_t)td.ncx, ncy = (uint32_t)td.ncy, ncz = (uint32_t)td.ncz;
+            for (int j = j0; j < j1; ++j) {
+                const float4 p = __ldg(a.scan + j);
+                const float x0 = fmaf(R00, p.x, fmaf(R01, p.y, fmaf(R02, p.z, t0)));
+                const float x1 = fmaf(R10, p.x, fmaf(R11, p.y, fmaf(R12, p.z, t1)));
+                const float x2 = fmaf(R20, p.x, fmaf(R21, p.y, fmaf(R22, p.z, t2)));
+                const int cx = (int)floorf((x0 - td.ox) * td.inv_h);
+                const int cy = (int)floorf((x1 - td.oy) * td.inv_h);
+                const int cz = (int)floorf((x2 - td.oz) * td.inv_h);
+                const bool inside = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+                float4 m = make_float4(0.f, 0.f, 0.f, 0.f), v0 = m, v1 = m;
+                if (inside) {
+                    const size_t idx = ((size_t)cz * ncy + (size_t)cy) * ncx + (size_t)cx;
+                    m = __ldg(recs + 3 * idx);
+                    v0 = __ldg(recs + 3 * idx + 1);
+                    v1 = __ldg(recs + 3 * idx + 2);
+                }
+                if (!(m.w > 0.f)) {
+                    lsum -= tau;
+                    continue;
+                }
+                // residual in the sensor frame: e~ = R^T (mu' - x)
+                const float e0 = m.x - x0, e1 = m.y - x1, e2 = m.z - x2;
+                const float f0 = fmaf(R00, e0, fmaf(R10, e1, R20 * e2));
+                const float f1 = fmaf(R01, e0, fmaf(R11, e1, R21 * e2));
+                const float f2 = fmaf(R02, e0, fmaf(R12, e1, R22 * e2));
+                // Sigma' R (columns c of R), then R^T (Sigma' R): the map covariance in the sensor frame
+                const float Sxx = v0.x, Sxy = v0.y, Sxz = v0.z, Syy = v0.w, Syz = v1.x, Szz = v1.y;
+                const float M00 = fmaf(Sxx, R00, fmaf(Sxy, R10, Sxz * R20));
+                const float M01 = fmaf(Sxx, R01, fmaf(Sxy, R11, Sxz * R21));
+                const float M02 = fmaf(Sxx, R02, fmaf(Sxy, R12, Sxz * R22));
+                const float M10 = fmaf(Sxy, R00, fmaf(Syy, R10, Syz * R20));
+                const float M11 = fmaf(Sxy, R01, fmaf(Syy, R11, Syz * R21));
+                const float M12 = fmaf(Sxy, R02, fmaf(Syy, R12, Syz * R22));
+                const float M20 = fmaf(Sxz, R00, fmaf(Syz, R10, Szz * R20));
+                const float M21 = fmaf(Sxz, R01, fmaf(Syz, R11, Szz * R21));
+                const float M22 = fmaf(Sxz, R02, fmaf(Syz, R12, Szz * R22));
+                const float4 c0 = __ldg(a.scov + 2 * j), c1 = __ldg(a.scov + 2 * j + 1);
+                const float a00 = fmaf(R00, M00, fmaf(R10, M10, fmaf(R20, M20, c0.x)));
+                const float a01 = fmaf(R00, M01, fmaf(R10, M11, fmaf(R20, M21, c0.y)));
+                const float a02 = fmaf(R00, M02, fmaf(R10, M12, fmaf(R20, M22, c0.z)));
+                const float a11 = fmaf(R01, M01, fmaf(R11, M11, fmaf(R21, M21, c0.w)));
+                const float a12 = fmaf(R01, M02, fmaf(R11, M12, fmaf(R21, M22, c1.x)));
+                const float a22 = fmaf(R02, M02, fmaf(R12, M12, fmaf(R22, M22, c1.y)));
+                // Omega~ = C^-1 by cofactors
+                const float i00 = fmaf(a11, a22, -a12 * a12);
+                const float i01 = fmaf(a02, a12, -a01 * a22);
+                const float i02 = fmaf(a01, a12, -a02 * a11);
+                const float i11 = fmaf(a00, a22, -a02 * a02);
+                const float i12 = fmaf(a01, a02, -a00 * a12);
+                const float i22 = fmaf(a00, a11, -a01 * a01);
+                const float det = fmaf(a00, i00, fmaf(a01, i01, a02 * i02));
+                const float rd = 1.f / det;
+                const float o00 = i00 * rd, o01 = i01 * rd, o02 = i02 * rd;
+                const float o11 = i11 * rd, o12 = i12 * rd, o22 = i22 * rd;
+                const float q0 = fmaf(o00, f0, fmaf(o01, f1, o02 * f2));
+                const float q1 = fmaf(o01, f0, fmaf(o11, f1, o12 * f2));
+                const float q2 = fmaf(o02, f0, fmaf(o12, f1, o22 * f2));
+                const float d2 = fmaf(f0, q0, fmaf(f1, q1, f2 * q2));
+                if (!(d2 < tau)) {
+                    lsum -= tau;
+                    continue;
+                }
+                lsum -= d2;
+                if constexpr (GRAD) {
+                    // b = [mu x q; q]
+                    acc[1] += fmaf(p.y, q2, -p.z * q1);
+                    acc[2] += fmaf(p.z, q0, -p.x * q2);
+                    acc[3] += fmaf(p.x, q1, -p.y * q0);
+                    acc[4] += q0;
+                    acc[5] += q1;
+                    acc[6] += q2;
+                    // K = [mu]x Omega~ (rows: -mz O1 + my O2, mz O0 - mx O2, -my O0 + mx O1)
+                    const float K00 = fmaf(-p.z, o01, p.y * o02), K01 = fmaf(-p.z, o11, p.y * o12),
+                                K02 = fmaf(-p.z, o12, p.y * o22);
+                    const float K10 = fmaf(p.z, o00, -p.x * o02), K11 = fmaf(p.z, o01, -p.x * o12),
+                                K12 = fmaf(p.z, o02, -p.x * o22);
+                    const float K20 = fmaf(-p.y, o00, p.x * o01), K21 = fmaf(-p.y, o01, p.x * o11),
+                                K22 = fmaf(-p.y, o02, p.x * o12);
+                    // rotation block -K [mu]x: (K [mu]x)[r] = (K_r1 mz - K_r2 my, K_r2 mx - K_r0 mz, K_r0 my - K_r1 mx)
+                    acc[7] -= fmaf(K01, p.z, -K02 * p.y);
+                    acc[8] -= fmaf(K02, p.x, -K00 * p.z);
+                    acc[9] -= fmaf(K00, p.y, -K01 * p.x);
+                    acc[13] -= fmaf(K12, p.x, -K10 * p.z);
+                    acc[14] -= fmaf(K10, p.y, -K11 * p.x);
+                    acc[18] -= fmaf(K20, p.y, -K21 * p.x);
+                    // cross block K
+                    acc[10] += K00; acc[11] += K01; acc[12] += K02;
+                    acc[15] += K10; acc[16] += K11; acc[17] += K12;
+                    acc[19] += K20; acc[20] += K21; acc[21] += K22;
+                    // translation block Omega~
+                    acc[22] += o00; acc[23] += o01; acc[24] += o02;
+                    acc[25] += o11; acc[26] += o12; acc[27] += o22;
+                }
+            }
+        }
+        acc[0] = lsum;
+    }
+    store_partials<NACC>(a, acc, ww);
+}
+
+// ------------------------------------------------------------------ launchers
+
+void launch_knn_cov(const KnnCovArgs& a, cudaStream_t s) {
+    if (a.n > 0) k_knn_cov<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+}
+
+void launch_voxel_accum(const VoxelArgs& a, cudaStream_t s) {
+    if (a.n > 0) k_voxel_accum<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+}
+
+void launch_voxel_final(const VoxelArgs& a, cudaStream_t s) {
+    const size_t nv = (size_t)a.nx * a.ny * a.nz;
+    size_t b = (nv + 255) / 256;
+    if (b > 148 * 32) b = 148 * 32;
+    if (nv > 0) k_voxel_final<<<(int)b, 256, 0, s>>>(a);
+}
+
+void launch_gicp_pass(const PassArgs& a, bool grad, cudaStream_t s) {
+    const int grid = grid_pass(a);
+    if (grid <= 0) return;
+    if (grad) k_gicp<true><<<grid, kPassThreads, 0, s>>>(a);
+    else k_gicp<false><<<grid, kPassThreads, 0, s>>>(a);
+}
+
+}  // namespace gmcs

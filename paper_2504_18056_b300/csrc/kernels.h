@@ -18,6 +18,7 @@ constexpr int kPassTW = GMCS_TW;
 constexpr int kPassCW = kPassWarps / kPassTW;
 static_assert(kPassTW * kPassCW == kPassWarps, "tile x chunk split of the CTA");
 constexpr int kAccGrad = 17;            // ll, d ll/d omega (3), d ll/d v (3), moments (10)
+constexpr int kAccGicp = 28;            // GICP: ll, b (6), H upper triangle (21)
 constexpr int kMaxGroups = 8;           // point-chunk groups per particle tile (scratch bound)
 
 // ------------------------------------------------------------------ tables
@@ -78,6 +79,9 @@ struct PassArgs {
     const int* nbr;
     const TableDesc* tables;
     const float4* scan;
+    const float4* scov;     // GICP: 2 float4 per point, covariance xx xy xz yy | yz zz - -
+    float tau;              // GICP: cap of a term's e^T Omega e
+    int model;              // 0 voxel likelihood field, 1 GICP
     float* part;            // [groups][nacc][ld]
     size_t ld;
     int P, N, k_nb;
@@ -102,6 +106,7 @@ struct FinishArgs {
     const float* kf_path;   // K odometry path lengths
     float path_now;
     int K, k_nb, propagate, loop_recent;
+    int model;              // 0 voxel likelihood field, 1 GICP
 };
 
 // Differentiable log-likelihood: poses T0 exp(xi) and the chain rule through Jr(xi).
@@ -114,6 +119,29 @@ void launch_soa_to_aos(const float* soa, size_t ld, int P, int C, float* aos, cu
 void launch_predict(const PredictArgs& a, cudaStream_t s);
 void launch_select(const SelectArgs& a, cudaStream_t s);
 void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s);
+void launch_gicp_pass(const PassArgs& a, bool grad, cudaStream_t s);
+
+// GICP keyframe maps and scan covariances (k_gicp.cu).
+struct KnnCovArgs {
+    const float4* pts;      // n points (x, y, z, -)
+    int n, k;               // k nearest (the point itself included), k <= kKnnMax
+    double eps;             // plane regularisation: eigenvalues (eps, 1, 1)
+    double* cov64;          // optional n x 6 doubles (xx xy xz yy yz zz)
+    float4* cov32;          // optional 2 float4 per point (xx xy xz yy | yz zz 0 0)
+};
+constexpr int kKnnMax = 32;
+void launch_knn_cov(const KnnCovArgs& a, cudaStream_t s);
+struct VoxelArgs {
+    const float4* pts;
+    const double* cov;      // n x 6
+    int n;
+    double ox, oy, oz, h;
+    int nx, ny, nz;
+    double* sums;           // voxels x 10: sum p (3), count, sum cov (6)
+    float4* rec;            // voxels x 3 float4: mean + valid | xx xy xz yy | yz zz 0 0
+};
+void launch_voxel_accum(const VoxelArgs& a, cudaStream_t s);
+void launch_voxel_final(const VoxelArgs& a, cudaStream_t s);
 void launch_finish(const FinishArgs& a, bool grad, cudaStream_t s);
 
 // ------------------------------------------------------------------ weights / resampling
@@ -243,7 +271,7 @@ void launch_scan_pack_b(const BatchList<ScanPackArgs>* L, cudaStream_t s);
 void launch_predict_b(const BatchList<PredictArgs>* L, cudaStream_t s);
 void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s);
 void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStream_t s);
-void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, cudaStream_t s);
+void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, bool gicp, cudaStream_t s);
 void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s);
 void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s);
 void launch_scan_totals_b(const BatchList<TotalsArgs>* L, cudaStream_t s);

@@ -160,10 +160,10 @@ int capture_graph(gmcs_server* s, TickSet& t) {
     launch_select_b(&d->sel, st);
     for (int k = 0; k < s->cfg.steps; ++k) {
         launch_pass3_b(&d->pgrad, s->cfg.table_dtype, true, st);
-        launch_finish_b(&d->fgrad, true, st);
+        launch_finish_b(&d->fgrad, true, false, st);
     }
     launch_pass3_b(&d->pval, s->cfg.table_dtype, false, st);
-    launch_finish_b(&d->fval, false, st);
+    launch_finish_b(&d->fval, false, false, st);
     launch_weigh_b(&d->weigh, st);
     if (s->cfg.resample == GMCS_RESAMPLE_PRUNE) {
         launch_prune_mark_b(&d->prune, st);
@@ -329,7 +329,8 @@ extern "C" {
 int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_sessions, gmcs_server** out) {
     if (!out) return GMCS_E_INVALID;
     *out = nullptr;
-    if (!cfg || budget_bytes == 0 || max_sessions <= 0 || cfg->k_nb != 3 || cfg->steps < 0 || cfg->steps > 64)
+    if (!cfg || budget_bytes == 0 || max_sessions <= 0 || cfg->k_nb != 3 || cfg->steps < 0 || cfg->steps > 64 ||
+        cfg->model != GMCS_MODEL_FIELD)
         return GMCS_E_INVALID;
     gmcs_server* s = new (std::nothrow) gmcs_server();
     if (!s) return GMCS_E_OOM;
