@@ -35,6 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "particle×point lik+grad evals/s; frame update ms @100k particles; p50/p99"
 UNIT = "evals/s"
 FLOPS_GRAD_LOOKUP = 87          # FP32 flops of one gradient lookup (FMA = 2); breakdown in the design doc
+# GICP model: FP32 flops (FMA = 2) of an inlier lookup with the Gauss-Newton terms,
+# and of a lookup that stops at an empty voxel (transform and cell only)
+FLOPS_GICP_INLIER = 255
+FLOPS_GICP_MISS = 24
+GICP_VOXEL = 1.0                # m, voxel edge of the GICP keyframe maps
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes read + written per gradient-pass launch, from one ncu capture of the
 # current kernel at the same particle and point counts (profiles/); None when stale
@@ -51,6 +56,8 @@ def parse():
     ap.add_argument("--points", type=int, default=2048)
     ap.add_argument("--keyframes", type=int, default=20)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--model", default="field", choices=["field", "gicp"],
+                    help="likelihood: voxel field (the benchmark's) or GICP distribution-to-distribution (Eq. 2-6)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-particles", type=int, default=1024, help="oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -168,11 +175,13 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_prepare(w, n_particles):
+def oracle_prepare(w, n_particles, model="field"):
     """FP64 oracle state for the first n_particles of the workload, with tables
-    for every keyframe a sampled particle can select (an empty 2x2x2 lattice far
-    away, which every lookup misses, stands in for the others)."""
+    (GICP: voxel maps) for every keyframe a sampled particle can select (an
+    empty 2x2x2 lattice far away, which every lookup misses, stands in for the
+    others)."""
     import oracle
+    import synth
     P = n_particles
     K = len(w["keyframes"])
     poses = w["particles"][:P].astype(np.float64)
@@ -183,32 +192,43 @@ def oracle_prepare(w, n_particles):
     need = set(np.nonzero((dist <= third[:, None] + 3.0).any(axis=0))[0].tolist())
     tables, grids = [], []
     for k, kf in enumerate(w["keyframes"]):
-        if k in need:
+        if k in need and model == "gicp":
+            grid = synth.grid_for_points(kf["points"], GICP_VOXEL, 1.0)
+            tables.append(oracle.gicp_voxel_map(kf["points"], oracle.knn_cov(kf["points"], 10), grid))
+            grids.append(grid)
+        elif k in need:
             tables.append(oracle.build_table(kf["points"], kf["grid"], 0.2, 1.0))
             grids.append(kf["grid"])
         else:
-            tables.append(np.zeros((2, 2, 2)))
-            grids.append({"origin": np.array([1e6, 1e6, 1e6]), "h": 1.0, "dims": (2, 2, 2)})
+            tables.append(np.zeros((1, 10)) if model == "gicp" else np.zeros((2, 2, 2)))
+            grids.append({"origin": np.array([1e6, 1e6, 1e6]), "h": 1.0,
+                          "dims": (1, 1, 1) if model == "gicp" else (2, 2, 2)})
     return oracle.State(poses, kfp, tables, grids)
 
 
-def oracle_frames(st, w, frames, first=0):
-    """Seconds of each whole oracle frame (single thread) on the prepared sample."""
+def oracle_frames(st, w, frames, first=0, model="field"):
+    """Seconds of each whole oracle frame (single thread) on the prepared sample
+    (GICP: the scan covariances are part of the frame)."""
+    import oracle
     out = []
     for fr in range(first, first + frames):
         t0 = time.perf_counter()
-        st.step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=fr)
+        if model == "gicp":
+            st.step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=fr, scov=oracle.knn_cov(w["scans"][fr], 10),
+                    model=1)
+        else:
+            st.step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=fr)
         out.append(time.perf_counter() - t0)
     return np.array(out)
 
 
-def oracle_sample(w, n_particles, frames=1):
+def oracle_sample(w, n_particles, frames=1, model="field"):
     """Evals per second of the oracle's whole frame on a particle sample."""
-    st = oracle_prepare(w, n_particles)
-    dt = oracle_frames(st, w, frames).sum()
+    st = oracle_prepare(w, n_particles, model)
+    dt = oracle_frames(st, w, frames, model=model).sum()
     N = w["scans"][0].shape[0]
     evals = n_particles * N * 3 * frames
-    desc = (f"FP64 oracle, whole frame on the first {n_particles} particles of the same session "
+    desc = (f"FP64 oracle ({model} model), whole frame on the first {n_particles} particles of the same session "
             f"({N} points, {len(w['keyframes'])} keyframes, 3 moves), {frames} frame(s), single thread")
     return evals / dt, dt, desc
 
@@ -228,11 +248,14 @@ def run_native(a, world, rank, local):
                               n_frames=frames)
     P, N, K = a.particles, a.points, a.keyframes
     dtype = {"f32": 0, "bf16": 1, "f16": 2}[a.dtype]
+    gicp = a.model == "gicp"
     stream = torch.cuda.current_stream(dev)
-    f = g.Filter(P, K, N, stream=stream.cuda_stream, table_dtype=dtype, seed=rank)
+    f = g.Filter(P, K, N, stream=stream.cuda_stream, table_dtype=dtype, seed=rank,
+                 model=g.MODEL_GICP if gicp else g.MODEL_FIELD)
     f.init_particles(w["particles"])
     for k, kf in enumerate(w["keyframes"]):
-        f.add_keyframe(kf["points"], kf["grid"], w["kf_particle_poses"][k])
+        grid = synth.grid_for_points(kf["points"], GICP_VOXEL, 1.0) if gicp else kf["grid"]
+        f.add_keyframe(kf["points"], grid, w["kf_particle_poses"][k])
     scans_d = [torch.from_numpy(s).to(dev) for s in w["scans"]]
     flush = None if a.no_flush else torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     torch.cuda.synchronize()
@@ -273,6 +296,12 @@ def run_native(a, world, rank, local):
     e2e_s = time.perf_counter() - t0
     assert out["status"] == 0
     dev_bytes = f.device_bytes()
+    inlier_frac = None
+    if gicp:
+        # share of lookups that reach a distribution and pass the cap, at the final state
+        mom = torch.zeros((P, 22), dtype=torch.float32, device=dev)
+        f.eval(scans_d[a.warmup + a.steps - 1], None, None, mom)
+        inlier_frac = float(mom[:, 21].sum().item()) / (float(P) * N * 3)
     f.close()
 
     total_ms = float(step_ms.sum())
@@ -288,8 +317,13 @@ def run_native(a, world, rank, local):
     lookups_per_launch = float(P) * N * 3
     rec_bytes = 32 if dtype == 0 else 16
     avg_ms = pg["ms"] / max(pg["launches"], 1)
-    # algorithmic work of one gradient lookup: 87 FP32 flops (FMA = 2), one cell record read
-    flops_per_launch = lookups_per_launch * FLOPS_GRAD_LOOKUP
+    # algorithmic work of one gradient lookup: 87 FP32 flops (FMA = 2), one cell record read;
+    # GICP: 255 per inlier, 24 per lookup that stops early, 48 B voxel record per lookup
+    if gicp:
+        flops_per_launch = lookups_per_launch * (inlier_frac * FLOPS_GICP_INLIER + (1 - inlier_frac) * FLOPS_GICP_MISS)
+        rec_bytes = 48
+    else:
+        flops_per_launch = lookups_per_launch * FLOPS_GRAD_LOOKUP
     achieved_tflops = flops_per_launch / (avg_ms / 1e3) / 1e12
     gather_gbs = lookups_per_launch * rec_bytes / (avg_ms / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -312,7 +346,9 @@ def run_native(a, world, rank, local):
                  "; f64 weights",
         "data": "synthetic (seeded procedural corridor + trunk scene, 64x1024 lidar ray-cast)",
         "config": {"workload": f"single session, {P} particles x {N}-point scans x {K} keyframes "
-                               f"(8192 pts, 0.2 m lattice), 3 neighbour keyframes, 3 moves/frame",
+                               + ("(8192 pts, GICP voxel maps at 1 m, knn 10)" if gicp else "(8192 pts, 0.2 m lattice)")
+                               + ", 3 neighbour keyframes, 3 moves/frame",
+                   "model": a.model,
                    "particles": P, "points": N, "keyframes": K, "k_nb": 3, "moves": 3,
                    "table": a.dtype, "l2": "flushed before every timed step (256 MB write)" if not a.no_flush
                    else "not flushed", "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -320,9 +356,11 @@ def run_native(a, world, rank, local):
                      "min": float(step_ms.min()), "max": float(step_ms.max())},
         "lookups_per_s": float(P) * N * 3 * 4 * a.steps * world / (max_ms / 1e3),
         "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in kinds.items() if v["launches"]},
-        "roofline": {"kernel": "k_pass3 gradient pass (lookup + gradient + moments)", "bound": "alu",
+        "roofline": {"kernel": "k_gicp gradient pass (GICP terms + Gauss-Newton matrix)" if gicp else
+                               "k_pass3 gradient pass (lookup + gradient + moments)", "bound": "alu",
                      "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(a.dtype),
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                     "traffic": None if gicp else TRAFFIC_PER_LAUNCH.get(a.dtype), "gicp_inlier_frac": inlier_frac,
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz",
                      "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms},
         "gather": {"algorithmic_bytes_per_launch": lookups_per_launch * rec_bytes, "achieved_gbs": gather_gbs,
@@ -338,7 +376,7 @@ def run_native(a, world, rank, local):
         "timed_kernel_share": timed_kernel_ms / total_ms if total_ms > 0 else None,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        v, dt, desc = oracle_sample(w, min(a.cpu_particles, P))
+        v, dt, desc = oracle_sample(w, min(a.cpu_particles if not gicp else a.cpu_particles // 4, P), model=a.model)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "seconds": dt}
     if world > 1:

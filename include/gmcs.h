@@ -239,7 +239,8 @@ int gmcs_select(gmcs_ctx* ctx, int* nbr_out);
  * GICP model (Eq. 3-6): ll = sum_{j,k} -min(e^T Omega e, gicp_tau) (gicp_tau for
  * points without a voxel), g = 2 b with b = sum J^T Omega e over the inliers
  * (the gradient of ll where Omega does not move with the pose), and mom = the
- * upper triangle of H = sum J^T Omega J, row-major (P x 21 floats).
+ * upper triangle of H = sum J^T Omega J, row-major, then the number of inlier
+ * lookups (P x 22 floats).
  * Any output may be NULL; outputs are host or device (host: synchronises).
  */
 int gmcs_eval(gmcs_ctx* ctx, const float* scan, int N, float* ll, float* g, float* mom);

@@ -364,7 +364,7 @@ def gicp_voxel_map(points, covs, grid):
     return rec
 
 
-def gicp_eval(T, kf_poses, maps, grids, scan, scov, tau=20.0, face_delta=1e-3):
+def gicp_eval(T, kf_poses, maps, grids, scan, scov, tau=20.0, face_delta=1e-3, gate_delta=0.0):
     """ora_gicp_eval_particle: ll, b (6), H (6 x 6), slack (3), valid lookups."""
     n_nb = len(kf_poses)
     Tk = np.ascontiguousarray(np.asarray(kf_poses, np.float64).reshape(n_nb, 12))
@@ -376,7 +376,8 @@ def gicp_eval(T, kf_poses, maps, grids, scan, scov, tau=20.0, face_delta=1e-3):
     T, pT = _d(np.asarray(T).reshape(12))
     ll = C.c_double(); b = np.zeros(6); H = np.zeros(36); sl = np.zeros(3); nv = C.c_int()
     lib().ora_gicp_eval_particle(pT, C.c_int(n_nb), Tk.ctypes.data_as(_dp), mp, grs, ps, psc,
-                                 C.c_int(scan.shape[0]), C.c_double(tau), C.c_double(face_delta), C.byref(ll),
+                                 C.c_int(scan.shape[0]), C.c_double(tau), C.c_double(face_delta),
+                                 C.c_double(gate_delta), C.byref(ll),
                                  b.ctypes.data_as(_dp), H.ctypes.data_as(_dp), sl.ctypes.data_as(_dp), C.byref(nv))
     return {"ll": ll.value, "b": b, "H": H.reshape(6, 6), "slack": sl, "nvalid": nv.value}
 

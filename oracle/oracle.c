@@ -559,10 +559,11 @@ static int inv3(const double A[9], double B[9]) {
 }
 
 /* One correspondence: voxel record vox (mean, count, covariance), scan point mu
- * with covariance S (6), relative pose rel. Returns 0 when the voxel is empty. */
-static int gicp_term(const double* vox, const double rel[12], const double mu[3], const double* S, double tau,
-                     double* l, double bj[6], double Hj[36]) {
-    *l = -tau;
+ * with covariance S (6), relative pose rel. Writes d2 = e^T Omega e and the
+ * term's b and H; returns 0 (and zeros) when there is no distribution. */
+static int gicp_dist(const double* vox, const double rel[12], const double mu[3], const double* S,
+                     double* d2out, double bj[6], double Hj[36]) {
+    *d2out = 0.0;
     for (int d = 0; d < 6; ++d) bj[d] = 0.0;
     for (int d = 0; d < 36; ++d) Hj[d] = 0.0;
     if (!vox || !(vox[3] > 0.0)) return 0;
@@ -582,9 +583,7 @@ static int gicp_term(const double* vox, const double rel[12], const double mu[3]
     if (!inv3(C, Om)) return 0;
     double Oe[3];
     for (int r = 0; r < 3; ++r) Oe[r] = Om[r * 3] * e[0] + Om[r * 3 + 1] * e[1] + Om[r * 3 + 2] * e[2];
-    double d2 = e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
-    if (!(d2 < tau)) return 0;                      /* outlier: the capped term, no gradient */
-    *l = -d2;                                       /* Eq. 3 */
+    *d2out = e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];     /* Eq. 3: the term is -d2 */
     /* J = d(kT_t exp(xi) mu)/d xi = R [-[mu]x | I]  (3 x 6) */
     double M[9], J[18];
     hat(mu, M);
@@ -602,9 +601,25 @@ static int gicp_term(const double* vox, const double rel[12], const double mu[3]
     return 1;
 }
 
+/* The capped term: an inlier (a distribution and d2 < tau) adds -d2, b, H;
+ * anything else adds -tau and no gradient. Returns 1 for an inlier. */
+static int gicp_term(const double* vox, const double rel[12], const double mu[3], const double* S, double tau,
+                     double* l, double bj[6], double Hj[36], double* d2, int* has) {
+    *has = gicp_dist(vox, rel, mu, S, d2, bj, Hj);
+    if (*has && *d2 < tau) {
+        *l = -*d2;
+        return 1;
+    }
+    *l = -tau;
+    for (int d = 0; d < 6; ++d) bj[d] = 0.0;
+    for (int d = 0; d < 36; ++d) Hj[d] = 0.0;
+    return 0;
+}
+
 void ora_gicp_eval_particle(const double Tt[12], int n_nb, const double* Tk, const double* const* maps,
                             const ora_grid* grids, const float* scan, const double* scov, int N, double tau,
-                            double face_delta, double* ll, double b[6], double H[36], double slack[3], int* nvalid) {
+                            double face_delta, double gate_delta, double* ll, double b[6], double H[36],
+                            double slack[3], int* nvalid) {
     double acc_l = 0.0, acc_b[6] = {0}, acc_H[36] = {0}, sl[3] = {0, 0, 0};
     int nv = 0;
     for (int s = 0; s < n_nb; ++s) {
@@ -623,10 +638,22 @@ void ora_gicp_eval_particle(const double Tt[12], int n_nb, const double* Tk, con
                 c[r] = (int)floor(u[r]);
                 if (c[r] < 0 || c[r] >= g->n[r]) inside = 0;
             }
-            double l, bj[6], Hj[36];
+            double l, bj[6], Hj[36], d2;
+            int has;
             int ok = gicp_term(inside ? map + 10 * vidx(g, c[0], c[1], c[2]) : NULL, rel, mu, scov + 6 * (size_t)j,
-                               tau, &l, bj, Hj);
+                               tau, &l, bj, Hj, &d2, &has);
             nv += ok;
+            if (slack && has && fabs(d2 - tau) < gate_delta * tau) {
+                /* at the cap, a different rounding of d2 flips the term in or out */
+                double bg[6], Hg[36], dd;
+                gicp_dist(map + 10 * vidx(g, c[0], c[1], c[2]), rel, mu, scov + 6 * (size_t)j, &dd, bg, Hg);
+                double nb = 0.0, nH = 0.0;
+                for (int d = 0; d < 6; ++d) nb += bg[d] * bg[d];
+                for (int d = 0; d < 36; ++d) nH += Hg[d] * Hg[d];
+                sl[0] += fabs(dd - tau);
+                sl[1] += sqrt(nb);
+                sl[2] += sqrt(nH);
+            }
             acc_l += l;
             for (int d = 0; d < 6; ++d) acc_b[d] += bj[d];
             for (int d = 0; d < 36; ++d) acc_H[d] += Hj[d];
@@ -645,9 +672,10 @@ void ora_gicp_eval_particle(const double Tt[12], int n_nb, const double* Tk, con
                     int in2 = 1;
                     for (int r = 0; r < 3; ++r)
                         if (c2[r] < 0 || c2[r] >= g->n[r]) in2 = 0;
-                    double l2, b2[6], H2[36];
+                    double l2, b2[6], H2[36], dd2;
+                    int has2;
                     gicp_term(in2 ? map + 10 * vidx(g, c2[0], c2[1], c2[2]) : NULL, rel, mu, scov + 6 * (size_t)j,
-                              tau, &l2, b2, H2);
+                              tau, &l2, b2, H2, &dd2, &has2);
                     double db = 0.0, dH = 0.0;
                     for (int d = 0; d < 6; ++d) db += (b2[d] - bj[d]) * (b2[d] - bj[d]);
                     for (int d = 0; d < 36; ++d) dH += (H2[d] - Hj[d]) * (H2[d] - Hj[d]);
@@ -904,7 +932,7 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
                 if (sp->model == 1) {
                     double Hg[36];
                     ora_gicp_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, scov, N, sp->gicp_tau,
-                                           sp->face_delta, NULL, g, Hg, NULL, NULL);
+                                           sp->face_delta, 0.0, NULL, g, Hg, NULL, NULL);
                     ora_move_h(poses + 12 * (size_t)i, g, Hg, &mp, poses + 12 * (size_t)i, psi);
                 } else {
                     ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
@@ -922,7 +950,7 @@ void ora_step(int P, int K, double* poses, double* kf_poses, double* logw,
                 }
             } else if (sp->model == 1) {
                 ora_gicp_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, scov, N, sp->gicp_tau,
-                                       sp->face_delta, ll + i, NULL, NULL, NULL, NULL);
+                                       sp->face_delta, 0.0, ll + i, NULL, NULL, NULL, NULL);
             } else {
                 ora_eval_particle(poses + 12 * (size_t)i, k_nb, Tk, tabs, grs, scan, N, &ep,
                                   ll + i, NULL, NULL, NULL, NULL, NULL, 0);

@@ -127,11 +127,14 @@ void ora_move_h(const double Tt[12], const double b[6], const double H[36], cons
  * otherwise (no voxel, empty voxel, or d2 >= tau) ll += -tau and nothing else
  * (the step psi = H^-1 b ascends ll). slack[3]: summed over lookups whose
  * coordinate lies within face_delta voxels of a face, |change| of the term's
- * ll, b (norm) and H (Frobenius) when the voxel across that face is used.
+ * ll, b (norm) and H (Frobenius) when the voxel across that face is used; and
+ * over lookups with |d2 - tau| < gate_delta tau, |d2 - tau| and the norms of
+ * the term's b and H (the cap decides them at the rounding level).
  * nvalid: inlier lookups. Any output may be NULL. */
 void ora_gicp_eval_particle(const double Tt[12], int n_nb, const double* Tk, const double* const* maps,
                             const ora_grid* grids, const float* scan, const double* scov, int N, double tau,
-                            double face_delta, double* ll, double b[6], double H[36], double slack[3], int* nvalid);
+                            double face_delta, double gate_delta, double* ll, double b[6], double H[36],
+                            double slack[3], int* nvalid);
 
 /* ---- keyframe pose propagation, Eq. 8-10: with o the oldest (lowest-index)
  * neighbour keyframe, every keyframe k > o moves by T_k exp(r_k psi),

@@ -1039,7 +1039,7 @@ int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float*
     float* dm = mom ? (md ? mom : nullptr) : nullptr;
     float* tmp = nullptr;
     if ((g && !gd) || (mom && !md)) {
-        if (cudaMalloc((void**)&tmp, sizeof(float) * 27 * (size_t)c->P) != cudaSuccess) {
+        if (cudaMalloc((void**)&tmp, sizeof(float) * 28 * (size_t)c->P) != cudaSuccess) {
             cudaGetLastError();
             return GMCS_E_OOM;
         }
@@ -1051,7 +1051,7 @@ int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float*
     rc = run_pass(c, N, grad, false, dl, dg, dm, nullptr);
     if (!rc && ll && !ld_) rc = copy_out(c, ll, c->ll, sizeof(float) * c->P);
     if (!rc && g && !gd) rc = copy_out(c, g, dg, sizeof(float) * 6 * (size_t)c->P);
-    const size_t nm = c->cfg.model == GMCS_MODEL_GICP ? 21 : 10;
+    const size_t nm = c->cfg.model == GMCS_MODEL_GICP ? 22 : 10;
     if (!rc && mom && !md) rc = copy_out(c, mom, dm, sizeof(float) * nm * (size_t)c->P);
     if (tmp) {
         cudaStreamSynchronize(c->stream);

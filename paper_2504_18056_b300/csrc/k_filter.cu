@@ -527,8 +527,8 @@ __device__ bool gn_step_h(const float* b, const float* hu, const FinishArgs& a, 
     return damped_solve(H, 1.f, b, a, psi);
 }
 
-// GICP: the accumulators are [l, b (6), H upper triangle (21)]; the gradient of
-// l is 2 b where the pose does not move Omega (Eq. 3 has no 1/2).
+// GICP: the accumulators are [l, b (6), H upper triangle (21), inlier count];
+// the gradient of l is 2 b where the pose does not move Omega (Eq. 3 has no 1/2).
 template <bool GRAD, bool GICP>
 __device__ __forceinline__ void finish_body(const FinishArgs& a, int vb, int vg) {
     const int i = vb * blockDim.x + threadIdx.x;
@@ -544,7 +544,7 @@ __device__ __forceinline__ void finish_body(const FinishArgs& a, int vb, int vg)
         if (a.out_g)
             for (int d = 0; d < 6; ++d) a.out_g[(size_t)i * 6 + d] = GICP ? 2.f * acc[1 + d] : acc[1 + d];
         if (a.out_mom) {
-            constexpr int NM = GICP ? 21 : 10;
+            constexpr int NM = GICP ? 22 : 10;
             for (int d = 0; d < NM; ++d) a.out_mom[(size_t)i * NM + d] = acc[7 + d];
         }
         if (a.do_move) {

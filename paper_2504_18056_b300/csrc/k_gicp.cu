@@ -27,78 +27,89 @@ namespace gmcs {
 
 // ------------------------------------------------------------------ covariances
 
-// One Jacobi rotation zeroing A[p][q] of a symmetric 3x3 matrix (r the third
-// index), accumulated into the eigenvector matrix V (Golub & Van Loan, the
-// symmetric Schur decomposition of a 2x2 block).
-template <int p, int q, int r>
-__device__ __forceinline__ void jacobi_rot(double (&A)[3][3], double (&V)[3][3]) {
-    const double apq = A[p][q];
+// One Jacobi rotation zeroing a_pq of a symmetric 3x3 matrix (a_rp, a_rq the
+// entries coupling the third index r), accumulated into the eigenvector
+// columns vp, vq (Golub & Van Loan, the symmetric Schur decomposition of the
+// 2x2 block). Scalars, so that everything stays in registers.
+__device__ __forceinline__ void jacobi_rot(double& app, double& aqq, double& apq, double& arp, double& arq,
+                                           double& vp0, double& vp1, double& vp2, double& vq0, double& vq1,
+                                           double& vq2) {
     if (apq == 0.0) return;
-    const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+    const double theta = (aqq - app) / (2.0 * apq);
     const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
     const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-    const double arp = A[r][p], arq = A[r][q];
-    A[r][p] = A[p][r] = c * arp - s * arq;
-    A[r][q] = A[q][r] = s * arp + c * arq;
-    A[p][p] -= t * apq;
-    A[q][q] += t * apq;
-    A[p][q] = A[q][p] = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const double vp = V[k][p], vq = V[k][q];
-        V[k][p] = c * vp - s * vq;
-        V[k][q] = s * vp + c * vq;
-    }
+    const double rp = arp, rq = arq;
+    arp = c * rp - s * rq;
+    arq = s * rp + c * rq;
+    app -= t * apq;
+    aqq += t * apq;
+    apq = 0.0;
+    double x = vp0, y = vq0;
+    vp0 = c * x - s * y; vq0 = s * x + c * y;
+    x = vp1; y = vq1;
+    vp1 = c * x - s * y; vq1 = s * x + c * y;
+    x = vp2; y = vq2;
+    vp2 = c * x - s * y; vq2 = s * x + c * y;
 }
 
-// Unit eigenvector of the smallest eigenvalue (lowest index on ties) by cyclic Jacobi.
-__device__ __forceinline__ void sym3_min_eigvec(double (&A)[3][3], double n[3]) {
-    double V[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+// Unit eigenvector of the smallest eigenvalue (lowest index on ties) of the
+// symmetric matrix [[a00 a01 a02] [a01 a11 a12] [a02 a12 a22]] by cyclic Jacobi.
+__device__ __forceinline__ void sym3_min_eigvec(double a00, double a01, double a02, double a11, double a12,
+                                                double a22, double n[3]) {
+    // V columns: (v00 v10 v20), (v01 v11 v21), (v02 v12 v22)
+    double v00 = 1.0, v01 = 0.0, v02 = 0.0, v10 = 0.0, v11 = 1.0, v12 = 0.0, v20 = 0.0, v21 = 0.0, v22 = 1.0;
     for (int sweep = 0; sweep < 50; ++sweep) {
-        const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
-        const double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+        const double off = a01 * a01 + a02 * a02 + a12 * a12;
+        const double dia = a00 * a00 + a11 * a11 + a22 * a22;
         if (!(off > 1e-36 * dia)) break;
-        jacobi_rot<0, 1, 2>(A, V);
-        jacobi_rot<0, 2, 1>(A, V);
-        jacobi_rot<1, 2, 0>(A, V);
+        jacobi_rot(a00, a11, a01, a02, a12, v00, v10, v20, v01, v11, v21);   // (p,q,r) = (0,1,2)
+        jacobi_rot(a00, a22, a02, a01, a12, v00, v10, v20, v02, v12, v22);   // (0,2,1)
+        jacobi_rot(a11, a22, a12, a01, a02, v01, v11, v21, v02, v12, v22);   // (1,2,0)
     }
     int m = 0;
-    if (A[1][1] < A[m][m]) m = 1;
-    if (A[2][2] < A[m][m]) m = 2;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) n[k] = (m == 0) ? V[k][0] : (m == 1 ? V[k][1] : V[k][2]);
+    double lm = a00;
+    if (a11 < lm) { m = 1; lm = a11; }
+    if (a22 < lm) m = 2;
+    n[0] = m == 0 ? v00 : (m == 1 ? v01 : v02);
+    n[1] = m == 0 ? v10 : (m == 1 ? v11 : v12);
+    n[2] = m == 0 ? v20 : (m == 1 ? v21 : v22);
 }
 
-// One thread per point. Candidates stream through shared memory in index order;
-// the k best are kept sorted by squared distance, formed in float as
-// ((dx*dx + dy*dy) + dz*dz) with separate round-to-nearest operations; a
-// candidate replaces an entry only when strictly closer, so ties keep the lower
-// index. The covariance of the k points is taken in FP64 (1/k) and regularised.
+// One warp per point. The cloud streams through shared memory in tiles; lane l
+// takes the candidates of index l mod 32 and keeps its k best sorted by squared
+// distance, formed in float as ((dx*dx + dy*dy) + dz*dz) with separate
+// round-to-nearest operations (a candidate enters only when strictly closer, so
+// equal distances stay in index order). The warp then merges the 32 lists by k
+// rounds of a shuffle arg-min on (distance, index): the k nearest points of the
+// cloud with ties to the lower index. Lane 0 takes their FP64 covariance (1/k)
+// and the plane regularisation.
+template <int KM>
 __global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
-    __shared__ float4 tile[128];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int kTile = 1024;
+    __shared__ float4 tile[kTile];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
     const bool act = i < a.n;
     const float4 p = act ? a.pts[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int k = min(a.k, a.n);
-    float bd[kKnnMax];
-    int bi[kKnnMax];
+    float bd[KM];
+    int bi[KM];
 #pragma unroll
-    for (int s = 0; s < kKnnMax; ++s) { bd[s] = __int_as_float(0x7f800000); bi[s] = 0; }
+    for (int s = 0; s < KM; ++s) { bd[s] = __int_as_float(0x7f800000); bi[s] = 0x7fffffff; }
     float worst = __int_as_float(0x7f800000);
-    for (int base = 0; base < a.n; base += blockDim.x) {
-        const int j = base + threadIdx.x;
-        if (j < a.n) tile[threadIdx.x] = a.pts[j];
+    for (int base = 0; base < a.n; base += kTile) {
+        const int m = min(kTile, a.n - base);
+        for (int t = threadIdx.x; t < m; t += blockDim.x) tile[t] = a.pts[base + t];
         __syncthreads();
-        const int m = min((int)blockDim.x, a.n - base);
         if (act) {
-            for (int t = 0; t < m; ++t) {
+            for (int t = lane; t < m; t += 32) {
                 const float4 q = tile[t];
                 const float dx = __fsub_rn(q.x, p.x), dy = __fsub_rn(q.y, p.y), dz = __fsub_rn(q.z, p.z);
                 const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                 if (d2 < worst) {
                     bool done = false;
 #pragma unroll
-                    for (int s = kKnnMax - 1; s >= 0; --s) {
+                    for (int s = KM - 1; s >= 0; --s) {
                         if (s < k && !done) {
                             if (s > 0 && bd[s - 1] > d2) {
                                 bd[s] = bd[s - 1];
@@ -111,19 +122,42 @@ __global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
                         }
                     }
 #pragma unroll
-                    for (int s = 0; s < kKnnMax; ++s)
+                    for (int s = 0; s < KM; ++s)
                         if (s == k - 1) worst = bd[s];
                 }
             }
         }
         __syncthreads();
     }
-    if (!act || k <= 0) return;
+    if (!act || k <= 0) return;                 // warp-uniform: one point per warp
+    int nb[KM];
+#pragma unroll
+    for (int r = 0; r < KM; ++r) {
+        nb[r] = 0;
+        if (r < k) {
+            float d = bd[0];
+            int j = bi[0];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, d, off);
+                const int oj = __shfl_xor_sync(0xffffffffu, j, off);
+                if (od < d || (od == d && oj < j)) { d = od; j = oj; }
+            }
+            nb[r] = j;
+            if (bi[0] == j) {                   // the owner pops its head
+#pragma unroll
+                for (int s = 0; s < KM - 1; ++s) { bd[s] = bd[s + 1]; bi[s] = bi[s + 1]; }
+                bd[KM - 1] = __int_as_float(0x7f800000);
+                bi[KM - 1] = 0x7fffffff;
+            }
+        }
+    }
+    if (lane != 0) return;
     double mx = 0.0, my = 0.0, mz = 0.0;
 #pragma unroll
-    for (int s = 0; s < kKnnMax; ++s) {
+    for (int s = 0; s < KM; ++s) {
         if (s < k) {
-            const float4 q = a.pts[bi[s]];
+            const float4 q = a.pts[nb[s]];
             mx += (double)q.x;
             my += (double)q.y;
             mz += (double)q.z;
@@ -132,21 +166,19 @@ __global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
     mx /= (double)k;
     my /= (double)k;
     mz /= (double)k;
-    double C[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    double c00 = 0.0, c01 = 0.0, c02 = 0.0, c11 = 0.0, c12 = 0.0, c22 = 0.0;
 #pragma unroll
-    for (int s = 0; s < kKnnMax; ++s) {
+    for (int s = 0; s < KM; ++s) {
         if (s < k) {
-            const float4 q = a.pts[bi[s]];
+            const float4 q = a.pts[nb[s]];
             const double dx = (double)q.x - mx, dy = (double)q.y - my, dz = (double)q.z - mz;
-            C[0][0] += dx * dx; C[0][1] += dx * dy; C[0][2] += dx * dz;
-            C[1][1] += dy * dy; C[1][2] += dy * dz; C[2][2] += dz * dz;
+            c00 += dx * dx; c01 += dx * dy; c02 += dx * dz;
+            c11 += dy * dy; c12 += dy * dz; c22 += dz * dz;
         }
     }
     const double ik = 1.0 / (double)k;
-    C[0][0] *= ik; C[0][1] *= ik; C[0][2] *= ik; C[1][1] *= ik; C[1][2] *= ik; C[2][2] *= ik;
-    C[1][0] = C[0][1]; C[2][0] = C[0][2]; C[2][1] = C[1][2];
     double n[3];
-    sym3_min_eigvec(C, n);
+    sym3_min_eigvec(c00 * ik, c01 * ik, c02 * ik, c11 * ik, c12 * ik, c22 * ik, n);
     const double w = 1.0 - a.eps;
     const double sxx = 1.0 - w * n[0] * n[0], sxy = -w * n[0] * n[1], sxz = -w * n[0] * n[2];
     const double syy = 1.0 - w * n[1] * n[1], syz = -w * n[1] * n[2], szz = 1.0 - w * n[2] * n[2];
@@ -318,6 +350,7 @@ __global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
                     // translation block Omega~
                     acc[22] += o00; acc[23] += o01; acc[24] += o02;
                     acc[25] += o11; acc[26] += o12; acc[27] += o22;
+                    acc[28] += 1.f;
                 }
             }
         }
@@ -329,7 +362,11 @@ __global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
 // ------------------------------------------------------------------ launchers
 
 void launch_knn_cov(const KnnCovArgs& a, cudaStream_t s) {
-    if (a.n > 0) k_knn_cov<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+    if (a.n <= 0) return;
+    const int grid = (a.n + 3) / 4;   // 4 points (warps) per CTA
+    if (a.k <= 8) k_knn_cov<8><<<grid, 128, 0, s>>>(a);
+    else if (a.k <= 16) k_knn_cov<16><<<grid, 128, 0, s>>>(a);
+    else k_knn_cov<32><<<grid, 128, 0, s>>>(a);
 }
 
 void launch_voxel_accum(const VoxelArgs& a, cudaStream_t s) {

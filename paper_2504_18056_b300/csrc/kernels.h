@@ -18,7 +18,7 @@ constexpr int kPassTW = GMCS_TW;
 constexpr int kPassCW = kPassWarps / kPassTW;
 static_assert(kPassTW * kPassCW == kPassWarps, "tile x chunk split of the CTA");
 constexpr int kAccGrad = 17;            // ll, d ll/d omega (3), d ll/d v (3), moments (10)
-constexpr int kAccGicp = 28;            // GICP: ll, b (6), H upper triangle (21)
+constexpr int kAccGicp = 29;            // GICP: ll, b (6), H upper triangle (21), inlier count
 constexpr int kMaxGroups = 8;           // point-chunk groups per particle tile (scratch bound)
 
 // ------------------------------------------------------------------ tables

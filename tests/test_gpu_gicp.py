@@ -22,6 +22,9 @@ TAU = 20.0
 @pytest.fixture(scope="module")
 def gw():
     w = synth.forest_workload(seed=5, n_particles=4096, n_points=512, n_keyframes=4, kf_points=2048, n_frames=3)
+    # the first 64 particles close to the truth (2 cm / 0.2 deg), so that most of their lookups are inliers
+    rng = np.random.default_rng(8)
+    w["particles"][:64] = synth.perturb_poses(w["truth"][0], 64, 0.02, np.deg2rad(0.2), rng).astype(np.float32)
     grids = [synth.grid_for_points(kf["points"], H_VOX, 1.0) for kf in w["keyframes"]]
     covs = [oracle.knn_cov(kf["points"], k=10, eps=EPS) for kf in w["keyframes"]]
     maps = [oracle.gicp_voxel_map(kf["points"], c, g) for kf, c, g in zip(w["keyframes"], covs, grids)]
@@ -34,6 +37,10 @@ def _filter(w, grids, P=None, **cfg):
     P = P or w["particles"].shape[0]
     f = g.Filter(P, len(grids), 4096, model=g.MODEL_GICP, **cfg)
     f.init_particles(np.ascontiguousarray(w["particles"][:P]))
+    return _with_keyframes(f, w, grids, P)
+
+
+def _with_keyframes(f, w, grids, P):
     for k, kf in enumerate(w["keyframes"]):
         f.add_keyframe(kf["points"], grids[k], np.ascontiguousarray(w["kf_particle_poses"][k][:P]))
     return f
@@ -96,27 +103,32 @@ def test_eval_matches_oracle(gw):
     scan = w["scans"][0]
     ll = np.zeros(P, np.float32)
     g = np.zeros((P, 6), np.float32)
-    Hu = np.zeros((P, 21), np.float32)
+    Hu = np.zeros((P, 22), np.float32)
     f.eval(scan, ll, g, Hu)
     scov = oracle.knn_cov(scan, k=10, eps=EPS)
     rng = np.random.default_rng(0)
     idx = np.unique(np.r_[np.arange(40), rng.choice(P, 88, replace=False), P - 1])
-    r_ll, r_g, r_h = [], [], []
+    r_ll, r_g, r_h, n_in = [], [], [], []
     for i in idx:
         ks = [int(k) for k in nbr[i]]
         o = oracle.gicp_eval(w["particles"][i].astype(np.float64), [w["kf_particle_poses"][k][i] for k in ks],
-                             [maps[k] for k in ks], [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4)
+                             [maps[k] for k in ks], [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4,
+                             gate_delta=1e-3)
         sl = o["slack"]
         r_ll.append(abs(ll[i] - o["ll"]) / (1e-6 * abs(o["ll"]) + sl[0]))
         gs = np.linalg.norm(o["b"]) * 2
         r_g.append(np.linalg.norm(g[i] - 2 * o["b"]) / (2e-4 * max(gs, 1e-3 * np.linalg.norm(o["H"])) + 2 * sl[1]))
         hs = np.linalg.norm(o["H"])
-        r_h.append(np.linalg.norm(Hu[i] - _upper(o["H"])) / (2e-4 * hs + sl[2] + 1e-6))
+        r_h.append(np.linalg.norm(Hu[i, :21] - _upper(o["H"])) / (2e-4 * hs + sl[2] + 1e-6))
+        n_in.append((Hu[i, 21], o["nvalid"], sl.sum() > 0))
     r_ll, r_g, r_h = map(np.array, (r_ll, r_g, r_h))
     print("\nGICP_EVAL " + json.dumps({"ll_over_tol_max": float(r_ll.max()), "g_over_tol_max": float(r_g.max()),
                                        "H_over_tol_max": float(r_h.max()), "ll_over_tol_median": float(np.median(r_ll)),
                                        "g_over_tol_median": float(np.median(r_g))}))
     assert r_ll.max() <= 1 and r_g.max() <= 1 and r_h.max() <= 1
+    # inlier counts: exact where no lookup is near a voxel face
+    assert all(a == b for a, b, near in n_in if not near)
+    assert sum(b >= 300 for _, b, _ in n_in) >= 20          # enough well-aligned particles were checked
     f.close()
 
 
@@ -135,7 +147,7 @@ def test_move_matches_oracle(gw):
         ks = [int(k) for k in nbr[i]]
         T0 = w["particles"][i].astype(np.float64)
         o = oracle.gicp_eval(T0, [w["kf_particle_poses"][k][i] for k in ks], [maps[k] for k in ks],
-                             [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4)
+                             [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4, gate_delta=1e-3)
         if o["slack"].sum() > 0:
             continue
         T1, psi = oracle.move_h(T0, o["b"], o["H"], lambda_=1e-3)
@@ -179,3 +191,46 @@ def test_step_matches_oracle_frame(gw):
         err = np.linalg.norm(o["estimate"][[3, 7, 11]] - w["truth"][fr + 1][[3, 7, 11]])
         assert err < 0.3, (fr, err)
     f.close()
+
+
+def test_full_size_eval_sampled():
+    """The benchmark's GICP configuration -- 100,000 particles x 2,048 points x 20
+    keyframes of 8,192 points, 1 m voxel maps -- evaluated in one launch and
+    checked against the oracle on 24 sampled particles (oracle maps built for the
+    keyframes they select)."""
+    import paper_2504_18056_b300 as g
+    torch_cuda()
+    P, N, K = 100_000, 2048, 20
+    w = synth.forest_workload(seed=0, n_particles=P, n_points=N, n_keyframes=K, n_frames=1)
+    grids = [synth.grid_for_points(kf["points"], H_VOX, 1.0) for kf in w["keyframes"]]
+    f = g.Filter(P, K, N, model=g.MODEL_GICP)
+    f.init_particles(w["particles"])
+    for k, kf in enumerate(w["keyframes"]):
+        f.add_keyframe(kf["points"], grids[k], w["kf_particle_poses"][k])
+    nbr = np.zeros((P, 3), np.int32)
+    f.select(nbr)
+    scan = w["scans"][0]
+    ll = np.zeros(P, np.float32)
+    gg = np.zeros((P, 6), np.float32)
+    Hu = np.zeros((P, 22), np.float32)
+    f.eval(scan, ll, gg, Hu)
+    f.close()
+    rng = np.random.default_rng(1)
+    idx = np.r_[0, P - 1, rng.choice(P, 22, replace=False)]
+    need = sorted(set(int(k) for k in nbr[idx].ravel()))
+    maps = {k: oracle.gicp_voxel_map(w["keyframes"][k]["points"], oracle.knn_cov(w["keyframes"][k]["points"], 10, EPS),
+                                     grids[k]) for k in need}
+    scov = oracle.knn_cov(scan, k=10, eps=EPS)
+    worst = 0.0
+    for i in idx:
+        ks = [int(k) for k in nbr[i]]
+        o = oracle.gicp_eval(w["particles"][i].astype(np.float64), [w["kf_particle_poses"][k][i] for k in ks],
+                             [maps[k] for k in ks], [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4,
+                             gate_delta=1e-3)
+        sl = o["slack"]
+        worst = max(worst, abs(ll[i] - o["ll"]) / (1e-6 * abs(o["ll"]) + sl[0]),
+                    np.linalg.norm(gg[i] - 2 * o["b"]) / (2e-4 * max(2 * np.linalg.norm(o["b"]), 1e-3 * np.linalg.norm(o["H"]))
+                                                           + 2 * sl[1] + 1e-6),
+                    np.linalg.norm(Hu[i, :21] - _upper(o["H"])) / (2e-4 * np.linalg.norm(o["H"]) + sl[2] + 1e-6))
+    print(f"\nGICP_FULL worst/tol {worst:.3g}")
+    assert worst <= 1
