@@ -393,6 +393,24 @@ def move_h(T, b, H, sigma=0.2, lambda_=1e-3, theta_max=np.deg2rad(2.0), t_max=0.
     return out, psi
 
 
+def occupancy_grid(pts, h):
+    """ora_occupancy_grid: the overlap lattice of a cloud as a grid dict."""
+    pts, pp = _f(np.asarray(pts).reshape(-1, 3))
+    g = Grid()
+    lib().ora_occupancy_grid(pp, C.c_int(pts.shape[0]), C.c_double(h), C.byref(g))
+    return {"origin": np.array(list(g.origin)), "h": g.h, "dims": tuple(int(v) for v in g.n)}
+
+
+def overlap(kf_pts, scan, T_rel, h=1.0):
+    """ora_overlap: share of scan points, moved by T_rel, in occupied voxels of kf_pts."""
+    kf, pk = _f(np.asarray(kf_pts).reshape(-1, 3))
+    sc, ps = _f(np.asarray(scan).reshape(-1, 3))
+    T, pT = _d(np.asarray(T_rel).reshape(12))
+    g = make_grid(occupancy_grid(kf, h))
+    lib().ora_overlap.restype = C.c_double
+    return lib().ora_overlap(pk, C.c_int(kf.shape[0]), C.byref(g), ps, C.c_int(sc.shape[0]), pT)
+
+
 class State:
     """Particle set held by the oracle in FP64: poses (P, 12), keyframe poses
     (K, P, 12), log-weights (P,), plus the shared keyframe tables."""

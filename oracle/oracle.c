@@ -878,6 +878,54 @@ int ora_prune(const double* x, const double* w, const double* ll, int P, int arg
 }
 
 /* ------------------------------------------------------------------------ */
+/* keyframe insertion by overlap, Sec. III-E                                 */
+/* ------------------------------------------------------------------------ */
+
+void ora_occupancy_grid(const float* pts, int n, double h, ora_grid* g) {
+    for (int a = 0; a < 3; ++a) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int i = 0; i < n; ++i) {
+            double v = pts[3 * i + a];
+            if (v < mn) mn = v;
+            if (v > mx) mx = v;
+        }
+        if (n == 0) mn = mx = 0.0;
+        double lo = floor(mn / h) - 1.0, hi = floor(mx / h) + 1.0;
+        g->origin[a] = lo * h;
+        g->n[a] = (int)(hi - lo) + 1;
+    }
+    g->h = h;
+}
+
+double ora_overlap(const float* kf_pts, int nk, const ora_grid* g, const float* scan, int n, const double T_rel[12]) {
+    size_t nv = (size_t)g->n[0] * g->n[1] * g->n[2];
+    unsigned char* occ = (unsigned char*)calloc(nv > 0 ? nv : 1, 1);
+    for (int i = 0; i < nk; ++i) {
+        int c[3], in = 1;
+        for (int a = 0; a < 3; ++a) {
+            c[a] = (int)floor(((double)kf_pts[3 * i + a] - g->origin[a]) / g->h);
+            if (c[a] < 0 || c[a] >= g->n[a]) in = 0;
+        }
+        if (in) occ[vidx(g, c[0], c[1], c[2])] = 1;
+    }
+    int hit = 0;
+    for (int j = 0; j < n; ++j) {
+        double p[3] = {scan[3 * j], scan[3 * j + 1], scan[3 * j + 2]};
+        int c[3], in = 1;
+        for (int a = 0; a < 3; ++a) {
+            double x = T_rel[4 * a] * p[0] + T_rel[4 * a + 1] * p[1];
+            x = x + T_rel[4 * a + 2] * p[2];
+            x = x + T_rel[4 * a + 3];
+            c[a] = (int)floor((x - g->origin[a]) / g->h);
+            if (c[a] < 0 || c[a] >= g->n[a]) in = 0;
+        }
+        if (in && occ[vidx(g, c[0], c[1], c[2])]) ++hit;
+    }
+    free(occ);
+    return n > 0 ? (double)hit / (double)n : 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* whole frame                                                               */
 /* ------------------------------------------------------------------------ */
 

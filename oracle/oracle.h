@@ -180,6 +180,18 @@ void ora_resample(const double* w, int P, double u, int* anc);
 int ora_prune(const double* x, const double* w, const double* ll, int P, int argmax, double prune_w,
               double ll_cut, double u, int* anc, double* logw_out);
 
+/* ---- keyframe insertion by overlap (Sec. III-E).
+ * Occupancy lattice of a cloud at voxel edge h: per axis lo = floor(min / h) - 1,
+ * hi = floor(max / h) + 1 (min, max over the points, FP64), origin = lo h,
+ * n = hi - lo + 1 voxels, so every point lies at least one voxel inside.
+ * ora_occupancy_grid fills g; ora_overlap returns the fraction of the n scan
+ * points that, moved by T_rel (the current frame in the last keyframe's frame,
+ * from odometry), fall into a voxel of g holding at least one keyframe point.
+ * Every product and sum is rounded separately (FP64), the voxel is
+ * floor((x - origin) / h). */
+void ora_occupancy_grid(const float* pts, int n, double h, ora_grid* g);
+double ora_overlap(const float* kf_pts, int nk, const ora_grid* g, const float* scan, int n, const double T_rel[12]);
+
 /* ---- whole frame over a particle set (the hot path, all steps in order). */
 typedef struct {
     double sigma, eps, lambda, theta_max, t_max, w_min, face_delta;
