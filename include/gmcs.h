@@ -94,6 +94,11 @@ typedef struct {
     float cov_eps;     /* GICP: plane regularisation, covariance eigenvalues (cov_eps, 1, 1) */
     float gicp_tau;    /* GICP: cap of a term's e^T Omega e; points without a voxel or with
                           e^T Omega e >= gicp_tau add -gicp_tau and no gradient (20) */
+    float kf_overlap;  /* > 0: gmcs_step inserts the frame as a keyframe when its overlap rate
+                          with the last keyframe falls below this (Sec. III-E: 0.7); 0: off */
+    float kf_voxel;    /* voxel edge (m) of the keyframes' occupancy lattices (1.0) */
+    float kf_h;        /* lattice step (field) or voxel edge (GICP) of inserted keyframes (0.2) */
+    int reserved;
     uint64_t seed;     /* key of the Philox4x32-10 draws (motion noise, resampling offset) */
 } gmcs_config;
 
@@ -115,7 +120,8 @@ typedef struct {
     uint32_t frame;       /* frame counter used for this frame's draws */
     int status;           /* GMCS_OK or GMCS_E_NONFINITE */
     int pruned;           /* GMCS_RESAMPLE_PRUNE: dead particles refilled this frame */
-    int reserved;
+    int kf_inserted;      /* 1 if the frame was inserted as a keyframe (cfg.kf_overlap) */
+    double overlap;       /* overlap rate with the last keyframe (cfg.kf_overlap > 0), else -1 */
 } gmcs_step_out;
 
 typedef struct {
@@ -133,7 +139,8 @@ typedef struct gmcs_ctx gmcs_ctx;
 /* Defaults: sigma 0.2 m, r_t 1.0 m, eps 1e-3, lambda 1e-3, theta_max 2 deg,
  * t_max 0.1 m, w_min 1e-6, k_nb 3, steps 3, FP32 tables, resample always,
  * no propagation, no loop condition, prune_w 1e-8, prune_lr 1e-16, voxel field
- * model (GICP settings knn 10, cov_eps 1e-3, gicp_tau 20), seed 0. */
+ * model (GICP settings knn 10, cov_eps 1e-3, gicp_tau 20), no keyframe insertion
+ * (kf_voxel 1.0, kf_h 0.2), seed 0. */
 void gmcs_config_default(gmcs_config* cfg);
 
 /*
@@ -198,6 +205,14 @@ int gmcs_add_keyframe(gmcs_ctx* ctx, const float* pts, int n, const gmcs_grid* g
  * u_override: NULL, or a host double in [0,1) used as the systematic offset.
  * out: NULL (asynchronous: nothing is read back; see gmcs_last_result), or a
  * host struct filled after synchronising the stream.
+ * Keyframe insertion (Sec. III-E, cfg.kf_overlap > 0): the scan is moved into
+ * the last keyframe's frame by the odometry accumulated since that keyframe and
+ * its overlap rate (gmcs_overlap) is computed on the device with the frame; with
+ * out != NULL, a rate below cfg.kf_overlap inserts the scan as a new keyframe
+ * (as gmcs_add_keyframe with kf_poses = NULL: every particle's pose after this
+ * frame; lattice step cfg.kf_h over the scan's bounding box plus r_t, or GICP
+ * voxels of edge cfg.kf_h) before the call returns, used from the next frame on.
+ * The asynchronous form reports the rate through gmcs_last_result only.
  * Errors: GMCS_E_INVALID, GMCS_E_CAPACITY (N > max_points), GMCS_E_STATE (no
  * particles or no keyframes), GMCS_E_CUDA.
  */
@@ -332,6 +347,15 @@ int gmcs_prune(gmcs_ctx* ctx, const double* x, const double* w, const float* ll,
 int gmcs_resample_noalloc(const double* w, int P, double u, int* anc, void* cuda_stream);
 
 /* ---- state access */
+
+/* Overlap rate (Sec. III-E) of a scan (N x 3 floats, host or device) with the
+ * last keyframe: the share of its points that, moved by T_rel (12 host doubles,
+ * the scan's frame in the keyframe's frame), fall into an occupied voxel of the
+ * keyframe's occupancy lattice (edge cfg.kf_voxel; per axis from floor(min/h) - 1
+ * to floor(max/h) + 1 voxels of the keyframe points). The transform is taken in
+ * FP64 with separately rounded products and sums, the voxel is floor((x - o)/h).
+ * Errors: GMCS_E_STATE without keyframes. */
+int gmcs_overlap(gmcs_ctx* ctx, const float* scan, int N, const double T_rel[12], double* rate);
 
 /* Copy current poses (P x 12 floats) and/or log-weights (P doubles) out; NULL skips. */
 int gmcs_get_particles(gmcs_ctx* ctx, float* poses, double* logw);

@@ -39,7 +39,8 @@ class Config(C.Structure):
                 ("theta_max", C.c_float), ("t_max", C.c_float), ("w_min", C.c_float), ("k_nb", C.c_int),
                 ("steps", C.c_int), ("table_dtype", C.c_int), ("resample", C.c_int), ("propagate", C.c_int),
                 ("loop_recent", C.c_int), ("prune_w", C.c_float), ("prune_lr", C.c_float), ("model", C.c_int),
-                ("knn", C.c_int), ("cov_eps", C.c_float), ("gicp_tau", C.c_float), ("seed", C.c_uint64)]
+                ("knn", C.c_int), ("cov_eps", C.c_float), ("gicp_tau", C.c_float), ("kf_overlap", C.c_float),
+                ("kf_voxel", C.c_float), ("kf_h", C.c_float), ("reserved", C.c_int), ("seed", C.c_uint64)]
 
 
 class Grid(C.Structure):
@@ -49,12 +50,14 @@ class Grid(C.Structure):
 class StepOut(C.Structure):
     _fields_ = [("estimate", C.c_double * 12), ("ess", C.c_double), ("max_w", C.c_double),
                 ("log_norm", C.c_double), ("argmax", C.c_int), ("resampled", C.c_int),
-                ("frame", C.c_uint32), ("status", C.c_int), ("pruned", C.c_int), ("reserved", C.c_int)]
+                ("frame", C.c_uint32), ("status", C.c_int), ("pruned", C.c_int), ("kf_inserted", C.c_int),
+                ("overlap", C.c_double)]
 
     def as_dict(self):
         return {"estimate": np.array(list(self.estimate)), "ess": self.ess, "max_w": self.max_w,
                 "log_norm": self.log_norm, "argmax": self.argmax, "resampled": bool(self.resampled),
-                "frame": self.frame, "status": self.status, "pruned": self.pruned}
+                "frame": self.frame, "status": self.status, "pruned": self.pruned,
+                "kf_inserted": bool(self.kf_inserted), "overlap": self.overlap}
 
 
 class Stats(C.Structure):
@@ -99,6 +102,7 @@ _SIGS = {
     "gmcs_get_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_get_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_point_covariances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_overlap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gmcs_set_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_get_frame_diag": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmcs_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_uint32)]),
@@ -326,6 +330,13 @@ class Filter:
 
     def frame_diag(self, ll=None, w=None, anc=None, nbr=None):
         _check(lib().gmcs_get_frame_diag(self.ctx, _ptr(ll), _ptr(w), _ptr(anc), _ptr(nbr)), "gmcs_get_frame_diag")
+
+    def overlap(self, scan, T_rel):
+        """Overlap rate of a scan with the last keyframe (gmcs_overlap)."""
+        r = C.c_double()
+        _check(lib().gmcs_overlap(self.ctx, _ptr(scan), int(scan.shape[0]), _dbl(T_rel, 12), C.byref(r)),
+               "gmcs_overlap")
+        return r.value
 
     def point_covariances(self, pts, cov=None):
         """GICP point covariances of a cloud (gmcs_point_covariances): n x 6 doubles."""

@@ -16,6 +16,9 @@ struct HostTable {
     size_t bytes = 0;
     gmcs_grid grid;
     int dtype = 0;
+    unsigned char* occ = nullptr;   // occupancy lattice for the overlap rate (Sec. III-E)
+    gmcs_grid occ_grid;
+    size_t occ_bytes = 0;
 };
 
 struct EvPair {
@@ -61,6 +64,13 @@ struct gmcs_ctx {
     std::vector<double> kf_path;     // odometry path length at each keyframe
     double path_now = 0.0;           // and at the current frame
     float* d_kf_path = nullptr;
+    double odo[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};   // odometry pose of the frame in the last keyframe's frame
+    int* d_mm = nullptr;             // bounding-box scratch (6 ints)
+    unsigned* d_ovl = nullptr;       // overlap hit count of the frame
+    unsigned* h_ovl = nullptr;       // pinned copy
+    bool ovl_valid = false;
+    int last_N = 0;
+    int last_inserted = 0;
     unsigned* d2 = nullptr;
     size_t d2_cap = 0;
     size_t dev_bytes = 0;

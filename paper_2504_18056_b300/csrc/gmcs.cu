@@ -20,8 +20,8 @@
 
 using namespace gmcs;
 
-static_assert(sizeof(gmcs_config) == 88, "gmcs_config layout is part of the ABI");
-static_assert(sizeof(gmcs_step_out) == 144, "gmcs_step_out layout is part of the ABI");
+static_assert(sizeof(gmcs_config) == 104, "gmcs_config layout is part of the ABI");
+static_assert(sizeof(gmcs_step_out) == 152, "gmcs_step_out layout is part of the ABI");
 static_assert(sizeof(gmcs_grid) == 48, "gmcs_grid layout is part of the ABI");
 
 namespace {
@@ -62,7 +62,7 @@ size_t ctx_device_bytes(int max_particles, int max_keyframes, int max_points) {
     b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * 3 * max_points + sizeof(float) * stage;
     b += sizeof(double) * kWeighPart * 148 * 4 + sizeof(unsigned) + sizeof(WeighResult);
     b += sizeof(unsigned long long) * (ld + 2 * (nb + 1)) + sizeof(int) * ld;
-    b += sizeof(TableDesc) * max_keyframes + sizeof(float) * max_keyframes;
+    b += sizeof(TableDesc) * max_keyframes + sizeof(float) * max_keyframes + sizeof(int) * 8 + sizeof(unsigned);
     return b;
 }
 
@@ -485,7 +485,8 @@ void fill_out(const WeighResult& r, uint32_t frame, gmcs_step_out* o) {
     o->frame = frame;
     o->status = r.nonfinite ? GMCS_E_NONFINITE : GMCS_OK;
     o->pruned = r.pruned;
-    o->reserved = 0;
+    o->kf_inserted = 0;
+    o->overlap = -1.0;
 }
 
 }  // namespace gmcs
@@ -525,6 +526,9 @@ void gmcs_config_default(gmcs_config* cfg) {
     cfg->knn = 10;
     cfg->cov_eps = 1e-3f;
     cfg->gicp_tau = 20.f;
+    cfg->kf_overlap = 0.f;
+    cfg->kf_voxel = 1.f;
+    cfg->kf_h = 0.2f;
     cfg->seed = 0;
 }
 
@@ -550,7 +554,8 @@ static bool config_ok(const gmcs_config* c) {
            c->steps <= 64 && c->table_dtype >= 0 && c->table_dtype <= 2 && c->resample >= 0 && c->resample <= 3 &&
            c->prune_w >= 0.f && c->prune_w < 1.f && c->prune_lr >= 0.f && c->prune_lr < 1.f &&
            (c->model == GMCS_MODEL_FIELD || c->model == GMCS_MODEL_GICP) && c->knn >= 1 && c->knn <= kKnnMax &&
-           c->cov_eps > 0.f && c->cov_eps <= 1.f && c->gicp_tau > 0.f;
+           c->cov_eps > 0.f && c->cov_eps <= 1.f && c->gicp_tau > 0.f && c->kf_overlap >= 0.f &&
+           c->kf_overlap <= 1.f && c->kf_voxel > 0.f && c->kf_h > 0.f;
 }
 
 int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, int max_points, void* cuda_stream,
@@ -595,6 +600,13 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     if (!rc) rc = dalloc(c, &c->anc, ld);
     if (!rc) rc = dalloc(c, &c->d_tables, (size_t)max_keyframes);
     if (!rc) rc = dalloc(c, &c->d_kf_path, (size_t)max_keyframes);
+    if (!rc) rc = dalloc(c, &c->d_mm, 8);
+    if (!rc) rc = dalloc(c, &c->d_ovl, 1);
+    if (!rc && cudaMallocHost((void**)&c->h_ovl, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_ovl = nullptr;
+        rc = GMCS_E_OOM;
+    }
     if (!rc && cudaMallocHost((void**)&c->h_res, sizeof(WeighResult)) != cudaSuccess) {
         cudaGetLastError();
         c->h_res = nullptr;
@@ -616,13 +628,17 @@ int gmcs_destroy(gmcs_ctx* c) {
     cudaStreamSynchronize(c->stream);
     harvest(c);
     for (auto e : c->free_events) cudaEventDestroy(e);
-    for (auto& t : c->tables) cudaFree(t.cells);
+    for (auto& t : c->tables) {
+        cudaFree(t.cells);
+        cudaFree(t.occ);
+    }
     void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->gbuf, c->ll, c->nbr, c->part, c->scan,
-                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->dtot, c->anc, c->d_tables, c->d2, c->scov,
+                    c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->dtot, c->anc, c->d_tables, c->d2, c->scov, c->d_mm, c->d_ovl,
                     c->d_kf_path};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
+    if (c->h_ovl) cudaFreeHost(c->h_ovl);
     cudaGetLastError();
     delete c;
     return GMCS_OK;
@@ -732,11 +748,86 @@ int build_gicp_map(gmcs_ctx* c, const float* dpts, int n, const gmcs_grid* grid,
     return rc;
 }
 
-// Table descriptor, per-particle keyframe poses and path length of a new
-// keyframe whose table t is built; frees t on failure.
+// Bounding box of n device points (n x 3 floats), synchronising.
+int device_bbox(gmcs_ctx* c, const float* dpts, int n, float4* p4, float mn[3], float mx[3]) {
+    {
+        Launch L(c, K_TABLE);
+        launch_scan_pack(dpts, n, p4, c->stream);
+    }
+    BBoxArgs ba{p4, n, c->d_mm};
+    {
+        Launch L(c, K_TABLE);
+        launch_bbox(ba, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    int mm[6];
+    CK(cudaMemcpyAsync(mm, c->d_mm, sizeof(mm), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < 6; ++d) {
+        const int i = mm[d] >= 0 ? mm[d] : mm[d] ^ 0x7fffffff;   // back from the order-preserving image
+        float f;
+        std::memcpy(&f, &i, sizeof(f));
+        (d < 3 ? mn[d] : mx[d - 3]) = f;
+    }
+    return GMCS_OK;
+}
+
+// Occupancy lattice of a keyframe (voxel edge kf_voxel; per axis lo = floor(min/h) - 1,
+// hi = floor(max/h) + 1, origin lo h, hi - lo + 1 voxels), for the overlap rate.
+int build_occupancy(gmcs_ctx* c, const float* dpts, int n, HostTable& t) {
+    const double h = (double)c->cfg.kf_voxel;
+    float4* p4 = nullptr;
+    if (cudaMalloc((void**)&p4, sizeof(float4) * (size_t)std::max(n, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return GMCS_E_OOM;
+    }
+    float mn[3] = {0.f, 0.f, 0.f}, mx[3] = {0.f, 0.f, 0.f};
+    int rc = n > 0 ? device_bbox(c, dpts, n, p4, mn, mx) : GMCS_OK;
+    size_t nv = 1;
+    for (int a = 0; a < 3 && !rc; ++a) {
+        const double lo = std::floor((double)mn[a] / h) - 1.0, hi = std::floor((double)mx[a] / h) + 1.0;
+        t.occ_grid.origin[a] = lo * h;
+        t.occ_grid.n[a] = (int)(hi - lo) + 1;
+        nv *= (size_t)t.occ_grid.n[a];
+    }
+    t.occ_grid.h = h;
+    if (!rc && nv >= ((size_t)1 << 32)) rc = GMCS_E_INVALID;
+    if (!rc && cudaMalloc((void**)&t.occ, nv) != cudaSuccess) {
+        cudaGetLastError();
+        t.occ = nullptr;
+        rc = GMCS_E_OOM;
+    }
+    if (!rc) rc = cuda_status(cudaMemsetAsync(t.occ, 0, nv, c->stream));
+    if (!rc && n > 0) {
+        OccArgs oa{p4, n, t.occ_grid.origin[0], t.occ_grid.origin[1], t.occ_grid.origin[2], h,
+                   t.occ_grid.n[0], t.occ_grid.n[1], t.occ_grid.n[2], t.occ};
+        {
+            Launch L(c, K_TABLE);
+            launch_occ_fill(oa, c->stream);
+        }
+        rc = check_launch();
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(p4);
+    if (rc && t.occ) {
+        cudaFree(t.occ);
+        t.occ = nullptr;
+    }
+    t.occ_bytes = rc ? 0 : nv;
+    return rc;
+}
+
+// Table descriptor, occupancy lattice, per-particle keyframe poses and path
+// length of a new keyframe whose table t is built; frees t on failure. The
+// odometry since the last keyframe restarts (the keyframe is the current frame).
 int register_keyframe(gmcs_ctx* c, HostTable& t, const gmcs_grid* grid, int ncx, int ncy, int ncz,
-                      const float* kf_poses, int* kf_id) {
-    int rc = GMCS_OK;
+                      const float* kf_poses, int* kf_id, const float* dpts, int n) {
+    int rc = build_occupancy(c, dpts, n, t);
+    if (rc) {
+        cudaFree(t.cells);
+        return rc;
+    }
     TableDesc td;
     std::memset(&td, 0, sizeof(td));
     td.cells = t.cells;
@@ -769,19 +860,22 @@ int register_keyframe(gmcs_ctx* c, HostTable& t, const gmcs_grid* grid, int ncx,
     if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));   // td lives on this stack frame
     if (rc) {
         cudaFree(t.cells);
+        cudaFree(t.occ);
         return rc;
     }
     {
         const float d = (float)c->path_now;
         if (cudaMemcpy(c->d_kf_path + k, &d, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaFree(t.cells);
+            cudaFree(t.occ);
             return GMCS_E_CUDA;
         }
     }
     c->kf_path.push_back(c->path_now);
-    c->dev_bytes += t.bytes;
+    c->dev_bytes += t.bytes + t.occ_bytes;
     c->tables.push_back(t);
     c->K = k + 1;
+    for (int e = 0; e < 12; ++e) c->odo[e] = (e % 5 == 0) ? 1.0 : 0.0;   // identity
     if (kf_id) *kf_id = k;
     return GMCS_OK;
 }
@@ -821,12 +915,12 @@ int add_keyframe_gicp(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     t.grid = *grid;
     t.dtype = 3;
     rc = build_gicp_map(c, dpts, n, grid, &t);
+    if (!rc) rc = register_keyframe(c, t, grid, grid->n[0], grid->n[1], grid->n[2], kf_poses, kf_id, dpts, n);
     if (tmp) {
         cudaStreamSynchronize(c->stream);
         cudaFree(tmp);
     }
-    if (rc) return rc;
-    return register_keyframe(c, t, grid, grid->n[0], grid->n[1], grid->n[2], kf_poses, kf_id);
+    return rc;
 }
 
 }  // namespace
@@ -923,16 +1017,96 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
         launch_pack(pa, c->stream);
     }
     rc = check_launch();
+    if (rc) {
+        if (tmp) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(tmp);
+        }
+        cudaFree(t.cells);
+        return rc;
+    }
+    rc = register_keyframe(c, t, grid, (int)nx - 1, (int)ny - 1, (int)nz - 1, kf_poses, kf_id, dpts, n);
     if (tmp) {
         cudaStreamSynchronize(c->stream);
         cudaFree(tmp);
     }
-    if (rc) {
-        cudaFree(t.cells);
-        return rc;
-    }
-    return register_keyframe(c, t, grid, (int)nx - 1, (int)ny - 1, (int)nz - 1, kf_poses, kf_id);
+    return rc;
 }
+
+namespace {
+
+// Enqueue the overlap count of the packed scan (c->scan) against the last keyframe.
+int enqueue_overlap(gmcs_ctx* c, int N, const double T[12]) {
+    const HostTable& t = c->tables[c->K - 1];
+    OverlapArgs oa;
+    oa.scan = c->scan;
+    oa.n = N;
+    for (int e = 0; e < 12; ++e) oa.T[e] = T[e];
+    oa.occ = t.occ;
+    oa.ox = t.occ_grid.origin[0];
+    oa.oy = t.occ_grid.origin[1];
+    oa.oz = t.occ_grid.origin[2];
+    oa.h = t.occ_grid.h;
+    oa.nx = t.occ_grid.n[0];
+    oa.ny = t.occ_grid.n[1];
+    oa.nz = t.occ_grid.n[2];
+    oa.count = c->d_ovl;
+    CK(cudaMemsetAsync(c->d_ovl, 0, sizeof(unsigned), c->stream));
+    {
+        Launch L(c, K_MISC);
+        launch_overlap(oa, c->stream);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->h_ovl, c->d_ovl, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    return GMCS_OK;
+}
+
+void pose_mul_d(const double* A, const double* B, double* C) {
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 4; ++k) {
+            double v = A[r * 4] * B[k] + A[r * 4 + 1] * B[4 + k] + A[r * 4 + 2] * B[8 + k];
+            if (k == 3) v += A[r * 4 + 3];
+            C[r * 4 + k] = v;
+        }
+}
+
+// Insert the frame's scan as a keyframe: every particle's current pose, a
+// lattice (field: step kf_h, margin r_t; GICP: voxels of edge kf_h, margin one
+// voxel) over the scan's bounding box.
+int insert_scan_keyframe(gmcs_ctx* c, const float* scan, int N) {
+    const float* dpts = nullptr;
+    float* tmp = nullptr;
+    int rc = stage_points(c, scan, N, &dpts, &tmp);
+    float4* p4 = nullptr;
+    if (!rc && cudaMalloc((void**)&p4, sizeof(float4) * (size_t)N) != cudaSuccess) {
+        cudaGetLastError();
+        rc = GMCS_E_OOM;
+    }
+    float mn[3], mx[3];
+    if (!rc) rc = device_bbox(c, dpts, N, p4, mn, mx);
+    cudaFree(p4);
+    if (!rc) {
+        const bool gicp = c->cfg.model == GMCS_MODEL_GICP;
+        const double h = (double)c->cfg.kf_h, margin = gicp ? h : (double)c->cfg.r_t;
+        gmcs_grid g;
+        for (int a = 0; a < 3; ++a) {
+            const double i0 = std::floor(((double)mn[a] - margin) / h), i1 = std::ceil(((double)mx[a] + margin) / h);
+            g.origin[a] = i0 * h;
+            g.n[a] = (int)(i1 - i0) + 1;
+        }
+        g.h = h;
+        int kid = 0;
+        rc = gmcs_add_keyframe(c, dpts, N, &g, nullptr, &kid);
+    }
+    if (tmp) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+    }
+    return rc;
+}
+
+}  // namespace
 
 int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], const double cov[36],
               const double* u_override, gmcs_step_out* out) {
@@ -944,6 +1118,14 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
     const uint32_t frame = c->frame;
     // odometry path length of this frame (Eq. 9 along the odometry trajectory)
     c->path_now += std::sqrt(delta_T[3] * delta_T[3] + delta_T[7] * delta_T[7] + delta_T[11] * delta_T[11]);
+    // odometry pose of this frame in the last keyframe's frame, and its overlap rate (Sec. III-E)
+    {
+        double o[12];
+        pose_mul_d(c->odo, delta_T, o);
+        std::memcpy(c->odo, o, sizeof(o));
+    }
+    c->ovl_valid = c->cfg.kf_overlap > 0.f && c->K > 0 && N > 0;
+    if (c->ovl_valid && (rc = enqueue_overlap(c, N, c->odo))) return rc;
     if ((rc = run_predict(c, delta_T, cov, nullptr, frame))) return rc;
     if ((rc = run_select(c, nullptr))) return rc;
     for (int s = 0; s < c->cfg.steps; ++s)
@@ -970,9 +1152,19 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
     c->frame = frame + 1;
     c->frames++;
     c->last_valid = true;
+    c->last_N = N;
+    c->last_inserted = 0;
     if (out) {
         CK(cudaStreamSynchronize(c->stream));
         fill_out(*c->h_res, frame, out);
+        if (c->ovl_valid) {
+            out->overlap = (double)*c->h_ovl / (double)N;
+            if (out->overlap < (double)c->cfg.kf_overlap && c->K < c->Kmax) {
+                if ((rc = insert_scan_keyframe(c, scan, N))) return rc;
+                out->kf_inserted = 1;
+                c->last_inserted = 1;
+            }
+        }
         c->last = *out;
     }
     return GMCS_OK;
@@ -1001,6 +1193,8 @@ int gmcs_last_result(gmcs_ctx* c, gmcs_step_out* out) {
     if (!c->last_valid) return GMCS_E_STATE;
     CK(cudaStreamSynchronize(c->stream));
     fill_out(*c->h_res, c->frame - 1, out);
+    if (c->ovl_valid && c->last_N > 0) out->overlap = (double)*c->h_ovl / (double)c->last_N;
+    out->kf_inserted = c->last_inserted;
     return GMCS_OK;
 }
 
@@ -1211,6 +1405,20 @@ int gmcs_prune(gmcs_ctx* c, const double* x, const double* w, const float* ll, i
     CK(cudaMemcpyAsync(hr, c->d_res, sizeof(WeighResult), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (n_dead) *n_dead = hr->pruned;
+    return GMCS_OK;
+}
+
+int gmcs_overlap(gmcs_ctx* c, const float* scan, int N, const double T_rel[12], double* rate) {
+    if (!c || !T_rel || !rate || N <= 0) return GMCS_E_INVALID;
+    if (c->K == 0) return GMCS_E_STATE;
+    for (int e = 0; e < 12; ++e)
+        if (!std::isfinite(T_rel[e])) return GMCS_E_INVALID;
+    c->ovl_valid = false;   // the count buffer is shared with the step's rate
+    int rc = upload_scan(c, scan, N);
+    if (!rc) rc = enqueue_overlap(c, N, T_rel);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    *rate = (double)*c->h_ovl / (double)N;
     return GMCS_OK;
 }
 

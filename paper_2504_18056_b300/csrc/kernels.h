@@ -142,6 +142,32 @@ struct VoxelArgs {
 };
 void launch_voxel_accum(const VoxelArgs& a, cudaStream_t s);
 void launch_voxel_final(const VoxelArgs& a, cudaStream_t s);
+
+// Keyframe insertion by overlap (k_keyframe.cu).
+struct BBoxArgs {
+    const float4* pts;
+    int n;
+    int* mm;                // 6 ints: order-preserving int images of min x, y, z and max x, y, z
+};
+struct OccArgs {
+    const float4* pts;
+    int n;
+    double ox, oy, oz, h;
+    int nx, ny, nz;
+    unsigned char* occ;     // [nz][ny][nx], 1 where a point falls
+};
+struct OverlapArgs {
+    const float4* scan;
+    int n;
+    double T[12];           // scan frame -> keyframe frame (odometry), row-major 3 x 4
+    const unsigned char* occ;
+    double ox, oy, oz, h;
+    int nx, ny, nz;
+    unsigned* count;        // += scan points over occupied voxels
+};
+void launch_bbox(const BBoxArgs& a, cudaStream_t s);
+void launch_occ_fill(const OccArgs& a, cudaStream_t s);
+void launch_overlap(const OverlapArgs& a, cudaStream_t s);
 void launch_finish(const FinishArgs& a, bool grad, cudaStream_t s);
 
 // ------------------------------------------------------------------ weights / resampling

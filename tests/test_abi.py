@@ -40,12 +40,13 @@ def test_binding_covers_header():
 
 def test_struct_sizes_and_defaults():
     import paper_2504_18056_b300 as g
-    assert C.sizeof(g.Config) == 88
-    assert C.sizeof(g.StepOut) == 144
+    assert C.sizeof(g.Config) == 104
+    assert C.sizeof(g.StepOut) == 152
     assert C.sizeof(g.Grid) == 48
     cfg = g.default_config()
     assert cfg.k_nb == 3 and cfg.steps == 3 and abs(cfg.sigma - 0.2) < 1e-7 and abs(cfg.r_t - 1.0) < 1e-7
     assert abs(cfg.prune_w - 1e-8) < 1e-15 and abs(cfg.prune_lr - 1e-16) < 1e-23
+    assert cfg.kf_overlap == 0.0 and cfg.kf_voxel == 1.0 and abs(cfg.kf_h - 0.2) < 1e-7
     assert cfg.model == g.MODEL_FIELD and cfg.knn == 10 and abs(cfg.cov_eps - 1e-3) < 1e-9 and cfg.gicp_tau == 20.0
     assert g.strerror(g.E_CAPACITY) == "capacity exceeded"
 
