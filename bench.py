@@ -264,6 +264,8 @@ def run_native(a, world, rank, local):
         f.step(scans_d[fr], w["odometry"][fr], w["cov"], sync=False)
     torch.cuda.synchronize()
 
+    # L2 gather ceiling: random cell-record reads from a 64 MB buffer (fits the 126 MB L2)
+    l2_gbs = None if gicp else g.probe_gather(64 << 20, 32 if dtype == 0 else 16)
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     f.set_profiling(True)
@@ -365,6 +367,8 @@ def run_native(a, world, rank, local):
                      "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms},
         "gather": {"algorithmic_bytes_per_launch": lookups_per_launch * rec_bytes, "achieved_gbs": gather_gbs,
                    "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src, "frac_of_hbm": gather_gbs / hbm_peak,
+                   "l2_gather_gbs": l2_gbs, "l2_gather_source": "gmcs_probe_gather, 64 MB buffer, random records",
+                   "frac_of_l2_gather": gather_gbs / l2_gbs if l2_gbs else None,
                    "frame_at_hbm_roofline_ms": float(P) * N * 3 * 4 * rec_bytes / (hbm_peak * 1e9) * 1e3},
         "clocks": clk,
         "gpu_launches": int(stats["launches"]),

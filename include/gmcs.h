@@ -346,6 +346,15 @@ int gmcs_prune(gmcs_ctx* ctx, const double* x, const double* w, const float* ll,
 #define GMCS_NOALLOC_MAX_P 262144
 int gmcs_resample_noalloc(const double* w, int P, double u, int* anc, void* cuda_stream);
 
+/*
+ * Calibration, no counterpart in the paper: the rate (GB/s, into *gbs) of
+ * random rec_bytes-sized (16 or 32) record reads from a device buffer of
+ * buffer_bytes, with the 16-byte vector loads of the lookup pass -- with a
+ * buffer that fits L2 (126 MB), the ceiling for lookups whose cells stay in L2.
+ * Allocates and frees the buffer; runs on cuda_stream and synchronises it.
+ */
+int gmcs_probe_gather(uint64_t buffer_bytes, int rec_bytes, void* cuda_stream, double* gbs);
+
 /* ---- state access */
 
 /* Overlap rate (Sec. III-E) of a scan (N x 3 floats, host or device) with the

@@ -112,6 +112,7 @@ _SIGS = {
     "gmcs_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "gmcs_strerror": (C.c_char_p, [C.c_int]),
     "gmcs_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
+    "gmcs_probe_gather": (C.c_int, [C.c_uint64, C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "gmcs_server_create": (C.c_int, [C.POINTER(Config), C.c_uint64, C.c_int, C.POINTER(C.c_void_p)]),
     "gmcs_server_destroy": (C.c_int, [C.c_void_p]),
     "gmcs_server_start": (C.c_int, [C.c_void_p]),
@@ -184,6 +185,14 @@ def resample_noalloc(w, u, anc, stream=None):
     st = _current_stream() if stream is None else C.c_void_p(int(stream))
     _check(lib().gmcs_resample_noalloc(_ptr(w), int(w.shape[0]), float(u), _ptr(anc), st), "gmcs_resample_noalloc")
     return anc
+
+
+def probe_gather(buffer_bytes, rec_bytes=32, stream=None):
+    """Random record-gather rate (GB/s) from a device buffer (gmcs_probe_gather)."""
+    st = _current_stream() if stream is None else C.c_void_p(int(stream))
+    r = C.c_double()
+    _check(lib().gmcs_probe_gather(C.c_uint64(int(buffer_bytes)), int(rec_bytes), st, C.byref(r)), "gmcs_probe_gather")
+    return r.value
 
 
 def default_config(**kw):

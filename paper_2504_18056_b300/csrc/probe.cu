@@ -1,0 +1,90 @@
+// probe.cu -- gather-bandwidth calibration (no counterpart in the paper).
+//
+// The lookup pass reads one cell record per lookup from tables whose touched
+// cells mostly stay in L1/L2, so neither the HBM copy rate nor the FP32 peak
+// alone bounds it. This probe measures the rate of random record gathers from a
+// buffer of a given size (an L2-resident size gives the L2 gather ceiling):
+// every thread reads `per_thread` records at pseudo-random indices (a 32-bit
+// integer hash of its global index and the step, no index traffic) with the
+// same 16-byte vector loads the lookup pass issues, and folds them into a sink.
+#include <cuda_runtime.h>
+
+#include "../../include/gmcs.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    // integer finaliser (xor-shift-multiply), used only to scatter indices
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+template <int VEC>   // 16-byte vectors per record: 2 (32 B) or 1 (16 B)
+__global__ void __launch_bounds__(256) k_probe_gather(const float4* __restrict__ buf, uint32_t nrec, int per_thread,
+                                                      float* __restrict__ sink) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.f;
+    for (int s = 0; s < per_thread; ++s) {
+        const uint32_t r = mix32(tid * 0x9e3779b9u + (uint32_t)s * 0x85ebca6bu) % nrec;
+        const float4* p = buf + (size_t)r * VEC;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const float4 q = __ldg(p + v);
+            acc += q.x + q.y + q.z + q.w;
+        }
+    }
+    sink[tid] = acc;
+}
+
+}  // namespace
+
+extern "C" int gmcs_probe_gather(uint64_t buffer_bytes, int rec_bytes, void* cuda_stream, double* gbs) {
+    if (!gbs || (rec_bytes != 16 && rec_bytes != 32) || buffer_bytes < (uint64_t)rec_bytes ||
+        buffer_bytes / rec_bytes >= ((uint64_t)1 << 32))
+        return GMCS_E_INVALID;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, threads = 256, per_thread = 256;
+    float4* buf = nullptr;
+    float* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = GMCS_OK;
+    if (cudaMalloc((void**)&buf, buffer_bytes) != cudaSuccess ||
+        cudaMalloc((void**)&sink, sizeof(float) * (size_t)blocks * threads) != cudaSuccess) {
+        cudaGetLastError();
+        rc = GMCS_E_OOM;
+    }
+    if (!rc && (cudaMemsetAsync(buf, 0, buffer_bytes, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                cudaEventCreate(&e1) != cudaSuccess))
+        rc = GMCS_E_CUDA;
+    if (!rc) {
+        const uint32_t nrec = (uint32_t)(buffer_bytes / rec_bytes);
+        float best = 1e30f;
+        for (int it = 0; it < 6; ++it) {   // 1 warm-up + 5 timed, best kept
+            cudaEventRecord(e0, s);
+            if (rec_bytes == 32) k_probe_gather<2><<<blocks, threads, 0, s>>>(buf, nrec, per_thread, sink);
+            else k_probe_gather<1><<<blocks, threads, 0, s>>>(buf, nrec, per_thread, sink);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = GMCS_E_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (it > 0 && ms < best) best = ms;
+        }
+        if (!rc) *gbs = (double)blocks * threads * per_thread * rec_bytes / (best * 1e-3) / 1e9;
+    }
+    if (cudaGetLastError() != cudaSuccess && !rc) rc = GMCS_E_CUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    cudaFree(sink);
+    return rc;
+}
