@@ -250,18 +250,24 @@ __global__ void __launch_bounds__(256) k_resample_search(SearchArgs a) { resampl
 
 // State gather by ancestor: current pose and every keyframe pose, then log-weights.
 __device__ __forceinline__ void gather_body(const GatherArgs& a, int vb, int vg) {
-    const size_t per = (size_t)(1 + a.K) * kPoseC;
-    const size_t n = per * a.P;
-    for (size_t e = vb * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)vg * blockDim.x) {
-        const size_t row = e / a.P;
-        const int m = (int)(e % a.P);
+    // work items = (4 consecutive rows, block of particles): the ancestor is read
+    // once and the four row reads are independent loads in flight together
+    constexpr int kRows = 4;
+    static_assert(kPoseC % kRows == 0, "row groups do not straddle pose and keyframe rows");
+    const size_t groups = (size_t)(1 + a.K) * kPoseC / kRows;
+    const size_t per_row = (a.P + blockDim.x - 1) / blockDim.x;
+    for (size_t item = vb; item < groups * per_row; item += vg) {
+        const size_t row = item / per_row * kRows;
+        const int m = (int)(item % per_row) * blockDim.x + threadIdx.x;
+        if (m >= a.P) continue;
         const int src = a.anc[m];
-        if (row < kPoseC) {
-            a.pose_dst[row * a.ld + m] = a.pose_src[row * a.ld + src];
-        } else {
-            const size_t r2 = row - kPoseC;
-            a.kf_dst[r2 * a.ld + m] = a.kf_src[r2 * a.ld + src];
-        }
+        const float* from = row < kPoseC ? a.pose_src + row * a.ld : a.kf_src + (row - kPoseC) * a.ld;
+        float* to = row < kPoseC ? a.pose_dst + row * a.ld : a.kf_dst + (row - kPoseC) * a.ld;
+        float v[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) v[r] = from[r * a.ld + src];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) to[r * a.ld + m] = v[r];
     }
     const double uni = -log((double)a.P);
     for (int m = vb * blockDim.x + threadIdx.x; m < a.P; m += vg * blockDim.x) {
