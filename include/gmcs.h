@@ -103,7 +103,8 @@ typedef struct {
 } gmcs_config;
 
 /* Lattice of one keyframe table, in the keyframe's own frame: vertex (ix,iy,iz)
- * sits at origin + h*(ix,iy,iz), 0 <= ix < n[0] etc. At least 2 vertices per axis. */
+ * sits at origin + h*(ix,iy,iz), 0 <= ix < n[0] etc. At least 2 and at most 2^22
+ * vertices per axis. */
 typedef struct {
     double origin[3];
     double h;

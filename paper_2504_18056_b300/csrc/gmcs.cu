@@ -930,8 +930,8 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     if (!c->have_particles) return GMCS_E_STATE;
     if (c->K >= c->Kmax) return GMCS_E_CAPACITY;
     if (c->cfg.model == GMCS_MODEL_GICP) return add_keyframe_gicp(c, pts, n, grid, kf_poses, kf_id);
-    for (int a = 0; a < 3; ++a)
-        if (grid->n[a] < 2 || !std::isfinite(grid->origin[a])) return GMCS_E_INVALID;
+    for (int a = 0; a < 3; ++a)   // the lookup's floor is exact below 2^22 cells per axis
+        if (grid->n[a] < 2 || grid->n[a] > (1 << 22) || !std::isfinite(grid->origin[a])) return GMCS_E_INVALID;
     if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return GMCS_E_INVALID;
     const size_t nx = grid->n[0], ny = grid->n[1], nz = grid->n[2];
     const size_t nv = nx * ny * nz;
