@@ -48,7 +48,7 @@ struct gmcs_ctx {
     float* part = nullptr;
     size_t part_floats = 0;
     float4* scan = nullptr;
-    float4* scov = nullptr;          // GICP: scan point covariances, 2 float4 per point
+    float4* scov = nullptr;          // GICP: scan point normals (plane-regularised covariances)
     float* stage = nullptr;          // N x 3 points / P x 6 noise staging
     size_t stage_floats = 0;
     double* wpart = nullptr;

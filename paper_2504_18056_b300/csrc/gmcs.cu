@@ -59,7 +59,7 @@ size_t ctx_device_bytes(int max_particles, int max_keyframes, int max_points) {
     size_t b = 0;
     b += 2 * (sizeof(float) * kPoseC * ld + sizeof(float) * kPoseC * ld * max_keyframes);
     b += sizeof(double) * ld * 2 + sizeof(float) * ld + sizeof(float) * 6 * ld;   // logw, w, ll, gbuf
-    b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * 3 * max_points + sizeof(float) * stage;
+    b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * 2 * max_points + sizeof(float) * stage;
     b += sizeof(double) * kWeighPart * 148 * 4 + sizeof(unsigned) + sizeof(WeighResult);
     b += sizeof(unsigned long long) * (ld + 2 * (nb + 1)) + sizeof(int) * ld;
     b += sizeof(TableDesc) * max_keyframes + sizeof(float) * max_keyframes + sizeof(int) * 8 + sizeof(unsigned);
@@ -182,7 +182,7 @@ int upload_scan(gmcs_ctx* c, const float* scan, int N) {
     ka.k = c->cfg.knn;
     ka.eps = (double)c->cfg.cov_eps;
     ka.cov64 = nullptr;
-    ka.cov32 = c->scov;
+    ka.nrm32 = c->scov;
     {
         Launch L(c, K_MISC);
         launch_knn_cov(ka, c->stream);
@@ -208,6 +208,8 @@ void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* o
     pa.tables = c->d_tables;
     pa.scan = c->scan;
     pa.scov = c->scov;
+    pa.cov_w = 1.f - c->cfg.cov_eps;
+    pa.cov_eps = c->cfg.cov_eps;
     pa.tau = c->cfg.gicp_tau;
     pa.model = c->cfg.model;
     pa.part = c->part;
@@ -589,7 +591,7 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     if (!rc) rc = dalloc(c, &c->nbr, (size_t)GMCS_MAX_NB * ld);
     if (!rc) rc = dalloc(c, &c->part, c->part_floats);
     if (!rc) rc = dalloc(c, &c->scan, (size_t)max_points);
-    if (!rc) rc = dalloc(c, &c->scov, (size_t)2 * max_points);
+    if (!rc) rc = dalloc(c, &c->scov, (size_t)max_points);
     if (!rc) rc = dalloc(c, &c->stage, c->stage_floats);
     if (!rc) rc = dalloc(c, &c->wpart, (size_t)kWeighPart * 148 * 4);
     if (!rc) rc = dalloc(c, &c->counter, 1);
@@ -703,7 +705,7 @@ int build_gicp_map(gmcs_ctx* c, const float* dpts, int n, const gmcs_grid* grid,
         ka.k = c->cfg.knn;
         ka.eps = (double)c->cfg.cov_eps;
         ka.cov64 = cov;
-        ka.cov32 = nullptr;
+        ka.nrm32 = nullptr;
         {
             Launch L(c, K_TABLE);
             launch_knn_cov(ka, c->stream);
@@ -1507,7 +1509,7 @@ int gmcs_point_covariances(gmcs_ctx* c, const float* pts, int n, double* cov) {
         ka.k = c->cfg.knn;
         ka.eps = (double)c->cfg.cov_eps;
         ka.cov64 = dcov;
-        ka.cov32 = nullptr;
+        ka.nrm32 = nullptr;
         {
             Launch L(c, K_MISC);
             launch_knn_cov(ka, c->stream);

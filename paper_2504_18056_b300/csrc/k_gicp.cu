@@ -8,14 +8,18 @@
 // covariances (the voxel-based correspondence of Sec. III-C1: a transformed
 // scan point corresponds to the voxel it falls in).
 //
-// The lookup pass works in the sensor frame of the particle's current pose:
-// with kT_t = [R | t] and x = R mu + t,
-//   e~ = R^T (mu' - x),  Omega~ = (R^T Sigma' R + Sigma_j)^-1 = R^T Omega R,
-//   d2 = e~^T Omega~ e~   (= e^T Omega e of Eq. 3-4),
-// and the Gauss-Newton terms of Eq. 5-6 for the right perturbation of the
-// current pose, J~ = [-[mu]x | I]:
-//   b += J~^T Omega~ e~ = [mu x q; q],  q = Omega~ e~,
-//   H += J~^T Omega~ J~ = [[-[mu]x Omega~ [mu]x, [mu]x Omega~], [.., Omega~]].
+// The lookup pass works in each neighbour keyframe's frame. With kT_t = [R | t],
+// the rotated point x' = R mu and x = x' + t,
+//   e = mu' - x,  Omega = (Sigma' + R Sigma_j R^T)^-1,  d2 = e^T Omega e  (Eq. 3-4),
+// where the scan covariance is plane-regularised, Sigma_j = I - (1 - eps) n n^T,
+// so R Sigma_j R^T = I - (1 - eps) m m^T with m = R n (a rank-one update, no
+// 3x3 rotation of a matrix per lookup). The right perturbation of the current
+// pose moves x by R (omega x mu + v) = [-[x']x | I] diag(R, R) xi (R [mu]x = [R mu]x R),
+// so the Gauss-Newton terms of Eq. 5-6 are accumulated per keyframe as
+//   b_k += [x' x q; q],  q = Omega e,
+//   H_k += [[-[x']x Omega [x']x, [x']x Omega], [.., Omega]]
+// and rotated once per (particle, keyframe): b += diag(R, R)^T b_k,
+// H += diag(R, R)^T H_k diag(R, R).
 // Every (point, neighbour) pair adds one term to the log-likelihood: -d2 for an
 // inlier (d2 < tau), -tau when the voxel is empty, outside the map, or d2 >= tau.
 #include <math.h>
@@ -186,10 +190,7 @@ __global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
         double* o = a.cov64 + 6 * (size_t)i;
         o[0] = sxx; o[1] = sxy; o[2] = sxz; o[3] = syy; o[4] = syz; o[5] = szz;
     }
-    if (a.cov32) {
-        a.cov32[2 * (size_t)i] = make_float4((float)sxx, (float)sxy, (float)sxz, (float)syy);
-        a.cov32[2 * (size_t)i + 1] = make_float4((float)syz, (float)szz, 0.f, 0.f);
-    }
+    if (a.nrm32) a.nrm32[i] = make_float4((float)n[0], (float)n[1], (float)n[2], 0.f);
 }
 
 // ------------------------------------------------------------------ voxel maps
@@ -232,6 +233,35 @@ __global__ void k_voxel_final(VoxelArgs a) {
 
 // ------------------------------------------------------------------ the lookup pass
 
+// R^T A R for a symmetric A given by its upper triangle (a00 a01 a02 a11 a12 a22),
+// written back in place.
+__device__ __forceinline__ void rot_sym(const float* R, float* u) {
+    const float A[9] = {u[0], u[1], u[2], u[1], u[3], u[4], u[2], u[4], u[5]};
+    float M[9];   // A R
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[r * 3 + c] = fmaf(A[r * 3], R[c], fmaf(A[r * 3 + 1], R[3 + c], A[r * 3 + 2] * R[6 + c]));
+    int e = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) u[e++] = fmaf(R[r], M[c], fmaf(R[3 + r], M[3 + c], R[6 + r] * M[6 + c]));
+}
+
+// R^T A R for a general 3x3 A (row-major), in place.
+__device__ __forceinline__ void rot_gen(const float* R, float* A) {
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[r * 3 + c] = fmaf(A[r * 3], R[c], fmaf(A[r * 3 + 1], R[3 + c], A[r * 3 + 2] * R[6 + c]));
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[r * 3 + c] = fmaf(R[r], M[c], fmaf(R[3 + r], M[3 + c], R[6 + r] * M[6 + c]));
+}
+
 template <bool GRAD>
 __global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
     constexpr int NACC = GRAD ? kAccGicp : 1;
@@ -244,7 +274,7 @@ __global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
     if (i < a.P && j0 < j1) {
         float Tt[12];
         load_pose(a.pose, a.ld, i, Tt);
-        const float tau = a.tau;
+        const float tau = a.tau, wn = a.cov_w, ce = a.cov_eps;
         float lsum = 0.f;
         for (int s = 0; s < a.k_nb; ++s) {
             const int k = a.nbr[(size_t)s * a.ld + i];
@@ -258,50 +288,46 @@ __global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
             const float R20 = rel[8], R21 = rel[9], R22 = rel[10], t2 = rel[11];
             const float4* __restrict__ recs = reinterpret_cast<const float4*>(td.cells);
             const uint32_t ncx = (uint32_t)td.ncx, ncy = (uint32_t)td.ncy, ncz = (uint32_t)td.ncz;
+            float bk[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float hk[21];
+#pragma unroll
+            for (int e = 0; e < 21; ++e) hk[e] = 0.f;
+            float nin = 0.f;
             for (int j = j0; j < j1; ++j) {
                 const float4 p = __ldg(a.scan + j);
-                const float x0 = fmaf(R00, p.x, fmaf(R01, p.y, fmaf(R02, p.z, t0)));
-                const float x1 = fmaf(R10, p.x, fmaf(R11, p.y, fmaf(R12, p.z, t1)));
-                const float x2 = fmaf(R20, p.x, fmaf(R21, p.y, fmaf(R22, p.z, t2)));
+                const float r0 = fmaf(R00, p.x, fmaf(R01, p.y, R02 * p.z));
+                const float r1 = fmaf(R10, p.x, fmaf(R11, p.y, R12 * p.z));
+                const float r2 = fmaf(R20, p.x, fmaf(R21, p.y, R22 * p.z));
+                const float x0 = r0 + t0, x1 = r1 + t1, x2 = r2 + t2;
                 const int cx = (int)floorf((x0 - td.ox) * td.inv_h);
                 const int cy = (int)floorf((x1 - td.oy) * td.inv_h);
                 const int cz = (int)floorf((x2 - td.oz) * td.inv_h);
                 const bool inside = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-                float4 m = make_float4(0.f, 0.f, 0.f, 0.f), v0 = m, v1 = m;
+                float4 mv = make_float4(0.f, 0.f, 0.f, 0.f), v0 = mv, v1 = mv;
                 if (inside) {
                     const size_t idx = ((size_t)cz * ncy + (size_t)cy) * ncx + (size_t)cx;
-                    m = __ldg(recs + 3 * idx);
+                    mv = __ldg(recs + 3 * idx);
                     v0 = __ldg(recs + 3 * idx + 1);
                     v1 = __ldg(recs + 3 * idx + 2);
                 }
-                if (!(m.w > 0.f)) {
+                if (!(mv.w > 0.f)) {
                     lsum -= tau;
                     continue;
                 }
-                // residual in the sensor frame: e~ = R^T (mu' - x)
-                const float e0 = m.x - x0, e1 = m.y - x1, e2 = m.z - x2;
-                const float f0 = fmaf(R00, e0, fmaf(R10, e1, R20 * e2));
-                const float f1 = fmaf(R01, e0, fmaf(R11, e1, R21 * e2));
-                const float f2 = fmaf(R02, e0, fmaf(R12, e1, R22 * e2));
-                // Sigma' R (columns c of R), then R^T (Sigma' R): the map covariance in the sensor frame
-                const float Sxx = v0.x, Sxy = v0.y, Sxz = v0.z, Syy = v0.w, Syz = v1.x, Szz = v1.y;
-                const float M00 = fmaf(Sxx, R00, fmaf(Sxy, R10, Sxz * R20));
-                const float M01 = fmaf(Sxx, R01, fmaf(Sxy, R11, Sxz * R21));
-                const float M02 = fmaf(Sxx, R02, fmaf(Sxy, R12, Sxz * R22));
-                const float M10 = fmaf(Sxy, R00, fmaf(Syy, R10, Syz * R20));
-                const float M11 = fmaf(Sxy, R01, fmaf(Syy, R11, Syz * R21));
-                const float M12 = fmaf(Sxy, R02, fmaf(Syy, R12, Syz * R22));
-                const float M20 = fmaf(Sxz, R00, fmaf(Syz, R10, Szz * R20));
-                const float M21 = fmaf(Sxz, R01, fmaf(Syz, R11, Szz * R21));
-                const float M22 = fmaf(Sxz, R02, fmaf(Syz, R12, Szz * R22));
-                const float4 c0 = __ldg(a.scov + 2 * j), c1 = __ldg(a.scov + 2 * j + 1);
-                const float a00 = fmaf(R00, M00, fmaf(R10, M10, fmaf(R20, M20, c0.x)));
-                const float a01 = fmaf(R00, M01, fmaf(R10, M11, fmaf(R20, M21, c0.y)));
-                const float a02 = fmaf(R00, M02, fmaf(R10, M12, fmaf(R20, M22, c0.z)));
-                const float a11 = fmaf(R01, M01, fmaf(R11, M11, fmaf(R21, M21, c0.w)));
-                const float a12 = fmaf(R01, M02, fmaf(R11, M12, fmaf(R21, M22, c1.x)));
-                const float a22 = fmaf(R02, M02, fmaf(R12, M12, fmaf(R22, M22, c1.y)));
-                // Omega~ = C^-1 by cofactors
+                const float e0 = mv.x - x0, e1 = mv.y - x1, e2 = mv.z - x2;
+                // C = Sigma' + eps m m^T + (I - m m^T), m = R n; the diagonal of I - m m^T is
+                // taken as the sum of the other two squares (no cancellation in the thin direction)
+                const float4 nj = __ldg(a.scov + j);
+                const float m0 = fmaf(R00, nj.x, fmaf(R01, nj.y, R02 * nj.z));
+                const float m1 = fmaf(R10, nj.x, fmaf(R11, nj.y, R12 * nj.z));
+                const float m2 = fmaf(R20, nj.x, fmaf(R21, nj.y, R22 * nj.z));
+                const float s0 = m0 * m0, s1 = m1 * m1, s2 = m2 * m2;
+                const float a00 = fmaf(ce, s0, v0.x + (s1 + s2));
+                const float a11 = fmaf(ce, s1, v0.w + (s0 + s2));
+                const float a22 = fmaf(ce, s2, v1.y + (s0 + s1));
+                const float wm0 = wn * m0, wm1 = wn * m1;
+                const float a01 = fmaf(-wm0, m1, v0.y), a02 = fmaf(-wm0, m2, v0.z), a12 = fmaf(-wm1, m2, v1.x);
+                // Omega = C^-1 by cofactors
                 const float i00 = fmaf(a11, a22, -a12 * a12);
                 const float i01 = fmaf(a02, a12, -a01 * a22);
                 const float i02 = fmaf(a01, a12, -a02 * a11);
@@ -312,46 +338,70 @@ __global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
                 const float rd = 1.f / det;
                 const float o00 = i00 * rd, o01 = i01 * rd, o02 = i02 * rd;
                 const float o11 = i11 * rd, o12 = i12 * rd, o22 = i22 * rd;
-                const float q0 = fmaf(o00, f0, fmaf(o01, f1, o02 * f2));
-                const float q1 = fmaf(o01, f0, fmaf(o11, f1, o12 * f2));
-                const float q2 = fmaf(o02, f0, fmaf(o12, f1, o22 * f2));
-                const float d2 = fmaf(f0, q0, fmaf(f1, q1, f2 * q2));
+                const float q0 = fmaf(o00, e0, fmaf(o01, e1, o02 * e2));
+                const float q1 = fmaf(o01, e0, fmaf(o11, e1, o12 * e2));
+                const float q2 = fmaf(o02, e0, fmaf(o12, e1, o22 * e2));
+                const float d2 = fmaf(e0, q0, fmaf(e1, q1, e2 * q2));
                 if (!(d2 < tau)) {
                     lsum -= tau;
                     continue;
                 }
                 lsum -= d2;
                 if constexpr (GRAD) {
-                    // b = [mu x q; q]
-                    acc[1] += fmaf(p.y, q2, -p.z * q1);
-                    acc[2] += fmaf(p.z, q0, -p.x * q2);
-                    acc[3] += fmaf(p.x, q1, -p.y * q0);
-                    acc[4] += q0;
-                    acc[5] += q1;
-                    acc[6] += q2;
-                    // K = [mu]x Omega~ (rows: -mz O1 + my O2, mz O0 - mx O2, -my O0 + mx O1)
-                    const float K00 = fmaf(-p.z, o01, p.y * o02), K01 = fmaf(-p.z, o11, p.y * o12),
-                                K02 = fmaf(-p.z, o12, p.y * o22);
-                    const float K10 = fmaf(p.z, o00, -p.x * o02), K11 = fmaf(p.z, o01, -p.x * o12),
-                                K12 = fmaf(p.z, o02, -p.x * o22);
-                    const float K20 = fmaf(-p.y, o00, p.x * o01), K21 = fmaf(-p.y, o01, p.x * o11),
-                                K22 = fmaf(-p.y, o02, p.x * o12);
-                    // rotation block -K [mu]x: (K [mu]x)[r] = (K_r1 mz - K_r2 my, K_r2 mx - K_r0 mz, K_r0 my - K_r1 mx)
-                    acc[7] -= fmaf(K01, p.z, -K02 * p.y);
-                    acc[8] -= fmaf(K02, p.x, -K00 * p.z);
-                    acc[9] -= fmaf(K00, p.y, -K01 * p.x);
-                    acc[13] -= fmaf(K12, p.x, -K10 * p.z);
-                    acc[14] -= fmaf(K10, p.y, -K11 * p.x);
-                    acc[18] -= fmaf(K20, p.y, -K21 * p.x);
+                    // b_k = [x' x q; q]
+                    bk[0] += fmaf(r1, q2, -r2 * q1);
+                    bk[1] += fmaf(r2, q0, -r0 * q2);
+                    bk[2] += fmaf(r0, q1, -r1 * q0);
+                    bk[3] += q0;
+                    bk[4] += q1;
+                    bk[5] += q2;
+                    // K = [x']x Omega (rows: -x2 O1 + x1 O2, x2 O0 - x0 O2, -x1 O0 + x0 O1)
+                    const float K00 = fmaf(-r2, o01, r1 * o02), K01 = fmaf(-r2, o11, r1 * o12),
+                                K02 = fmaf(-r2, o12, r1 * o22);
+                    const float K10 = fmaf(r2, o00, -r0 * o02), K11 = fmaf(r2, o01, -r0 * o12),
+                                K12 = fmaf(r2, o02, -r0 * o22);
+                    const float K20 = fmaf(-r1, o00, r0 * o01), K21 = fmaf(-r1, o01, r0 * o11),
+                                K22 = fmaf(-r1, o02, r0 * o12);
+                    // rotation block -K [x']x
+                    hk[0] -= fmaf(K01, r2, -K02 * r1);
+                    hk[1] -= fmaf(K02, r0, -K00 * r2);
+                    hk[2] -= fmaf(K00, r1, -K01 * r0);
+                    hk[6] -= fmaf(K12, r0, -K10 * r2);
+                    hk[7] -= fmaf(K10, r1, -K11 * r0);
+                    hk[11] -= fmaf(K20, r1, -K21 * r0);
                     // cross block K
-                    acc[10] += K00; acc[11] += K01; acc[12] += K02;
-                    acc[15] += K10; acc[16] += K11; acc[17] += K12;
-                    acc[19] += K20; acc[20] += K21; acc[21] += K22;
-                    // translation block Omega~
-                    acc[22] += o00; acc[23] += o01; acc[24] += o02;
-                    acc[25] += o11; acc[26] += o12; acc[27] += o22;
-                    acc[28] += 1.f;
+                    hk[3] += K00; hk[4] += K01; hk[5] += K02;
+                    hk[8] += K10; hk[9] += K11; hk[10] += K12;
+                    hk[12] += K20; hk[13] += K21; hk[14] += K22;
+                    // translation block Omega
+                    hk[15] += o00; hk[16] += o01; hk[17] += o02;
+                    hk[18] += o11; hk[19] += o12; hk[20] += o22;
+                    nin += 1.f;
                 }
+            }
+            if constexpr (GRAD) {
+                // back to the current pose's tangent space: b += D^T b_k, H += D^T H_k D, D = diag(R, R)
+                const float R[9] = {R00, R01, R02, R10, R11, R12, R20, R21, R22};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    acc[1 + c] += fmaf(R[c], bk[0], fmaf(R[3 + c], bk[1], R[6 + c] * bk[2]));
+                    acc[4 + c] += fmaf(R[c], bk[3], fmaf(R[3 + c], bk[4], R[6 + c] * bk[5]));
+                }
+                float tl[6] = {hk[0], hk[1], hk[2], hk[6], hk[7], hk[11]};
+                float tr[9] = {hk[3], hk[4], hk[5], hk[8], hk[9], hk[10], hk[12], hk[13], hk[14]};
+                float br[6] = {hk[15], hk[16], hk[17], hk[18], hk[19], hk[20]};
+                rot_sym(R, tl);
+                rot_gen(R, tr);
+                rot_sym(R, br);
+                // accumulator layout: H upper triangle row-major at acc[7..27]
+                acc[7] += tl[0]; acc[8] += tl[1]; acc[9] += tl[2];
+                acc[13] += tl[3]; acc[14] += tl[4]; acc[18] += tl[5];
+                acc[10] += tr[0]; acc[11] += tr[1]; acc[12] += tr[2];
+                acc[15] += tr[3]; acc[16] += tr[4]; acc[17] += tr[5];
+                acc[19] += tr[6]; acc[20] += tr[7]; acc[21] += tr[8];
+                acc[22] += br[0]; acc[23] += br[1]; acc[24] += br[2];
+                acc[25] += br[3]; acc[26] += br[4]; acc[27] += br[5];
+                acc[28] += nin;
             }
         }
         acc[0] = lsum;

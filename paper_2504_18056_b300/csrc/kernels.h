@@ -79,7 +79,8 @@ struct PassArgs {
     const int* nbr;
     const TableDesc* tables;
     const float4* scan;
-    const float4* scov;     // GICP: 2 float4 per point, covariance xx xy xz yy | yz zz - -
+    const float4* scov;     // GICP: scan point normals (n, 0); covariance I - cov_w n n^T
+    float cov_w, cov_eps;   // GICP: 1 - eps and eps of the plane regularisation
     float tau;              // GICP: cap of a term's e^T Omega e
     int model;              // 0 voxel likelihood field, 1 GICP
     float* part;            // [groups][nacc][ld]
@@ -127,7 +128,7 @@ struct KnnCovArgs {
     int n, k;               // k nearest (the point itself included), k <= kKnnMax
     double eps;             // plane regularisation: eigenvalues (eps, 1, 1)
     double* cov64;          // optional n x 6 doubles (xx xy xz yy yz zz)
-    float4* cov32;          // optional 2 float4 per point (xx xy xz yy | yz zz 0 0)
+    float4* nrm32;          // optional unit normal per point (n, 0): covariance I - (1 - eps) n n^T
 };
 constexpr int kKnnMax = 32;
 void launch_knn_cov(const KnnCovArgs& a, cudaStream_t s);
