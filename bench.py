@@ -38,7 +38,7 @@ FLOPS_GRAD_LOOKUP = 87          # FP32 flops of one gradient lookup (FMA = 2); b
 # GICP model: FP32 flops (FMA = 2) of an inlier lookup with the Gauss-Newton terms in
 # the keyframe-frame form the kernel uses, and of a lookup that stops at an empty voxel
 # (transform and cell only); lookups rejected by the cap are counted as the latter
-FLOPS_GICP_INLIER = 183
+FLOPS_GICP_INLIER = 198
 FLOPS_GICP_MISS = 24
 GICP_VOXEL = 1.0                # m, voxel edge of the GICP keyframe maps
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -321,7 +321,7 @@ def run_native(a, world, rank, local):
     rec_bytes = 32 if dtype == 0 else 16
     avg_ms = pg["ms"] / max(pg["launches"], 1)
     # algorithmic work of one gradient lookup: 87 FP32 flops (FMA = 2), one cell record read;
-    # GICP: 183 per inlier, 24 per other lookup, 48 B voxel record per lookup
+    # GICP: 198 per inlier, 24 per other lookup, 48 B voxel record per lookup
     if gicp:
         flops_per_launch = lookups_per_launch * (inlier_frac * FLOPS_GICP_INLIER + (1 - inlier_frac) * FLOPS_GICP_MISS)
         rec_bytes = 48
