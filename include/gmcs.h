@@ -433,7 +433,7 @@ typedef struct {
     double latency_p50_s, latency_p99_s, latency_max_s, latency_mean_s;   /* submission to completion */
 } gmcs_server_stats;
 
-/* cfg: shared by all sessions (k_nb must be 3, voxel field model); budget_bytes: device memory the
+/* cfg: shared by all sessions (k_nb must be 3); budget_bytes: device memory the
  * sessions may hold; max_sessions: open-session limit. Errors: GMCS_E_INVALID,
  * GMCS_E_OOM, GMCS_E_CUDA. */
 int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_sessions, gmcs_server** out);

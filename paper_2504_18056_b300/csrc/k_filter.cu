@@ -660,15 +660,6 @@ __global__ void __launch_bounds__(128) k_chain(const float* __restrict__ xi, con
 // Walk the virtual blocks of every session in a BatchList; the trailing barrier
 // keeps a CTA's shared memory from being reused by the next virtual block while
 // slower threads still read it.
-#define GMCS_BATCH_LOOP(L, CALL)                                               \
-    for (int item = blockIdx.x; item < (L)->total; item += gridDim.x) {        \
-        int s = 0;                                                             \
-        while (s + 1 < (L)->count && (L)->offset[s + 1] <= item) ++s;          \
-        const int vb = item - (L)->offset[s], vg = (L)->vgrid[s];              \
-        (void)vg;                                                              \
-        CALL;                                                                  \
-        __syncthreads();                                                       \
-    }
 
 __global__ void __launch_bounds__(256) k_scan_pack_b(const BatchList<ScanPackArgs>* L) {
     GMCS_BATCH_LOOP(L, const ScanPackArgs a = L->args[s]; scan_pack_body(a, vb, vg));

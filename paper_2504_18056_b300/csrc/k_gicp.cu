@@ -88,11 +88,11 @@ __device__ __forceinline__ void sym3_min_eigvec(double a00, double a01, double a
 // cloud with ties to the lower index. Lane 0 takes their FP64 covariance (1/k)
 // and the plane regularisation.
 template <int KM>
-__global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
+__device__ __forceinline__ void knn_cov_body(const KnnCovArgs& a, int vb) {
     constexpr int kTile = 1024;
     __shared__ float4 tile[kTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int i = vb * (blockDim.x >> 5) + warp;
     const bool act = i < a.n;
     const float4 p = act ? a.pts[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int k = min(a.k, a.n);
@@ -193,6 +193,16 @@ __global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
     if (a.nrm32) a.nrm32[i] = make_float4((float)n[0], (float)n[1], (float)n[2], 0.f);
 }
 
+template <int KM>
+__global__ void __launch_bounds__(128) k_knn_cov(KnnCovArgs a) {
+    knn_cov_body<KM>(a, blockIdx.x);
+}
+
+template <int KM>
+__global__ void __launch_bounds__(128) k_knn_cov_b(const BatchList<KnnCovArgs>* L) {
+    GMCS_BATCH_LOOP(L, const KnnCovArgs a = L->args[s]; knn_cov_body<KM>(a, vb));
+}
+
 // ------------------------------------------------------------------ voxel maps
 
 __global__ void k_voxel_accum(VoxelArgs a) {
@@ -263,9 +273,9 @@ __device__ __forceinline__ void rot_gen(const float* R, float* A) {
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
+__device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
     constexpr int NACC = GRAD ? kAccGicp : 1;
-    const WarpWork ww = warp_work(a, blockIdx.x);
+    const WarpWork ww = warp_work(a, vb);
     const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
     float acc[NACC];
 #pragma unroll
@@ -409,14 +419,68 @@ __global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
     store_partials<NACC>(a, acc, ww);
 }
 
+template <bool GRAD>
+__global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
+    gicp_body<GRAD>(a, blockIdx.x);
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kPassThreads) k_gicp_b(const BatchList<PassArgs>* L) {
+    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; gicp_body<GRAD>(a, vb));
+}
+
 // ------------------------------------------------------------------ launchers
+
+int grid_knn_cov(int n) { return (n + 3) / 4; }   // 4 points (warps) per CTA
 
 void launch_knn_cov(const KnnCovArgs& a, cudaStream_t s) {
     if (a.n <= 0) return;
-    const int grid = (a.n + 3) / 4;   // 4 points (warps) per CTA
+    const int grid = grid_knn_cov(a.n);
     if (a.k <= 8) k_knn_cov<8><<<grid, 128, 0, s>>>(a);
     else if (a.k <= 16) k_knn_cov<16><<<grid, 128, 0, s>>>(a);
     else k_knn_cov<32><<<grid, 128, 0, s>>>(a);
+}
+
+template <typename K>
+static int persistent_grid_g(K kernel, int threads) {
+    int per_sm = 0, dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * sms;
+}
+
+template <int KM>
+static int grid_knn_b() {
+    static const int g = persistent_grid_g(k_knn_cov_b<KM>, 128);
+    return g;
+}
+template <bool G>
+static int grid_gicp_b() {
+    static const int g = persistent_grid_g(k_gicp_b<G>, kPassThreads);
+    return g;
+}
+
+void launch_knn_cov_b(const BatchList<KnnCovArgs>* L, int k, cudaStream_t s) {
+    if (k <= 8) k_knn_cov_b<8><<<grid_knn_b<8>(), 128, 0, s>>>(L);
+    else if (k <= 16) k_knn_cov_b<16><<<grid_knn_b<16>(), 128, 0, s>>>(L);
+    else k_knn_cov_b<32><<<grid_knn_b<32>(), 128, 0, s>>>(L);
+}
+
+void launch_gicp_b(const BatchList<PassArgs>* L, bool grad, cudaStream_t s) {
+    if (grad) k_gicp_b<true><<<grid_gicp_b<true>(), kPassThreads, 0, s>>>(L);
+    else k_gicp_b<false><<<grid_gicp_b<false>(), kPassThreads, 0, s>>>(L);
+}
+
+void prepare_gicp_batched() {
+    grid_knn_b<8>();
+    grid_knn_b<16>();
+    grid_knn_b<32>();
+    grid_gicp_b<true>();
+    grid_gicp_b<false>();
 }
 
 void launch_voxel_accum(const VoxelArgs& a, cudaStream_t s) {

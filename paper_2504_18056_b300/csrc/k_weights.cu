@@ -436,14 +436,6 @@ __global__ void __launch_bounds__(256) k_prune_reweigh(PruneArgs a) { prune_rewe
 
 // ------------------------------------------------------------------ batched launches
 
-#define GMCS_BATCH_LOOP(L, CALL)                                               \
-    for (int item = blockIdx.x; item < (L)->total; item += gridDim.x) {        \
-        int s = 0;                                                             \
-        while (s + 1 < (L)->count && (L)->offset[s + 1] <= item) ++s;          \
-        const int vb = item - (L)->offset[s], vg = (L)->vgrid[s];              \
-        CALL;                                                                  \
-        __syncthreads();                                                       \
-    }
 
 __global__ void __launch_bounds__(kWeighThreads) k_weigh_b(const BatchList<WeighArgs>* L) {
     GMCS_BATCH_LOOP(L, const WeighArgs a = L->args[s]; weigh_body(a, vb, vg));

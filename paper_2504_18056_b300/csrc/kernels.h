@@ -143,6 +143,7 @@ struct VoxelArgs {
 };
 void launch_voxel_accum(const VoxelArgs& a, cudaStream_t s);
 void launch_voxel_final(const VoxelArgs& a, cudaStream_t s);
+int grid_knn_cov(int n);
 
 // Keyframe insertion by overlap (k_keyframe.cu).
 struct BBoxArgs {
@@ -285,6 +286,18 @@ void launch_prune_reweigh(const PruneArgs& a, cudaStream_t s);
 // single-session kernel with blockIdx / gridDim replaced by (vb, vgrid[s]).
 constexpr int kMaxSlots = 32;
 
+// Persistent-grid walk over a BatchList: CTA-sized items, item -> (session s,
+// virtual block vb of vgrid[s]); every thread reaches the barrier after each item.
+#define GMCS_BATCH_LOOP(L, CALL)                                               \
+    for (int item = blockIdx.x; item < (L)->total; item += gridDim.x) {        \
+        int s = 0;                                                             \
+        while (s + 1 < (L)->count && (L)->offset[s + 1] <= item) ++s;          \
+        const int vb = item - (L)->offset[s], vg = (L)->vgrid[s];              \
+        (void)vg;                                                              \
+        CALL;                                                                  \
+        __syncthreads();                                                       \
+    }
+
 template <typename A>
 struct BatchList {
     int count;                 // sessions in this launch
@@ -308,6 +321,9 @@ void launch_prune_mark_b(const BatchList<PruneArgs>* L, cudaStream_t s);
 void launch_prune_totals_b(const BatchList<PruneArgs>* L, cudaStream_t s);
 void launch_prune_spawn_b(const BatchList<PruneArgs>* L, cudaStream_t s);
 void launch_prune_reweigh_b(const BatchList<PruneArgs>* L, cudaStream_t s);
+void launch_knn_cov_b(const BatchList<KnnCovArgs>* L, int k, cudaStream_t s);
+void launch_gicp_b(const BatchList<PassArgs>* L, bool grad, cudaStream_t s);
+void prepare_gicp_batched();
 // Size every persistent grid (occupancy queries) before a graph capture records the launches.
 void prepare_filter_batched();
 void prepare_weights_batched();

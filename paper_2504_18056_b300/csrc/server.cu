@@ -44,6 +44,7 @@ double now_s() {
 
 struct TickDesc {
     BatchList<ScanPackArgs> pack;
+    BatchList<KnnCovArgs> knn;       // GICP: scan normals
     BatchList<PredictArgs> pred;
     BatchList<SelectArgs> sel;
     BatchList<PassArgs> pgrad;
@@ -155,15 +156,19 @@ int capture_graph(gmcs_server* s, TickSet& t) {
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GMCS_E_CUDA;
     cudaLaunchHostFunc(st, stamp_start, &t);
     cudaMemcpyAsync(d, t.h_desc, sizeof(TickDesc), cudaMemcpyHostToDevice, st);
+    const bool gicp = s->cfg.model == GMCS_MODEL_GICP;
     launch_scan_pack_b(&d->pack, st);
+    if (gicp) launch_knn_cov_b(&d->knn, s->cfg.knn, st);
     launch_predict_b(&d->pred, st);
     launch_select_b(&d->sel, st);
     for (int k = 0; k < s->cfg.steps; ++k) {
-        launch_pass3_b(&d->pgrad, s->cfg.table_dtype, true, st);
-        launch_finish_b(&d->fgrad, true, false, st);
+        if (gicp) launch_gicp_b(&d->pgrad, true, st);
+        else launch_pass3_b(&d->pgrad, s->cfg.table_dtype, true, st);
+        launch_finish_b(&d->fgrad, true, gicp, st);
     }
-    launch_pass3_b(&d->pval, s->cfg.table_dtype, false, st);
-    launch_finish_b(&d->fval, false, false, st);
+    if (gicp) launch_gicp_b(&d->pval, false, st);
+    else launch_pass3_b(&d->pval, s->cfg.table_dtype, false, st);
+    launch_finish_b(&d->fval, false, gicp, st);
     launch_weigh_b(&d->weigh, st);
     if (s->cfg.resample == GMCS_RESAMPLE_PRUNE) {
         launch_prune_mark_b(&d->prune, st);
@@ -244,7 +249,7 @@ int launch_tick(gmcs_server* s) {
               [](Session* a, Session* b) { return a->pending.front().t_arrive < b->pending.front().t_arrive; });
     if ((int)cand.size() > kMaxSlots) cand.resize(kMaxSlots);
     TickDesc& D = *t->h_desc;
-    list_clear(D.pack); list_clear(D.pred); list_clear(D.sel); list_clear(D.pgrad); list_clear(D.fgrad);
+    list_clear(D.pack); list_clear(D.knn); list_clear(D.pred); list_clear(D.sel); list_clear(D.pgrad); list_clear(D.fgrad);
     list_clear(D.pval); list_clear(D.fval); list_clear(D.weigh); list_clear(D.scan); list_clear(D.tot);
     list_clear(D.search); list_clear(D.gather); list_clear(D.prune); list_clear(D.ptot); list_clear(D.pslot);
     for (size_t k = 0; k < cand.size(); ++k) {
@@ -258,6 +263,16 @@ int launch_tick(gmcs_server* s) {
         const uint32_t frame = c->frame;
         c->path_now += std::sqrt(f.dT[3] * f.dT[3] + f.dT[7] * f.dT[7] + f.dT[11] * f.dT[11]);
         list_add(D.pack, ScanPackArgs{c->stage, f.N, c->scan}, grid_scan_pack(f.N));
+        if (s->cfg.model == GMCS_MODEL_GICP) {
+            KnnCovArgs ka;
+            ka.pts = c->scan;
+            ka.n = f.N;
+            ka.k = s->cfg.knn;
+            ka.eps = (double)s->cfg.cov_eps;
+            ka.cov64 = nullptr;
+            ka.nrm32 = c->scov;
+            list_add(D.knn, ka, grid_knn_cov(f.N));
+        }
         list_add(D.pred, predict_args(c, f.dT, f.cov, nullptr, frame), grid_per_particle(c->P));
         list_add(D.sel, select_args(c, nullptr), grid_per_particle(c->P));
         PassArgs pa;
@@ -329,8 +344,7 @@ extern "C" {
 int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_sessions, gmcs_server** out) {
     if (!out) return GMCS_E_INVALID;
     *out = nullptr;
-    if (!cfg || budget_bytes == 0 || max_sessions <= 0 || cfg->k_nb != 3 || cfg->steps < 0 || cfg->steps > 64 ||
-        cfg->model != GMCS_MODEL_FIELD)
+    if (!cfg || budget_bytes == 0 || max_sessions <= 0 || cfg->k_nb != 3 || cfg->steps < 0 || cfg->steps > 64)
         return GMCS_E_INVALID;
     gmcs_server* s = new (std::nothrow) gmcs_server();
     if (!s) return GMCS_E_OOM;
@@ -340,6 +354,7 @@ int gmcs_server_create(const gmcs_config* cfg, uint64_t budget_bytes, int max_se
     cudaGetDevice(&s->device);
     prepare_filter_batched();
     prepare_weights_batched();
+    prepare_gicp_batched();
     int rc = GMCS_OK;
     if (cudaStreamCreateWithFlags(&s->setup_stream, cudaStreamNonBlocking) != cudaSuccess) rc = GMCS_E_CUDA;
     for (TickSet& t : s->sets) {

@@ -234,3 +234,42 @@ def test_full_size_eval_sampled():
                     np.linalg.norm(Hu[i, :21] - _upper(o["H"])) / (2e-4 * np.linalg.norm(o["H"]) + sl[2] + 1e-6))
     print(f"\nGICP_FULL worst/tol {worst:.3g}")
     assert worst <= 1
+
+
+def test_served_gicp_session_equals_plain_step(gw):
+    """The serving graph runs the GICP model with the same kernel bodies and block
+    decomposition as gmcs_step: a served session (mixed with a second one) is
+    bit-identical to the plain step."""
+    import paper_2504_18056_b300 as g
+    torch_cuda()
+    w, grids, _, _ = gw
+    P, K = 1024, len(grids)
+    srv = g.Server(budget_bytes=8 << 30, max_sessions=4, background=True, model=g.MODEL_GICP)
+    sids = []
+    for seed, n in ((31, P), (32, 700)):
+        sid = srv.open(n, K, 1024, table_bytes=0, seed=seed)
+        s = srv.session(sid)
+        s.init_particles(np.ascontiguousarray(w["particles"][:n]))
+        for k, kf in enumerate(w["keyframes"]):
+            s.add_keyframe(kf["points"], grids[k], np.ascontiguousarray(w["kf_particle_poses"][k][:n]))
+        srv.ready(sid)
+        sids.append((sid, s))
+    tickets = [[srv.submit(sid, w["scans"][fr], w["odometry"][fr], w["cov"]) for fr in range(3)] for sid, _ in sids]
+    srv.drain()
+    served = []
+    for t in tickets[0]:
+        r = None
+        while r is None:
+            r = srv.poll(t)
+        served.append(r[0])
+    sp, sl = sids[0][1].particles()
+    srv.close()
+    f = _filter(w, grids, P=P, seed=31)
+    plain = [f.step(w["scans"][fr], w["odometry"][fr], w["cov"]) for fr in range(3)]
+    pp, pl = f.particles()
+    f.close()
+    for a, b in zip(served, plain):
+        np.testing.assert_array_equal(a["estimate"], b["estimate"])
+        assert a["ess"] == b["ess"] and a["argmax"] == b["argmax"]
+    np.testing.assert_array_equal(sp, pp)
+    np.testing.assert_array_equal(sl, pl)
