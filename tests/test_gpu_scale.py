@@ -1,0 +1,72 @@
+"""Precision at scale: 1,000,000 particles x 2,048 points x 200 keyframes of 8,192
+points (0.2 m tables, about 92 GB in BF16 / 184 GB in FP32 on the device), BF16 and
+FP16 tables against the FP64 oracle on sampled particles, and whole frames compared
+with the all-FP32 run on the same seeds.
+
+The session (200 ray-cast keyframes, 200 x 1e6 perturbed keyframe poses) takes about
+two minutes to generate on the host; GMCS_SCALE=0 skips the module."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import grad_tolerance, gpu_eval, gpu_nbr, make_filter, moment_scales
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow,
+              pytest.mark.skipif(os.environ.get("GMCS_SCALE") == "0", reason="GMCS_SCALE=0")]
+
+P, N, K = 1_000_000, 2048, 200
+DT_NAME = {0: "f32", 1: "bf16", 2: "f16"}
+
+
+@pytest.fixture(scope="module")
+def big():
+    return synth.forest_workload(seed=0, n_particles=P, n_points=N, n_keyframes=K, n_frames=2)
+
+
+def test_precision_at_scale(big):
+    w = big
+    scan = w["scans"][0]
+    grids = [kf["grid"] for kf in w["keyframes"]]
+    idx = np.unique(np.r_[0, P - 1, np.linspace(1, P - 2, 22).astype(int)])
+    res, est = {}, {}
+    nbr = None
+    for dt in (0, 1, 2):
+        f = make_filter(w, P, dt, max_points=N, seed=7)
+        nb = gpu_nbr(f, P, 3)
+        if nbr is None:
+            nbr = nb
+        np.testing.assert_array_equal(nb, nbr)
+        res[dt] = gpu_eval(f, scan, P)
+        out = f.step(scan, w["odometry"][0], w["cov"])
+        est[dt] = out["estimate"]
+        f.close()
+    need = sorted(set(int(k) for k in nbr[idx].ravel()))
+    exact = {k: oracle.build_table(w["keyframes"][k]["points"], grids[k], 0.2, 1.0) for k in need}
+    o64 = oracle.eval_batch(w["particles"], nbr, w["kf_particle_poses"], [exact.get(k) for k in range(K)],
+                            grids, scan, idx=idx)
+    report = {"keyframes_touched_by_sample": len(need)}
+    for dt in (0, 1, 2):
+        ll, g, mom = res[dt]
+        if dt == 0:
+            oq = o64
+        else:
+            quant = {k: oracle.quantize(exact[k], dt) for k in need}
+            oq = oracle.eval_batch(w["particles"], nbr, w["kf_particle_poses"], [quant.get(k) for k in range(K)],
+                                   grids, scan, idx=idx)
+        assert np.all(np.abs(ll[idx] - oq["ll"]) <= 1e-4 * np.abs(oq["ll"])), DT_NAME[dt]
+        assert np.all(np.linalg.norm(g[idx] - oq["g"], axis=1) <= grad_tolerance(oq)), DT_NAME[dt]
+        assert np.all(np.abs(mom[idx] - oq["mom"]) <= 1e-4 * moment_scales(oq["mom"], scan)), DT_NAME[dt]
+        e_ll = np.abs(ll[idx] - o64["ll"]) / np.abs(o64["ll"])
+        e_g = np.linalg.norm(g[idx] - o64["g"], axis=1) / np.maximum(np.linalg.norm(o64["g"], axis=1),
+                                                                      1e-2 * o64["gabs"])
+        e_vs32 = np.abs(ll - res[0][0]) / np.abs(res[0][0])
+        d_est = np.linalg.norm(np.asarray(est[dt])[[3, 7, 11]] - np.asarray(est[0])[[3, 7, 11]])
+        report[DT_NAME[dt]] = {"ll_rel_err_max": float(e_ll.max()), "ll_rel_err_median": float(np.median(e_ll)),
+                               "grad_rel_err_max": float(e_g.max()), "grad_rel_err_median": float(np.median(e_g)),
+                               "ll_rel_diff_vs_f32_max_all_particles": float(e_vs32.max()),
+                               "estimate_vs_f32_m": float(d_est)}
+    print("\nPRECISION_AT_SCALE " + json.dumps(report))
