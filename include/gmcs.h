@@ -50,6 +50,7 @@ extern "C" {
 #define GMCS_E_STATE (-5)     /* call out of order (e.g. step before particles exist) */
 #define GMCS_E_NONFINITE (-6) /* weights degenerated (all log-weights -inf or NaN); reset to uniform */
 #define GMCS_E_BUDGET (-7)    /* serving: the session does not fit the memory budget or the session limit */
+#define GMCS_E_IO (-8)        /* checkpoint file cannot be written, read or is not a checkpoint */
 #define GMCS_PENDING 1        /* serving: the frame has not completed yet */
 
 #define GMCS_TABLE_F32 0
@@ -366,6 +367,22 @@ int gmcs_probe_gather(uint64_t buffer_bytes, int rec_bytes, void* cuda_stream, d
  * FP64 with separately rounded products and sums, the voxel is floor((x - o)/h).
  * Errors: GMCS_E_STATE without keyframes. */
 int gmcs_overlap(gmcs_ctx* ctx, const float* scan, int N, const double T_rel[12], double* rate);
+
+/*
+ * Checkpoint / resume of a session. gmcs_save writes the context's state to a
+ * file: particles (current poses, log-weights), every keyframe's table as stored,
+ * its occupancy lattice, path length and per-particle poses, and the frame
+ * counter, odometry path, odometry since the last keyframe and the config.
+ * gmcs_load restores it into a context that holds no keyframes yet and whose
+ * capacities are at least the saved counts; the context's config becomes the
+ * saved one, and the frames that follow are bit-identical to those the saved
+ * context would have computed.
+ * Errors: GMCS_E_IO (file unreadable or not a checkpoint), GMCS_E_STATE (save
+ * without particles, load into a context with keyframes), GMCS_E_CAPACITY,
+ * GMCS_E_OOM.
+ */
+int gmcs_save(gmcs_ctx* ctx, const char* path);
+int gmcs_load(gmcs_ctx* ctx, const char* path);
 
 /* Copy current poses (P x 12 floats) and/or log-weights (P doubles) out; NULL skips. */
 int gmcs_get_particles(gmcs_ctx* ctx, float* poses, double* logw);

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgmcs.so")
 
 OK = 0
-E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE, E_BUDGET = -1, -2, -3, -4, -5, -6, -7
+E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE, E_BUDGET, E_IO = -1, -2, -3, -4, -5, -6, -7, -8
 PENDING = 1
 TABLE_F32, TABLE_BF16, TABLE_F16 = 0, 1, 2
 RESAMPLE_ALWAYS, RESAMPLE_ESS_HALF, RESAMPLE_NEVER, RESAMPLE_PRUNE = 0, 1, 2, 3
@@ -99,6 +99,8 @@ _SIGS = {
     "gmcs_prune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                              C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     "gmcs_get_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gmcs_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "gmcs_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gmcs_get_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_get_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_point_covariances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -326,6 +328,13 @@ class Filter:
         _check(lib().gmcs_prune(self.ctx, _ptr(x), _ptr(w), _ptr(ll), int(x.shape[0]), int(argmax), float(u),
                                 _ptr(anc), _ptr(logw), C.byref(d)), "gmcs_prune")
         return d.value
+
+    # --- checkpoint
+    def save(self, path):
+        _check(lib().gmcs_save(self.ctx, os.fsencode(path)), "gmcs_save")
+
+    def load(self, path):
+        _check(lib().gmcs_load(self.ctx, os.fsencode(path)), "gmcs_load")
 
     # --- readback
     def get_particles(self, poses=None, logw=None):

@@ -544,6 +544,7 @@ const char* gmcs_strerror(int code) {
         case GMCS_E_STATE: return "call out of order";
         case GMCS_E_NONFINITE: return "weights degenerated (reset to uniform)";
         case GMCS_E_BUDGET: return "session does not fit the serving budget";
+        case GMCS_E_IO: return "checkpoint file error";
         case GMCS_PENDING: return "pending";
         default: return "unknown error";
     }
