@@ -201,7 +201,9 @@ int gmcs_add_keyframe(gmcs_ctx* ctx, const float* pts, int n, const gmcs_grid* g
  *   weights, exact integer prefix sums), and the gather of all particle state;
  *   under GMCS_RESAMPLE_PRUNE instead only the dead slots are refilled in place
  *   from the survivors (as gmcs_prune, with the value-pass log-likelihoods).
- * scan: N points (N x 3 floats, host or device) in the sensor frame.
+ * scan: N points (N x 3 floats, host or device) in the sensor frame; a point with
+ * a non-finite coordinate is taken as a point far from every map (all its
+ * lookups miss), which leaves the normalised weights and the moves unchanged.
  * delta_T: odometry increment (T^o_{t-1})^-1 T^o_t as 12 doubles (host).
  * cov: 6 x 6 motion covariance in the tangent space (36 doubles, host, row-major).
  * u_override: NULL, or a host double in [0,1) used as the systematic offset.

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gmcs.h"
 #include "context.h"
 #include "kernels.h"
@@ -127,12 +129,14 @@ struct Launch {
     int kind;
     cudaEvent_t a = nullptr;
     Launch(gmcs_ctx* ctx, int k) : c(ctx), kind(k) {
+        nvtxRangePushA(kKindName[k]);   // an NVTX range per launch, for timeline tools
         if (c->profiling) {
             a = take_event(c);
             cudaEventRecord(a, c->stream);
         }
     }
     ~Launch() {
+        nvtxRangePop();
         c->launches++;
         c->kind_launches[kind]++;
         if (c->profiling) {

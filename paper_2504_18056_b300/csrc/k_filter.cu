@@ -27,9 +27,16 @@ namespace gmcs {
 
 // ------------------------------------------------------------------ layout helpers
 
+// A non-finite point is replaced by one far outside every map, so each of its
+// lookups is a miss: it adds the same constant to every particle's log-likelihood
+// (which the weight normalisation removes) and nothing to gradients or moments,
+// instead of turning every particle's likelihood into NaN.
 __device__ __forceinline__ void scan_pack_body(const ScanPackArgs& a, int vb, int vg) {
-    for (int j = vb * blockDim.x + threadIdx.x; j < a.n; j += vg * blockDim.x)
-        a.out[j] = make_float4(a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], 0.f);
+    for (int j = vb * blockDim.x + threadIdx.x; j < a.n; j += vg * blockDim.x) {
+        float x = a.xyz[3 * j], y = a.xyz[3 * j + 1], z = a.xyz[3 * j + 2];
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) x = y = z = 1e30f;
+        a.out[j] = make_float4(x, y, z, 0.f);
+    }
 }
 
 __global__ void k_scan_pack(ScanPackArgs a) { scan_pack_body(a, blockIdx.x, gridDim.x); }

@@ -141,3 +141,33 @@ def test_given_offset_and_stats(box_room):
     assert s["kinds"]["pass_grad"]["ms"] > 0 and s["kinds"]["pass_grad"]["launches"] == 3
     assert f.device_bytes() > 0
     f.close()
+
+
+def test_non_finite_scan_points_are_misses(box_room):
+    """NaN / inf scan points (a dropped lidar return) do not poison the frame: the
+    normalised weights, the estimate and the moved particles equal those of the
+    same frame with the points removed (up to the float summation order)."""
+    P = 1024
+    w = box_room
+    scan = w["scans"][0].copy()
+    bad = np.array([3, 100, 257, 511])
+    dirty = scan.copy()
+    dirty[bad[0], 0] = np.nan
+    dirty[bad[1]] = np.inf
+    dirty[bad[2], 2] = -np.inf
+    dirty[bad[3], 1] = np.nan
+    clean = np.delete(scan, bad, axis=0)
+    outs, parts, ws = [], [], []
+    for s in (dirty, clean):
+        f = make_filter(w, P, seed=2, resample=2)      # no resampling: compare the moved particles
+        outs.append(f.step(np.ascontiguousarray(s), w["odometry"][0], w["cov"]))
+        wg = np.zeros(P)
+        f.frame_diag(None, wg, None, None)
+        ws.append(wg)
+        parts.append(f.particles()[0])
+        f.close()
+    assert outs[0]["status"] == 0 and np.isfinite(ws[0]).all()
+    np.testing.assert_allclose(ws[0], ws[1], rtol=1e-2, atol=1e-12)
+    assert outs[0]["argmax"] == outs[1]["argmax"]
+    np.testing.assert_allclose(outs[0]["estimate"], outs[1]["estimate"], atol=1e-5)
+    np.testing.assert_allclose(parts[0], parts[1], atol=1e-4)
