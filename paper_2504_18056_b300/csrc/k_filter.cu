@@ -236,28 +236,15 @@ __device__ __forceinline__ int floor_split(float u, float& fl) {
 // A cell outside [0, n-1) on any axis reads as L = 0 (the load is skipped).
 // The record holds the cell's corners as z-pairs (slot dz + 2 dy + 4 dx):
 // P0 = x0y0, P1 = x0y1, P2 = x1y0, P3 = x1y1, each (z0, z1).
+// The lookup in cell (cx, cy, cz) at fractional position (fx, fy, fz).
 template <int DT, bool GRAD>
-__device__ __forceinline__ void lookup_one(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
-                                           float ux, float uy, float uz, float eps, float& lsum, float& w,
-                                           float& gx, float& gy, float& gz) {
-    // FP32 tables: floor on the FMA/ALU pipes (gradient pass 2.08 -> 2.01 ms); the
-    // 16-bit tables widen their records on the ALU pipe and are faster with the
-    // conversion unit doing the floor (1.84 vs 2.03 ms)
-    float flx, fly, flz;
-    int cx, cy, cz;
-    if constexpr (DT == 0) {
-        cx = floor_split(ux, flx);
-        cy = floor_split(uy, fly);
-        cz = floor_split(uz, flz);
-    } else {
-        flx = floorf(ux); fly = floorf(uy); flz = floorf(uz);
-        cx = (int)flx; cy = (int)fly; cz = (int)flz;
-    }
+__device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
+                                            int cx, int cy, int cz, float fx, float fy, float fz, float eps,
+                                            float& lsum, float& w, float& gx, float& gy, float& gz) {
     const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
     const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
     float v[8];
     load_cell<DT>(cells, idx, valid, v);
-    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
     const float2 P0 = make_float2(v[0], v[1]), P1 = make_float2(v[2], v[3]);
     const float2 P2 = make_float2(v[4], v[5]), P3 = make_float2(v[6], v[7]);
     const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
@@ -279,6 +266,33 @@ __device__ __forceinline__ void lookup_one(const void* __restrict__ cells, uint3
         gz = Lz * inv;
         w = L * inv;
     }
+}
+
+template <int DT, bool GRAD>
+__device__ __forceinline__ void lookup_one(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
+                                           float ux, float uy, float uz, float eps, float& lsum, float& w,
+                                           float& gx, float& gy, float& gz) {
+    // FP32 tables: floor on the FMA/ALU pipes (gradient pass 2.08 -> 2.01 ms); the
+    // 16-bit tables widen their records on the ALU pipe and are faster with the
+    // conversion unit doing the floor (1.84 vs 2.03 ms)
+    float flx, fly, flz;
+    int cx, cy, cz;
+    if constexpr (DT == 0) {
+        cx = floor_split(ux, flx);
+        cy = floor_split(uy, fly);
+        cz = floor_split(uz, flz);
+    } else {
+        flx = floorf(ux); fly = floorf(uy); flz = floorf(uz);
+        cx = (int)flx; cy = (int)fly; cz = (int)flz;
+    }
+    lookup_cell<DT, GRAD>(cells, ncx, ncy, ncz, cx, cy, cz, ux - flx, uy - fly, uz - flz, eps, lsum, w, gx, gy, gz);
+}
+
+__device__ __forceinline__ float2 p2_add_rm(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&d);
 }
 
 // Affine map p -> u = A p + b of one (particle, neighbour keyframe) pair onto
@@ -413,14 +427,34 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
         for (int j = j0; j < j1; ++j) {
             const float4 p = __ldg(a.scan + j);
             float wsum = 0.f;
+            // FP32 tables: (ux, uy) and their floor on packed pairs (gradient pass 2.01 -> 1.95 ms);
+            // the 16-bit tables are faster with the scalar form (1.82 vs 1.89 ms)
+            const float2 PX = make_float2(p.x, p.x), PY = make_float2(p.y, p.y), PZ = make_float2(p.z, p.z);
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
-                const float ux = fmaf(sl[s].A00, p.x, fmaf(sl[s].A01, p.y, fmaf(sl[s].A02, p.z, sl[s].b0)));
-                const float uy = fmaf(sl[s].A10, p.x, fmaf(sl[s].A11, p.y, fmaf(sl[s].A12, p.z, sl[s].b1)));
+                float w, gx, gy, gz, ux, uy;
                 const float uz = fmaf(sl[s].A20, p.x, fmaf(sl[s].A21, p.y, fmaf(sl[s].A22, p.z, sl[s].b2)));
-                float w, gx, gy, gz;
-                lookup_one<DT, GRAD>(sl[s].cells, sl[s].ncx, sl[s].ncy, sl[s].ncz, ux, uy, uz, eps, lsum, w, gx, gy,
-                                     gz);
+                if constexpr (DT == 0) {
+                    const float2 uxy = p2_fma(make_float2(sl[s].A00, sl[s].A10), PX,
+                                              p2_fma(make_float2(sl[s].A01, sl[s].A11), PY,
+                                                     p2_fma(make_float2(sl[s].A02, sl[s].A12), PZ,
+                                                            make_float2(sl[s].b0, sl[s].b1))));
+                    ux = uxy.x;
+                    uy = uxy.y;
+                    const float2 C2 = make_float2(12582912.0f, 12582912.0f);
+                    const float2 t2 = p2_add_rm(uxy, C2);
+                    const float2 f2 = p2_sub(uxy, p2_sub(t2, C2));
+                    float flz;
+                    const int cz = floor_split(uz, flz);
+                    lookup_cell<DT, GRAD>(sl[s].cells, sl[s].ncx, sl[s].ncy, sl[s].ncz,
+                                          __float_as_int(t2.x) - 0x4B400000, __float_as_int(t2.y) - 0x4B400000, cz,
+                                          f2.x, f2.y, uz - flz, eps, lsum, w, gx, gy, gz);
+                } else {
+                    ux = fmaf(sl[s].A00, p.x, fmaf(sl[s].A01, p.y, fmaf(sl[s].A02, p.z, sl[s].b0)));
+                    uy = fmaf(sl[s].A10, p.x, fmaf(sl[s].A11, p.y, fmaf(sl[s].A12, p.z, sl[s].b1)));
+                    lookup_one<DT, GRAD>(sl[s].cells, sl[s].ncx, sl[s].ncy, sl[s].ncz, ux, uy, uz, eps, lsum, w,
+                                         gx, gy, gz);
+                }
                 if constexpr (GRAD) {
                     G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
                     C[s][0] = fmaf(uy, gz, fmaf(-uz, gy, C[s][0]));
