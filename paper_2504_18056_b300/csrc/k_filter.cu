@@ -478,7 +478,10 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
 // The value pass fits 128 registers at 4 CTAs per SM (1.37 -> 1.25 ms FP32); the
 // gradient pass keeps its ~150 registers (capping them at 128 costs 4 %).
 template <int DT, bool GRAD, int UNROLL>
-__global__ void __launch_bounds__(kPassThreads, GRAD ? GMCS_PASS3_MINBLOCKS : 4) k_pass3(PassArgs a) {
+#ifndef GMCS_VALUE_MINBLOCKS
+#define GMCS_VALUE_MINBLOCKS 4
+#endif
+__global__ void __launch_bounds__(kPassThreads, GRAD ? GMCS_PASS3_MINBLOCKS : GMCS_VALUE_MINBLOCKS) k_pass3(PassArgs a) {
     pass3_body<DT, GRAD, UNROLL>(a, blockIdx.x);
 }
 
