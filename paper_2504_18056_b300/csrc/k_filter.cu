@@ -239,14 +239,10 @@ __device__ __forceinline__ int floor_split(float u, float& fl) {
 // The lookup in cell (cx, cy, cz) at fractional position (fx, fy, fz). With PROD
 // the likelihood L + eps is multiplied into lsum (the caller takes one log2 of
 // the product of a point's three lookups, each factor in [eps, 1 + eps]).
-template <int DT, bool GRAD, bool PROD = false>
-__device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
-                                            int cx, int cy, int cz, float fx, float fy, float fz, float eps,
-                                            float& lsum, float& w, float& gx, float& gy, float& gz) {
-    const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-    const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
-    float v[8];
-    load_cell<DT>(cells, idx, valid, v);
+// Trilinear interpolation of one cell record v at fraction (fx, fy, fz).
+template <bool GRAD, bool PROD = false>
+__device__ __forceinline__ void lookup_interp(const float* v, float fx, float fy, float fz, float eps, float& lsum,
+                                              float& w, float& gx, float& gy, float& gz) {
     const float2 P0 = make_float2(v[0], v[1]), P1 = make_float2(v[2], v[3]);
     const float2 P2 = make_float2(v[4], v[5]), P3 = make_float2(v[6], v[7]);
     const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
@@ -269,6 +265,17 @@ __device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint
         gz = Lz * inv;
         w = L * inv;
     }
+}
+
+template <int DT, bool GRAD, bool PROD = false>
+__device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
+                                            int cx, int cy, int cz, float fx, float fy, float fz, float eps,
+                                            float& lsum, float& w, float& gx, float& gy, float& gz) {
+    const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+    const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
+    float v[8];
+    load_cell<DT>(cells, idx, valid, v);
+    lookup_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
 }
 
 template <int DT, bool GRAD, bool PROD = false>
@@ -486,14 +493,263 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
     store_partials<NACC>(a, acc, ww);
 }
 
-// The value pass fits 128 registers at 4 CTAs per SM (1.37 -> 1.25 ms FP32); the
-// gradient pass keeps its ~150 registers (capping them at 128 costs 4 %).
-template <int DT, bool GRAD, int UNROLL>
+// ---- software-pipelined three-neighbour pass: two stages in turn, so that
+// while one point's three cell records are interpolated, the next point's are
+// in flight (FP32 gradient pass 1.95 -> 1.77 ms). The 16-bit gradient passes
+// are faster unpipelined with two points unrolled (1.80 vs 1.95 ms BF16), and
+// so are the value passes (1.19 vs 1.20 ms FP32 at 4 CTAs per SM, 1.63 ms at 3).
+#ifndef GMCS_PIPE_G32
+#define GMCS_PIPE_G32 1
+#endif
+#ifndef GMCS_PIPE_G16
+#define GMCS_PIPE_G16 0
+#endif
+#ifndef GMCS_PIPE_V32
+#define GMCS_PIPE_V32 0
+#endif
+#ifndef GMCS_PIPE_V16
+#define GMCS_PIPE_V16 0
+#endif
+template <int DT, bool GRAD>
+constexpr bool pass3_pipelined() {
+    return GRAD ? (DT == 0 ? GMCS_PIPE_G32 : GMCS_PIPE_G16) : (DT == 0 ? GMCS_PIPE_V32 : GMCS_PIPE_V16);
+}
+
+// u = A p + b of one slot as three float4 in the order the packed (ux, uy)
+// transform reads it, so that each operand pair sits in adjacent registers:
+// q0 = (A00, A10, A01, A11), q1 = (A02, A12, b0, b1), q2 = (A20, A21, A22, b2).
+// (Scalar fields cost the pipelined gradient pass 1.77 -> 1.91 ms.)
+struct Xf {
+    float4 q0, q1, q2;
+};
+
+__device__ __forceinline__ Xf slot_xf(const Slot& s) {
+    Xf x;
+    x.q0 = make_float4(s.A00, s.A10, s.A01, s.A11);
+    x.q1 = make_float4(s.A02, s.A12, s.b0, s.b1);
+    x.q2 = make_float4(s.A20, s.A21, s.A22, s.b2);
+    return x;
+}
+
+__device__ __forceinline__ void xf_slot(const Xf& x, Slot& s) {
+    s.A00 = x.q0.x; s.A10 = x.q0.y; s.A01 = x.q0.z; s.A11 = x.q0.w;
+    s.A02 = x.q1.x; s.A12 = x.q1.y; s.b0 = x.q1.z; s.b1 = x.q1.w;
+    s.A20 = x.q2.x; s.A21 = x.q2.y; s.A22 = x.q2.z; s.b2 = x.q2.w;
+}
+
+// Lattice coordinate u of p in one slot, its cell c and in-cell fraction f
+// (FP32 tables: (ux, uy) on packed pairs and the round-down floor; 16-bit
+// tables: scalar transform and floorf, as in the unpipelined pass).
+template <int DT>
+__device__ __forceinline__ void slot_point(const Xf& x, float4 p, float& ux, float& uy, float& uz, int& cx, int& cy,
+                                           int& cz, float& fx, float& fy, float& fz) {
+    uz = fmaf(x.q2.x, p.x, fmaf(x.q2.y, p.y, fmaf(x.q2.z, p.z, x.q2.w)));
+    if constexpr (DT == 0) {
+        const float2 uxy = p2_fma(make_float2(x.q0.x, x.q0.y), make_float2(p.x, p.x),
+                                  p2_fma(make_float2(x.q0.z, x.q0.w), make_float2(p.y, p.y),
+                                         p2_fma(make_float2(x.q1.x, x.q1.y), make_float2(p.z, p.z),
+                                                make_float2(x.q1.z, x.q1.w))));
+        ux = uxy.x;
+        uy = uxy.y;
+        const float2 C2 = make_float2(12582912.0f, 12582912.0f);
+        const float2 t2 = p2_add_rm(uxy, C2);
+        const float2 f2 = p2_sub(uxy, p2_sub(t2, C2));
+        float flz;
+        cz = floor_split(uz, flz);
+        cx = __float_as_int(t2.x) - 0x4B400000;
+        cy = __float_as_int(t2.y) - 0x4B400000;
+        fx = f2.x;
+        fy = f2.y;
+        fz = uz - flz;
+    } else {
+        ux = fmaf(x.q0.x, p.x, fmaf(x.q0.z, p.y, fmaf(x.q1.x, p.z, x.q1.z)));
+        uy = fmaf(x.q0.y, p.x, fmaf(x.q0.w, p.y, fmaf(x.q1.y, p.z, x.q1.w)));
+        const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+        cx = (int)flx; cy = (int)fly; cz = (int)flz;
+        fx = ux - flx; fy = uy - fly; fz = uz - flz;
+    }
+}
+
+// A cell record as loaded: two float4 (FP32) or one uint4 of 16-bit z-pairs;
+// widened to floats only when it is interpolated.
+template <int DT>
+struct RawRec {
+    uint4 q;
+};
+template <>
+struct RawRec<0> {
+    float4 a, b;
+};
+
+// Issue the load of cell c of a slot's table; a cell outside the table, or a
+// stage with no point (live = false), reads as zeros without a load.
+template <int DT>
+__device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
+                                          int cx, int cy, int cz, bool live, RawRec<DT>& r) {
+    const bool valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+    const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
+    if constexpr (DT == 0) {
+        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.b = r.a;
+        if (valid) {
+            const float4* q = reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx;
+            r.a = __ldg(q);
+            r.b = __ldg(q + 1);
+        }
+    } else {
+        r.q = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void unpack_raw(const RawRec<DT>& r, float* v) {
+    if constexpr (DT == 0) {
+        v[0] = r.a.x; v[1] = r.a.y; v[2] = r.a.z; v[3] = r.a.w;
+        v[4] = r.b.x; v[5] = r.b.y; v[6] = r.b.z; v[7] = r.b.w;
+    } else {
+        const uint32_t w[4] = {r.q.x, r.q.y, r.q.z, r.q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (DT == 1) {
+                v[2 * e] = __uint_as_float(w[e] << 16);
+                v[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+            } else {
+                const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
+                v[2 * e] = h.x;
+                v[2 * e + 1] = h.y;
+            }
+        }
+    }
+}
+
+// One point between the issue of its three loads and their use.
+template <int DT>
+struct Stage {
+    float4 p;
+    float u[3][3], f[3][3];
+    RawRec<DT> r[3];
+};
+
+template <int DT, bool GRAD>
+__device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
+    constexpr int NACC = GRAD ? kAccGrad : 1;
+    const WarpWork ww = warp_work(a, vb);
+    const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
+
+    float acc[NACC];
+#pragma unroll
+    for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
+
+    if (i < a.P && j0 < j1) {
+        Xf xf[3];
+        const void* cells[3];
+        uint32_t ncx[3], ncy[3], ncz[3];
+        int ks[3];
+        {
+            float Tt[12];
+            load_pose(a.pose, a.ld, i, Tt);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                ks[s] = a.nbr[(size_t)s * a.ld + i];
+                const Slot sl = make_slot(a, i, ks[s], Tt);
+                xf[s] = slot_xf(sl);
+                cells[s] = sl.cells;
+                ncx[s] = sl.ncx; ncy[s] = sl.ncy; ncz[s] = sl.ncz;
+            }
+        }
+        const float eps = a.eps;
+        float lsum = 0.f;
+        float G[3][3], C[3][3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) G[s][d] = C[s][d] = 0.f;
+
+        auto issue = [&](Stage<DT>& st, int j, bool live) {
+            st.p = __ldg(a.scan + j);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                int cx, cy, cz;
+                slot_point<DT>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0], st.f[s][1],
+                               st.f[s][2]);
+                fetch_raw<DT>(cells[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
+            }
+        };
+        auto use = [&](const Stage<DT>& st) {
+            if constexpr (GRAD) {
+                float wsum = 0.f;
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    float v[8], w, gx, gy, gz;
+                    unpack_raw<DT>(st.r[s], v);
+                    lookup_interp<true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lsum, w, gx, gy, gz);
+                    const float ux = st.u[s][0], uy = st.u[s][1], uz = st.u[s][2];
+                    G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
+                    C[s][0] = fmaf(uy, gz, fmaf(-uz, gy, C[s][0]));
+                    C[s][1] = fmaf(uz, gx, fmaf(-ux, gz, C[s][1]));
+                    C[s][2] = fmaf(ux, gy, fmaf(-uy, gx, C[s][2]));
+                    wsum += w;
+                }
+                add_moments(wsum, st.p, acc);
+            } else {
+                // one log2 per point of the product of its three L + eps
+                float lprod = 1.f, w, gx, gy, gz;
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    float v[8];
+                    unpack_raw<DT>(st.r[s], v);
+                    lookup_interp<false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
+                }
+                lsum += __log2f(lprod);
+            }
+        };
+        Stage<DT> SA, SB;
+        issue(SA, j0, true);
+        for (int j = j0;; j += 2) {   // j1 and the exits are uniform across the warp
+            const bool m1 = j + 1 < j1;
+            issue(SB, m1 ? j + 1 : j, m1);
+            use(SA);
+            if (!m1) break;
+            const bool m2 = j + 2 < j1;
+            issue(SA, m2 ? j + 2 : j + 1, m2);
+            use(SB);
+            if (!m2) break;
+        }
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                Slot sl;
+                xf_slot(xf[s], sl);
+                fold_slot(sl, a.tables[ks[s]].h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
+            }
+        }
+        acc[0] = lsum * 0.69314718055994531f;
+    }
+    store_partials<NACC>(a, acc, ww);
+}
+
+// CTAs per SM the register allocation is sized for: the pipelined gradient
+// pass fits 168 registers at 3 CTAs per SM; the unpipelined one uses ~150 and
+// capping it at 128 costs 4 %; the value pass fits 128 at 4 CTAs per SM
+// (1.37 -> 1.25 ms FP32).
 #ifndef GMCS_VALUE_MINBLOCKS
 #define GMCS_VALUE_MINBLOCKS 4
 #endif
-__global__ void __launch_bounds__(kPassThreads, GRAD ? GMCS_PASS3_MINBLOCKS : GMCS_VALUE_MINBLOCKS) k_pass3(PassArgs a) {
-    pass3_body<DT, GRAD, UNROLL>(a, blockIdx.x);
+template <int DT, bool GRAD>
+constexpr int pass3_minblocks() {
+    return GRAD ? (pass3_pipelined<DT, GRAD>() ? 3 : GMCS_PASS3_MINBLOCKS) : GMCS_VALUE_MINBLOCKS;
+}
+
+template <int DT, bool GRAD, int UNROLL>
+__device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
+    if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD>(a, vb);
+    else pass3_body<DT, GRAD, UNROLL>(a, vb);
+}
+
+template <int DT, bool GRAD, int UNROLL>
+__global__ void __launch_bounds__(kPassThreads, pass3_minblocks<DT, GRAD>()) k_pass3(PassArgs a) {
+    pass3_any<DT, GRAD, UNROLL>(a, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ finish: sums, move (Eq. 5-7)
@@ -730,7 +986,7 @@ __global__ void __launch_bounds__(128) k_select_b(const BatchList<SelectArgs>* L
 
 template <int DT, bool GRAD, int UNROLL>
 __global__ void __launch_bounds__(kPassThreads, 3) k_pass3_b(const BatchList<PassArgs>* L) {
-    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_body<DT, GRAD, UNROLL>(a, vb)));
+    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_any<DT, GRAD, UNROLL>(a, vb)));
 }
 
 template <bool GRAD, bool GICP>
