@@ -353,7 +353,8 @@ int gmcs_resample_noalloc(const double* w, int P, double u, int* anc, void* cuda
 /*
  * Calibration, no counterpart in the paper: the rate (GB/s, into *gbs) of
  * random rec_bytes-sized (16 or 32) record reads from a device buffer of
- * buffer_bytes, with the 16-byte vector loads of the lookup pass -- with a
+ * buffer_bytes, with the loads of the lookup pass (one 256-bit load per 32-byte
+ * record, one 128-bit load per 16-byte record) -- with a
  * buffer that fits L2 (126 MB), the ceiling for lookups whose cells stay in L2.
  * Allocates and frees the buffer; runs on cuda_stream and synchronises it.
  */

@@ -495,9 +495,10 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
 
 // ---- software-pipelined three-neighbour pass: two stages in turn, so that
 // while one point's three cell records are interpolated, the next point's are
-// in flight (FP32 gradient pass 1.95 -> 1.77 ms). The 16-bit gradient passes
-// are faster unpipelined with two points unrolled (1.80 vs 1.95 ms BF16), and
-// so are the value passes (1.19 vs 1.20 ms FP32 at 4 CTAs per SM, 1.63 ms at 3).
+// in flight (FP32 gradient pass 1.95 -> 1.77 ms; FP32 value pass, with the
+// 256-bit record load, 1.16 -> 1.08 ms at 4 CTAs per SM). The 16-bit passes are
+// faster unpipelined with two points unrolled (BF16 gradient 1.80 vs 1.95 ms,
+// value 1.16 vs 1.38 ms).
 #ifndef GMCS_PIPE_G32
 #define GMCS_PIPE_G32 1
 #endif
@@ -505,7 +506,7 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
 #define GMCS_PIPE_G16 0
 #endif
 #ifndef GMCS_PIPE_V32
-#define GMCS_PIPE_V32 0
+#define GMCS_PIPE_V32 1
 #endif
 #ifndef GMCS_PIPE_V16
 #define GMCS_PIPE_V16 0
@@ -591,11 +592,7 @@ __device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, uint32
     if constexpr (DT == 0) {
         r.a = make_float4(0.f, 0.f, 0.f, 0.f);
         r.b = r.a;
-        if (valid) {
-            const float4* q = reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx;
-            r.a = __ldg(q);
-            r.b = __ldg(q + 1);
-        }
+        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
     } else {
         r.q = make_uint4(0u, 0u, 0u, 0u);
         if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
@@ -731,8 +728,8 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 
 // CTAs per SM the register allocation is sized for: the pipelined gradient
 // pass fits 168 registers at 3 CTAs per SM; the unpipelined one uses ~150 and
-// capping it at 128 costs 4 %; the value pass fits 128 at 4 CTAs per SM
-// (1.37 -> 1.25 ms FP32).
+// capping it at 128 costs 4 %; the value passes fit 128 at 4 CTAs per SM
+// (unpipelined FP32 1.37 -> 1.25 ms; pipelined at 3 CTAs per SM: 1.63 ms).
 #ifndef GMCS_VALUE_MINBLOCKS
 #define GMCS_VALUE_MINBLOCKS 4
 #endif

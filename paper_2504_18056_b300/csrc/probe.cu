@@ -6,7 +6,8 @@
 // buffer of a given size (an L2-resident size gives the L2 gather ceiling):
 // every thread reads `per_thread` records at pseudo-random indices (a 32-bit
 // integer hash of its global index and the step, no index traffic) with the
-// same 16-byte vector loads the lookup pass issues, and folds them into a sink.
+// loads the lookup pass issues (one 256-bit load per 32-byte record, one
+// 128-bit load per 16-byte record), and folds them into a sink.
 #include <cuda_runtime.h>
 
 #include "../../include/gmcs.h"
@@ -31,9 +32,14 @@ __global__ void __launch_bounds__(256) k_probe_gather(const float4* __restrict__
     for (int s = 0; s < per_thread; ++s) {
         const uint32_t r = mix32(tid * 0x9e3779b9u + (uint32_t)s * 0x85ebca6bu) % nrec;
         const float4* p = buf + (size_t)r * VEC;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const float4 q = __ldg(p + v);
+        if constexpr (VEC == 2) {
+            float4 a, b;
+            asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                : "l"(p));
+            acc += (a.x + a.y + a.z + a.w) + (b.x + b.y + b.z + b.w);
+        } else {
+            const float4 q = __ldg(p);
             acc += q.x + q.y + q.z + q.w;
         }
     }
