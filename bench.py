@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--serve-pool", type=int, default=60, help="distinct keyframe clouds shared by the sessions")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="frames per second per session")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-at-a-time plain FP32 comparison")
+    ap.add_argument("--serve-dtype", default="bf16", choices=["f32", "bf16", "f16"],
+                    help="table storage of the served sessions")
     return ap.parse_args()
 
 
@@ -423,8 +425,8 @@ def _saturate(srv, sat_sids, a, pool, frame_idx):
 def run_serve(a):
     """Config 5: sessions with P ~ U[4096, 200000], N ~ U[1024, 8192], K ~ U[10, 300],
     Poisson frames at 10 Hz per session, admission by a device-memory budget;
-    BF16 tables through the server, against the plain FP32 path serving the same
-    sessions one at a time."""
+    BF16 tables (or --serve-dtype) through the server, against the plain FP32 path
+    serving the same sessions one at a time."""
     import torch
     import paper_2504_18056_b300 as g
     import synth
@@ -442,8 +444,10 @@ def run_serve(a):
         for sp in specs:
             sp["arrivals"] = sp["arrivals"] * (10.0 / a.serve_rate)
 
+    sdt = {"f32": 0, "bf16": 1, "f16": 2}[a.serve_dtype]
+    rec = 32 if sdt == 0 else 16        # bytes per cell record
     srv = g.Server(budget_bytes=int(a.budget_gb * (1 << 30)), max_sessions=a.sessions, background=True,
-                   table_dtype=1)
+                   table_dtype=sdt)
     waiting = list(range(len(specs)))
     active = {}
     e2e_lat = []
@@ -456,7 +460,7 @@ def run_serve(a):
             spec = specs[waiting[0]]
             P, K, N = spec["P"], spec["K"], spec["N"]
             tb = K * (pool["keyframes"][0]["grid"]["dims"][0] * pool["keyframes"][0]["grid"]["dims"][1] *
-                      pool["keyframes"][0]["grid"]["dims"][2]) * 16
+                      pool["keyframes"][0]["grid"]["dims"][2]) * rec
             sid = srv.open(P, K, N, table_bytes=tb, seed=spec["seed"])
             if sid is None:
                 break
@@ -494,7 +498,7 @@ def run_serve(a):
     srv.reset_stats()
     sat_sids = []
     for spec in specs:
-        tb = spec["K"] * int(np.prod(pool["keyframes"][0]["grid"]["dims"])) * 16
+        tb = spec["K"] * int(np.prod(pool["keyframes"][0]["grid"]["dims"])) * rec
         sid = srv.open(spec["P"], spec["K"], spec["N"], table_bytes=tb, seed=spec["seed"])
         if sid is None:
             break
@@ -540,7 +544,7 @@ def run_serve(a):
         "value": served_rate, "unit": "evals/s", "n_gpus": 1, "higher_is_better": True,
         "config": {"workload": f"{len(specs)} sessions, P~U[4096,200000], N~U[1024,8192], K~U[10,300], "
                                f"{a.session_frames} Poisson frames at {a.serve_rate:g} Hz each, {a.budget_gb:.0f} GB budget, "
-                               f"BF16 tables, scenes to {a.serve_range:.0f} m",
+                               f"{a.serve_dtype.upper()} tables, scenes to {a.serve_range:.0f} m",
                    "sessions": len(specs), "frames": stats["frames"]},
         "latency_ms": {"p50": stats["latency_p50_s"] * 1e3, "p99": stats["latency_p99_s"] * 1e3,
                        "max": stats["latency_max_s"] * 1e3, "mean": stats["latency_mean_s"] * 1e3,

@@ -981,8 +981,15 @@ __global__ void __launch_bounds__(128) k_select_b(const BatchList<SelectArgs>* L
     GMCS_BATCH_LOOP(L, const SelectArgs a = L->args[s]; select_body(a, vb, vg));
 }
 
+// The persistent loop costs the 16-bit gradient pass registers: bounded at 3
+// CTAs per SM like the pipelined one (unbounded it takes 180, i.e. 2 per SM).
+template <int DT, bool GRAD>
+constexpr int pass3_b_minblocks() {
+    return pass3_minblocks<DT, GRAD>() < 3 ? 3 : pass3_minblocks<DT, GRAD>();
+}
+
 template <int DT, bool GRAD, int UNROLL>
-__global__ void __launch_bounds__(kPassThreads, 3) k_pass3_b(const BatchList<PassArgs>* L) {
+__global__ void __launch_bounds__(kPassThreads, pass3_b_minblocks<DT, GRAD>()) k_pass3_b(const BatchList<PassArgs>* L) {
     GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_any<DT, GRAD, UNROLL>(a, vb)));
 }
 
