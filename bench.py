@@ -34,7 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle×point lik+grad evals/s; frame update ms @100k particles; p50/p99"
 UNIT = "evals/s"
-FLOPS_GRAD_LOOKUP = 87          # FP32 flops of one gradient lookup (FMA = 2); breakdown in the design doc
+# FP32 flops of one gradient lookup (FMA = 2); breakdown in the design doc. FP32 tables hold
+# trilinear coefficients (value and gradient in 11 FMAs), 16-bit tables corner values
+FLOPS_GRAD_LOOKUP = {"f32": 76, "bf16": 87, "f16": 87}
 # GICP model: FP32 flops (FMA = 2) of an inlier lookup with the Gauss-Newton terms in
 # the keyframe-frame form the kernel uses, and of a lookup that stops at an empty voxel
 # (transform and cell only); lookups rejected by the cap are counted as the latter
@@ -44,7 +46,7 @@ GICP_VOXEL = 1.0                # m, voxel edge of the GICP keyframe maps
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes read + written per gradient-pass launch, from one ncu capture of the
 # current kernel at the same particle and point counts (profiles/); None when stale
-TRAFFIC_PER_LAUNCH = {"f32": 32.551e6, "bf16": 30.560e6, "f16": None}
+TRAFFIC_PER_LAUNCH = {"f32": None, "bf16": 30.560e6, "f16": None}
 
 
 def parse():
@@ -322,13 +324,14 @@ def run_native(a, world, rank, local):
     lookups_per_launch = float(P) * N * 3
     rec_bytes = 32 if dtype == 0 else 16
     avg_ms = pg["ms"] / max(pg["launches"], 1)
-    # algorithmic work of one gradient lookup: 87 FP32 flops (FMA = 2), one cell record read;
+    # algorithmic work of one gradient lookup: 76 (FP32 tables) / 87 (16-bit) FP32 flops
+    # (FMA = 2), one cell record read;
     # GICP: 198 per inlier, 24 per other lookup, 48 B voxel record per lookup
     if gicp:
         flops_per_launch = lookups_per_launch * (inlier_frac * FLOPS_GICP_INLIER + (1 - inlier_frac) * FLOPS_GICP_MISS)
         rec_bytes = 48
     else:
-        flops_per_launch = lookups_per_launch * FLOPS_GRAD_LOOKUP
+        flops_per_launch = lookups_per_launch * FLOPS_GRAD_LOOKUP[a.dtype]
     achieved_tflops = flops_per_launch / (avg_ms / 1e3) / 1e12
     gather_gbs = lookups_per_launch * rec_bytes / (avg_ms / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -172,8 +172,11 @@ int gmcs_init_particles(gmcs_ctx* ctx, const float* poses, int P, const double* 
  * Insert a keyframe (Sec. III-A: shared cloud P_k, per-particle pose T_k^i).
  * pts: n points (n x 3 floats, host or device) in the keyframe's own frame.
  * grid: the table lattice in that frame. The library builds the table on the
- * device (K8: splat of d^2 within r_t, then exp) and stores it packed per cell
- * (8 corner values contiguous) in cfg.table_dtype.
+ * device (K8: splat of d^2 within r_t, then exp) and stores one 32-byte
+ * (FP32) or 16-byte (BF16/FP16) record per lattice cell, in cfg.table_dtype:
+ * FP32 records hold the 8 coefficients of the cell's trilinear polynomial
+ * (computed from the corner values in double, rounded once), 16-bit records
+ * the 8 corner values rounded to the storage type.
  * GICP model: grid is the voxel lattice (n = voxels per axis, voxel (ix,iy,iz)
  * covering origin + h [ix, ix+1) x ...); the library computes every point's
  * plane-regularised covariance from its cfg.knn nearest keyframe points (FP64)
@@ -380,7 +383,8 @@ int gmcs_overlap(gmcs_ctx* ctx, const float* scan, int N, const double T_rel[12]
  * capacities are at least the saved counts; the context's config becomes the
  * saved one, and the frames that follow are bit-identical to those the saved
  * context would have computed.
- * Errors: GMCS_E_IO (file unreadable or not a checkpoint), GMCS_E_STATE (save
+ * Errors: GMCS_E_IO (file unreadable, not a checkpoint, or written by another
+ * format version: version 1 held FP32 tables as corner values), GMCS_E_STATE (save
  * without particles, load into a context with keyframes), GMCS_E_CAPACITY,
  * GMCS_E_OOM.
  */
@@ -408,7 +412,9 @@ int gmcs_get_frame_diag(gmcs_ctx* ctx, float* ll, double* w, int* anc, int* nbr)
  * cov: n x 6 doubles (xx xy xz yy yz zz), host or device. Any model. */
 int gmcs_point_covariances(gmcs_ctx* ctx, const float* pts, int n, double* cov);
 
-/* Copy table k as float vertex values [n2][n1][n0] (unpacked from its cells).
+/* Copy table k as float vertex values [n2][n1][n0] (unpacked from its cells;
+ * from FP32 coefficient records, the sum of the corner's coefficients in double,
+ * within a few float roundings of the value the table was built from).
  * GICP model: the voxel records, 12 floats per voxel [n2][n1][n0]: mean (3),
  * 1 or 0 (voxel holds points), covariance xx xy xz yy yz zz, 0, 0. */
 int gmcs_get_table(gmcs_ctx* ctx, int k, float* vals);

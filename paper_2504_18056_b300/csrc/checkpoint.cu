@@ -24,7 +24,7 @@ using namespace gmcs;
 namespace {
 
 const char kMagic[8] = {'G', 'M', 'C', 'S', 'C', 'K', 'P', 'T'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;   // 2: FP32 field tables hold trilinear coefficients
 
 struct Header {
     char magic[8];

@@ -207,10 +207,51 @@ __device__ __forceinline__ void normal6(uint64_t seed, uint32_t i, uint32_t t, f
 
 // ---------------------------------------------------------------- table cells
 
-// Slot of corner (dx, dy, dz) within a cell record.
+// 16-bit tables: a cell record holds the cell's 8 corner values; slot of corner
+// (dx, dy, dz) within it.
 __host__ __device__ constexpr int rec_slot(int dx, int dy, int dz) { return dz + 2 * dy + 4 * dx; }
 
-// The 8 corner values of cell `idx`, widened to float.
+// FP32 tables: a cell record holds the 8 coefficients of the cell's trilinear
+// polynomial in the in-cell fraction (x, y, z) in [0, 1)^3,
+//   L = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz,
+// stored as the pairs (c4, c2), (c7, c6), (c1, c0), (c5, c3) that the packed
+// evaluation reads. Slot of coefficient i:
+__host__ __device__ constexpr int coef_slot(int i) {
+    return i == 0 ? 5 : i == 1 ? 4 : i == 2 ? 1 : i == 3 ? 7 : i == 4 ? 0 : i == 5 ? 6 : i == 6 ? 3 : 2;
+}
+
+// Coefficients from the corner values v[rec_slot(dx, dy, dz)] (inclusion-
+// exclusion over the corners, in double, rounded once), into record order.
+__device__ __forceinline__ void corners_to_coef(const float* v, float* rec) {
+    const double v000 = v[rec_slot(0, 0, 0)], v100 = v[rec_slot(1, 0, 0)], v010 = v[rec_slot(0, 1, 0)];
+    const double v001 = v[rec_slot(0, 0, 1)], v110 = v[rec_slot(1, 1, 0)], v101 = v[rec_slot(1, 0, 1)];
+    const double v011 = v[rec_slot(0, 1, 1)], v111 = v[rec_slot(1, 1, 1)];
+    const double c[8] = {v000,
+                         v100 - v000,
+                         v010 - v000,
+                         v001 - v000,
+                         (v110 - v100) - (v010 - v000),
+                         (v101 - v100) - (v001 - v000),
+                         (v011 - v010) - (v001 - v000),
+                         ((v111 - v110) - (v101 - v100)) - ((v011 - v010) - (v001 - v000))};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rec[coef_slot(i)] = (float)c[i];
+}
+
+// The value at corner (dx, dy, dz) of an FP32 coefficient record (in double,
+// rounded once).
+__host__ __device__ inline float coef_corner(const float* rec, int dx, int dy, int dz) {
+    double s = rec[coef_slot(0)];
+    if (dx) s += rec[coef_slot(1)];
+    if (dy) s += rec[coef_slot(2)];
+    if (dz) s += rec[coef_slot(3)];
+    if (dx && dy) s += rec[coef_slot(4)];
+    if (dx && dz) s += rec[coef_slot(5)];
+    if (dy && dz) s += rec[coef_slot(6)];
+    if (dx && dy && dz) s += rec[coef_slot(7)];
+    return (float)s;
+}
+
 // One 32-byte FP32 cell record (32-byte aligned) in a single 256-bit read-only
 // load: one L1 tag lookup per record instead of two for a pair of 128-bit
 // loads (lookup passes 1.77 -> 1.72 ms gradient, 1.19 -> 1.16 ms value).
@@ -219,6 +260,9 @@ __device__ __forceinline__ void ld_record32(const float4* p, float4& a, float4& 
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
 }
+
+// The record of cell `idx` widened to float (FP32: the coefficient record as
+// stored; 16-bit: the 8 corner values); zeros when !valid, without a load.
 
 template <int DT>
 __device__ __forceinline__ void load_cell(const void* __restrict__ cells, uint32_t idx, bool valid, float* v) {

@@ -234,12 +234,13 @@ __device__ __forceinline__ int floor_split(float u, float& fl) {
 // One lookup at lattice coordinate u of a table: adds log2(L + eps) to lsum
 // and, with GRAD, returns w = L / (L + eps) and g = grad_u L / (L + eps).
 // A cell outside [0, n-1) on any axis reads as L = 0 (the load is skipped).
-// The record holds the cell's corners as z-pairs (slot dz + 2 dy + 4 dx):
-// P0 = x0y0, P1 = x0y1, P2 = x1y0, P3 = x1y1, each (z0, z1).
 // The lookup in cell (cx, cy, cz) at fractional position (fx, fy, fz). With PROD
 // the likelihood L + eps is multiplied into lsum (the caller takes one log2 of
 // the product of a point's three lookups, each factor in [eps, 1 + eps]).
-// Trilinear interpolation of one cell record v at fraction (fx, fy, fz).
+//
+// Trilinear interpolation of one corner record v (16-bit tables): the record
+// holds the cell's corners as z-pairs (slot dz + 2 dy + 4 dx): P0 = x0y0,
+// P1 = x0y1, P2 = x1y0, P3 = x1y1, each (z0, z1).
 template <bool GRAD, bool PROD = false>
 __device__ __forceinline__ void lookup_interp(const float* v, float fx, float fy, float fz, float eps, float& lsum,
                                               float& w, float& gx, float& gy, float& gz) {
@@ -267,6 +268,45 @@ __device__ __forceinline__ void lookup_interp(const float* v, float fx, float fy
     }
 }
 
+// The same lookup on an FP32 coefficient record r = (c4, c2, c7, c6, c1, c0, c5, c3):
+// with a = c4 + c7 z, b = c1 + c5 z, d = c2 + c6 z, e = c0 + c3 z,
+//   L = e + d y + x (b + a y),  dL/dx = b + a y,  dL/dy = d + a x,
+//   dL/dz = (c3 + c6 y) + x (c5 + c7 y):
+// 4 packed and 3 scalar FMAs for L and its gradient (the corner form takes 9
+// packed and 6 scalar operations).
+template <bool GRAD, bool PROD = false>
+__device__ __forceinline__ void coef_interp(const float* r, float fx, float fy, float fz, float eps, float& lsum,
+                                            float& w, float& gx, float& gy, float& gz) {
+    const float2 Q0 = make_float2(r[0], r[1]), Q1 = make_float2(r[2], r[3]);   // (c4, c2), (c7, c6)
+    const float2 Q2 = make_float2(r[4], r[5]), Q3 = make_float2(r[6], r[7]);   // (c1, c0), (c5, c3)
+    const float2 ZZ = make_float2(fz, fz), YY = make_float2(fy, fy);
+    const float2 AD = p2_fma(Q1, ZZ, Q0);                          // (a, d)
+    const float2 BE = p2_fma(Q3, ZZ, Q2);                          // (b, e)
+    const float2 XE = p2_fma(YY, AD, BE);                          // (dL/dx, L at x = 0)
+    const float L = fmaf(fx, XE.x, XE.y);
+    const float den = L + eps;
+    if constexpr (PROD) lsum *= den;
+    else lsum += __log2f(den);
+    if constexpr (GRAD) {
+        const float2 TS = p2_fma(Q1, YY, Q3);                      // (c5 + c7 y, c3 + c6 y)
+        const float Ly = fmaf(fx, AD.x, AD.y);
+        const float Lz = fmaf(fx, TS.x, TS.y);
+        const float inv = __fdividef(1.f, den);
+        gx = XE.x * inv;
+        gy = Ly * inv;
+        gz = Lz * inv;
+        w = L * inv;
+    }
+}
+
+// Either record form: FP32 coefficient records, 16-bit corner records.
+template <int DT, bool GRAD, bool PROD = false>
+__device__ __forceinline__ void record_interp(const float* v, float fx, float fy, float fz, float eps, float& lsum,
+                                              float& w, float& gx, float& gy, float& gz) {
+    if constexpr (DT == 0) coef_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
+    else lookup_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
+}
+
 template <int DT, bool GRAD, bool PROD = false>
 __device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
                                             int cx, int cy, int cz, float fx, float fy, float fz, float eps,
@@ -275,7 +315,7 @@ __device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint
     const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
     float v[8];
     load_cell<DT>(cells, idx, valid, v);
-    lookup_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
+    record_interp<DT, GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
 }
 
 template <int DT, bool GRAD, bool PROD = false>
@@ -540,8 +580,11 @@ __device__ __forceinline__ void xf_slot(const Xf& x, Slot& s) {
 
 // Lattice coordinate u of p in one slot, its cell c and in-cell fraction f
 // (FP32 tables: (ux, uy) on packed pairs and the round-down floor; 16-bit
-// tables: scalar transform and floorf, as in the unpipelined pass).
-template <int DT>
+// tables: scalar transform and floorf, as in the unpipelined pass). ZCVT takes
+// the z floor on the conversion unit instead, which the FP32 value pass, with
+// fewer conversions of its own, absorbs (1.078 -> 1.061 ms; the gradient pass
+// slows 1.720 -> 1.743 ms).
+template <int DT, bool ZCVT = false>
 __device__ __forceinline__ void slot_point(const Xf& x, float4 p, float& ux, float& uy, float& uz, int& cx, int& cy,
                                            int& cz, float& fx, float& fy, float& fz) {
     uz = fmaf(x.q2.x, p.x, fmaf(x.q2.y, p.y, fmaf(x.q2.z, p.z, x.q2.w)));
@@ -556,7 +599,12 @@ __device__ __forceinline__ void slot_point(const Xf& x, float4 p, float& ux, flo
         const float2 t2 = p2_add_rm(uxy, C2);
         const float2 f2 = p2_sub(uxy, p2_sub(t2, C2));
         float flz;
-        cz = floor_split(uz, flz);
+        if constexpr (ZCVT) {
+            flz = floorf(uz);
+            cz = (int)flz;
+        } else {
+            cz = floor_split(uz, flz);
+        }
         cx = __float_as_int(t2.x) - 0x4B400000;
         cy = __float_as_int(t2.y) - 0x4B400000;
         fx = f2.x;
@@ -668,8 +716,8 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 int cx, cy, cz;
-                slot_point<DT>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0], st.f[s][1],
-                               st.f[s][2]);
+                slot_point<DT, !GRAD>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0],
+                                      st.f[s][1], st.f[s][2]);
                 fetch_raw<DT>(cells[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
             }
         };
@@ -680,7 +728,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 for (int s = 0; s < 3; ++s) {
                     float v[8], w, gx, gy, gz;
                     unpack_raw<DT>(st.r[s], v);
-                    lookup_interp<true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lsum, w, gx, gy, gz);
+                    record_interp<DT, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lsum, w, gx, gy, gz);
                     const float ux = st.u[s][0], uy = st.u[s][1], uz = st.u[s][2];
                     G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
                     C[s][0] = fmaf(uy, gz, fmaf(-uz, gy, C[s][0]));
@@ -696,7 +744,8 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 for (int s = 0; s < 3; ++s) {
                     float v[8];
                     unpack_raw<DT>(st.r[s], v);
-                    lookup_interp<false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
+                    record_interp<DT, false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy,
+                                                   gz);
                 }
                 lsum += __log2f(lprod);
             }

@@ -70,7 +70,8 @@ __device__ __forceinline__ float field_value(unsigned bits, float inv_two_sigma2
     return (d2 <= r_t2) ? expf(-d2 * inv_two_sigma2) : 0.0f;
 }
 
-// One thread per cell: 8 corner values -> one packed record.
+// One thread per cell: 8 corner values -> one record (FP32: the coefficients of
+// the cell's trilinear polynomial; 16-bit: the corner values, rounded).
 __global__ void k_pack(PackArgs a) {
     const int ncx = a.nx - 1, ncy = a.ny - 1, ncz = a.nz - 1;
     const size_t ncell = (size_t)ncx * ncy * ncz;
@@ -89,9 +90,11 @@ __global__ void k_pack(PackArgs a) {
                     v[rec_slot(dx, dy, dz)] = field_value(a.d2[vi], a.inv_two_sigma2, a.r_t2);
                 }
         if (a.dtype == 0) {
+            float r[8];
+            corners_to_coef(v, r);
             float4* out = reinterpret_cast<float4*>(a.cells) + 2 * c;
-            out[0] = make_float4(v[0], v[1], v[2], v[3]);
-            out[1] = make_float4(v[4], v[5], v[6], v[7]);
+            out[0] = make_float4(r[0], r[1], r[2], r[3]);
+            out[1] = make_float4(r[4], r[5], r[6], r[7]);
         } else {
             uint32_t w[4];
 #pragma unroll
@@ -111,7 +114,8 @@ __global__ void k_pack(PackArgs a) {
     }
 }
 
-// Vertex values read back from the cell records (vertex i lives in cell min(i, nc-1)).
+// Vertex values read back from the cell records (vertex i lives in cell min(i, nc-1);
+// FP32 records give it back from their coefficients, to within their rounding).
 __global__ void k_unpack(const void* __restrict__ cells, int dtype, int nx, int ny, int nz, float* __restrict__ out) {
     const size_t nv = (size_t)nx * ny * nz;
     const int ncx = nx - 1, ncy = ny - 1, ncz = nz - 1;
@@ -122,7 +126,7 @@ __global__ void k_unpack(const void* __restrict__ cells, int dtype, int nx, int 
         const size_t c = ((size_t)cz * ncy + cy) * ncx + cx;
         float val;
         if (dtype == 0) {
-            val = reinterpret_cast<const float*>(cells)[8 * c + corner];
+            val = coef_corner(reinterpret_cast<const float*>(cells) + 8 * c, ix - cx, iy - cy, iz - cz);
         } else {
             const unsigned short b = reinterpret_cast<const unsigned short*>(cells)[8 * c + corner];
             val = (dtype == 1) ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));

@@ -1,7 +1,8 @@
 """Checkpoint / resume (gmcs_save, gmcs_load): a session saved after two frames
 and restored into a fresh context continues bit for bit like the original, for
 the voxel-field and the GICP models; restoring into a context that already has
-keyframes, or from a file that is not a checkpoint, is refused."""
+keyframes, or from a file that is not a checkpoint of this format version, is
+refused."""
 import numpy as np
 import pytest
 
@@ -58,6 +59,14 @@ def test_refusals(tmp_path, box_room):
     b = g.Filter(256, 8, 1024)
     with pytest.raises(g.GmcsError) as e:
         b.load(str(bad))
+    assert e.value.code == g.E_IO
+    old = tmp_path / "v1.ckpt"             # a file of the earlier format (FP32 tables as corners)
+    raw = bytearray(open(path, "rb").read())
+    assert raw[:8] == b"GMCSCKPT" and int.from_bytes(raw[8:12], "little") == 2
+    raw[8:12] = (1).to_bytes(4, "little")
+    old.write_bytes(bytes(raw))
+    with pytest.raises(g.GmcsError) as e:
+        b.load(str(old))
     assert e.value.code == g.E_IO
     small = g.Filter(128, 8, 1024)
     with pytest.raises(g.GmcsError) as e:
