@@ -175,7 +175,7 @@ int gmcs_init_particles(gmcs_ctx* ctx, const float* poses, int P, const double* 
  * device (K8: splat of d^2 within r_t, then exp) and stores one 32-byte
  * (FP32) or 16-byte (BF16/FP16) record per lattice cell, in cfg.table_dtype:
  * FP32 records hold the 8 coefficients of the cell's trilinear polynomial
- * (computed from the corner values in double, rounded once), 16-bit records
+ * (differences of the corner values in float), 16-bit records
  * the 8 corner values rounded to the storage type.
  * GICP model: grid is the voxel lattice (n = voxels per axis, voxel (ix,iy,iz)
  * covering origin + h [ix, ix+1) x ...); the library computes every point's

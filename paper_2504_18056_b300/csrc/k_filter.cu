@@ -581,9 +581,9 @@ __device__ __forceinline__ void xf_slot(const Xf& x, Slot& s) {
 // Lattice coordinate u of p in one slot, its cell c and in-cell fraction f
 // (FP32 tables: (ux, uy) on packed pairs and the round-down floor; 16-bit
 // tables: scalar transform and floorf, as in the unpipelined pass). ZCVT takes
-// the z floor on the conversion unit instead, which the FP32 value pass, with
-// fewer conversions of its own, absorbs (1.078 -> 1.061 ms; the gradient pass
-// slows 1.720 -> 1.743 ms).
+// the z floor on the conversion unit instead, off the FMA pipe: with coefficient
+// records the pipelined FP32 passes gain (gradient 1.65 -> 1.58 ms, value
+// 1.078 -> 1.061 ms; with corner records the gradient pass lost, 1.720 -> 1.743).
 template <int DT, bool ZCVT = false>
 __device__ __forceinline__ void slot_point(const Xf& x, float4 p, float& ux, float& uy, float& uz, int& cx, int& cy,
                                            int& cz, float& fx, float& fy, float& fz) {
@@ -716,7 +716,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 int cx, cy, cz;
-                slot_point<DT, !GRAD>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0],
+                slot_point<DT, true>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0],
                                       st.f[s][1], st.f[s][2]);
                 fetch_raw<DT>(cells[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
             }
@@ -782,9 +782,12 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 #ifndef GMCS_VALUE_MINBLOCKS
 #define GMCS_VALUE_MINBLOCKS 4
 #endif
+#ifndef GMCS_PIPE_GRAD_MINBLOCKS
+#define GMCS_PIPE_GRAD_MINBLOCKS 3
+#endif
 template <int DT, bool GRAD>
 constexpr int pass3_minblocks() {
-    return GRAD ? (pass3_pipelined<DT, GRAD>() ? 3 : GMCS_PASS3_MINBLOCKS) : GMCS_VALUE_MINBLOCKS;
+    return GRAD ? (pass3_pipelined<DT, GRAD>() ? GMCS_PIPE_GRAD_MINBLOCKS : GMCS_PASS3_MINBLOCKS) : GMCS_VALUE_MINBLOCKS;
 }
 
 template <int DT, bool GRAD, int UNROLL>
