@@ -62,7 +62,7 @@ size_t ctx_device_bytes(int max_particles, int max_keyframes, int max_points) {
     b += 2 * (sizeof(float) * kPoseC * ld + sizeof(float) * kPoseC * ld * max_keyframes);
     b += sizeof(double) * ld * 2 + sizeof(float) * ld + sizeof(float) * 6 * ld;   // logw, w, ll, gbuf
     b += sizeof(int) * GMCS_MAX_NB * ld + sizeof(float) * part + sizeof(float4) * 2 * max_points + sizeof(float) * stage;
-    b += sizeof(double) * kWeighPart * 148 * 4 + sizeof(unsigned) + sizeof(WeighResult);
+    b += sizeof(double) * kWeighPart * kWeighMaxBlocks + sizeof(unsigned) + sizeof(WeighResult);
     b += sizeof(unsigned long long) * (ld + 2 * (nb + 1)) + sizeof(int) * ld;
     b += sizeof(TableDesc) * max_keyframes + sizeof(float) * max_keyframes + sizeof(int) * 8 + sizeof(unsigned);
     return b;
@@ -598,7 +598,7 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     if (!rc) rc = dalloc(c, &c->scan, (size_t)max_points);
     if (!rc) rc = dalloc(c, &c->scov, (size_t)max_points);
     if (!rc) rc = dalloc(c, &c->stage, c->stage_floats);
-    if (!rc) rc = dalloc(c, &c->wpart, (size_t)kWeighPart * 148 * 4);
+    if (!rc) rc = dalloc(c, &c->wpart, (size_t)kWeighPart * kWeighMaxBlocks);
     if (!rc) rc = dalloc(c, &c->counter, 1);
     if (!rc) rc = dalloc(c, &c->d_res, 1);
     if (!rc) rc = dalloc(c, &c->cl, ld);

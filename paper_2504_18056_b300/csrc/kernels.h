@@ -268,6 +268,7 @@ struct PruneArgs {
 };
 
 void launch_weigh(const WeighArgs& a, int nblocks, cudaStream_t s);
+constexpr int kWeighMaxBlocks = 148 * 4;   // CTA partials of the weight reduction (scratch bound)
 int weigh_blocks(int P);
 void launch_resample_scan(const ScanArgs& a, cudaStream_t s);
 void launch_scan_totals(unsigned long long* btot, int nblocks, cudaStream_t s);
