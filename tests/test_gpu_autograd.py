@@ -109,3 +109,33 @@ def test_backward_matches_central_differences(setup):
     print("\nAUTOGRAD_FD " + json.dumps(stats))
     assert np.median(rel) <= 2e-2
     assert np.percentile(rel, 90) <= 0.15
+
+
+def test_forward_backward_timing(setup):
+    """Device time of the autograd forward (value pass at T0 exp(xi)) and
+    backward (gradient pass plus the right-Jacobian chain) at the full size,
+    CUDA events after warm-up; reported, with a loose sanity bound only."""
+    torch, w, f, nbr, xi, scan_d = setup
+    from paper_2504_18056_b300.autograd import scan_loglik
+    xi_d = torch.from_numpy(xi).cuda().requires_grad_(True)
+    for _ in range(3):
+        scan_loglik(xi_d, f, scan_d).sum().backward()
+    reps = 10
+    fwd, bwd = [], []
+    for _ in range(reps):
+        xi_d.grad = None
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        ll = scan_loglik(xi_d, f, scan_d)
+        e1.record()
+        ll.sum().backward()
+        e2.record()
+        torch.cuda.synchronize()
+        fwd.append(e0.elapsed_time(e1))
+        bwd.append(e1.elapsed_time(e2))
+    lookups = P * N * 3
+    t = {"forward_ms": float(np.median(fwd)), "backward_ms": float(np.median(bwd)),
+         "forward_lookups_per_s": lookups / (np.median(fwd) * 1e-3),
+         "backward_lookups_per_s": lookups / (np.median(bwd) * 1e-3)}
+    print("\nAUTOGRAD_TIMING " + json.dumps(t))
+    assert 0 < t["forward_ms"] < 1e3 and 0 < t["backward_ms"] < 1e3
