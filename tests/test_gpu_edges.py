@@ -10,7 +10,11 @@ from gpu_common import gpu_eval, gpu_nbr, grad_tolerance, make_filter, oracle_nb
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("P,N,K", [(1, 1, 1), (1, 512, 4), (33, 7, 2), (65, 300, 3)])
+# with K >= 3 the three-neighbour pass runs; P, N chosen so that its warps get point
+# chunks of 1 (N = 1, 3), 9 (N = 97) and 10 points with a last chunk of 1 (N = 301):
+# odd and even chunks end the software-pipelined loop at either of its two exits
+@pytest.mark.parametrize("P,N,K", [(1, 1, 1), (1, 512, 4), (33, 7, 2), (65, 300, 3), (40, 1, 4), (40, 3, 4),
+                                   (65, 301, 4), (130, 97, 4)])
 def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K):
     kfs = box_room["keyframes"][:K]
     f = make_filter(box_room, P, keyframes=kfs)
@@ -23,6 +27,8 @@ def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K):
                           box_room_tables[:K], [kf["grid"] for kf in kfs], scan)
     assert np.all(np.abs(ll - o["ll"]) <= 1e-4 * np.abs(o["ll"]))
     assert np.all(np.linalg.norm(g - o["g"], axis=1) <= grad_tolerance(o))
+    llv, _, _ = gpu_eval(f, scan, P, grad=False)     # the value-only pass
+    assert np.all(np.abs(llv - o["ll"]) <= 1e-4 * np.abs(o["ll"]))
     f.close()
 
 
