@@ -305,6 +305,9 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
             float nin = 0.f;
             for (int j = j0; j < j1; ++j) {
                 const float4 p = __ldg(a.scan + j);
+                // the point's normal is loaded with the point, not after the voxel
+                // test, off the record load's dependency chain (4.69 -> 4.61 ms)
+                const float4 nj = __ldg(a.scov + j);
                 const float r0 = fmaf(R00, p.x, fmaf(R01, p.y, R02 * p.z));
                 const float r1 = fmaf(R10, p.x, fmaf(R11, p.y, R12 * p.z));
                 const float r2 = fmaf(R20, p.x, fmaf(R21, p.y, R22 * p.z));
@@ -327,7 +330,6 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
                 const float e0 = mv.x - x0, e1 = mv.y - x1, e2 = mv.z - x2;
                 // C = Sigma' + eps m m^T + (I - m m^T), m = R n; the diagonal of I - m m^T is
                 // taken as the sum of the other two squares (no cancellation in the thin direction)
-                const float4 nj = __ldg(a.scov + j);
                 const float m0 = fmaf(R00, nj.x, fmaf(R01, nj.y, R02 * nj.z));
                 const float m1 = fmaf(R10, nj.x, fmaf(R11, nj.y, R12 * nj.z));
                 const float m2 = fmaf(R20, nj.x, fmaf(R21, nj.y, R22 * nj.z));
