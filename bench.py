@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--model", default="field", choices=["field", "gicp"],
                     help="likelihood: voxel field (the benchmark's) or GICP distribution-to-distribution (Eq. 2-6)")
+    ap.add_argument("--resample", default="always", choices=["always", "ess", "never", "prune"],
+                    help="resampling policy (always: the benchmark's systematic resampling every frame; "
+                         "prune: the paper's dead-particle pruning)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-particles", type=int, default=8192,
                     help="oracle sample for cpu_baseline, split over the host cores")
@@ -212,7 +215,10 @@ def oracle_prepare(w, n_particles, model="field"):
     return oracle.State(poses, kfp, tables, grids)
 
 
-def oracle_frames(st, w, frames, first=0, model="field"):
+POLICY = {"always": 0, "ess": 1, "never": 2, "prune": 3}
+
+
+def oracle_frames(st, w, frames, first=0, model="field", resample="always"):
     """Seconds of each whole oracle frame (single thread) on the prepared sample
     (GICP: the scan covariances are part of the frame)."""
     import oracle
@@ -221,9 +227,9 @@ def oracle_frames(st, w, frames, first=0, model="field"):
         t0 = time.perf_counter()
         if model == "gicp":
             st.step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=fr, scov=oracle.knn_cov(w["scans"][fr], 10),
-                    model=1)
+                    model=1, resample=POLICY[resample])
         else:
-            st.step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=fr)
+            st.step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=fr, resample=POLICY[resample])
         out.append(time.perf_counter() - t0)
     return np.array(out)
 
@@ -235,8 +241,8 @@ _POOL_W = None
 
 
 def _pool_frame(task):
-    i, fr, model = task
-    return float(oracle_frames(_POOL_STATES[i], _POOL_W, 1, first=fr, model=model)[0])
+    i, fr, model, resample = task
+    return float(oracle_frames(_POOL_STATES[i], _POOL_W, 1, first=fr, model=model, resample=resample)[0])
 
 
 def host_cores():
@@ -252,13 +258,14 @@ class OraclePool:
     are built once in the parent and shared). Must be created before the process
     first touches CUDA: a pool forked after that can hang."""
 
-    def __init__(self, w, total_particles, model="field", max_workers=64):
+    def __init__(self, w, total_particles, model="field", max_workers=64, resample="always"):
         import multiprocessing as mp
         import oracle
         global _POOL_STATES, _POOL_W
         self.workers = max(1, min(host_cores(), max_workers))
         self.per_worker = max(16, total_particles // self.workers)
         self.model = model
+        self.resample = resample
         n = min(self.per_worker * self.workers, w["particles"].shape[0])
         self.per_worker = n // self.workers
         base = oracle_prepare(w, self.per_worker * self.workers, model)
@@ -272,7 +279,8 @@ class OraclePool:
         """Wall seconds of frame fr on every worker's block at once, and the
         workers' own seconds."""
         t0 = time.perf_counter()
-        per = self.pool.map(_pool_frame, [(i, fr, self.model) for i in range(self.workers)], chunksize=1)
+        per = self.pool.map(_pool_frame, [(i, fr, self.model, self.resample) for i in range(self.workers)],
+                            chunksize=1)
         return time.perf_counter() - t0, per
 
     def close(self):
@@ -292,7 +300,8 @@ def run_native(a, world, rank, local):
     # the oracle's worker pool forks before this process touches CUDA
     opool = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        opool = OraclePool(w, a.cpu_particles if a.model != "gicp" else a.cpu_particles // 4, model=a.model)
+        opool = OraclePool(w, a.cpu_particles if a.model != "gicp" else a.cpu_particles // 4, model=a.model,
+                           resample=a.resample)
     torch.cuda.set_device(local)
     torch.cuda.init()
     dist_init(world, "nccl")
@@ -302,7 +311,7 @@ def run_native(a, world, rank, local):
     gicp = a.model == "gicp"
     stream = torch.cuda.current_stream(dev)
     f = g.Filter(P, K, N, stream=stream.cuda_stream, table_dtype=dtype, seed=rank,
-                 model=g.MODEL_GICP if gicp else g.MODEL_FIELD)
+                 model=g.MODEL_GICP if gicp else g.MODEL_FIELD, resample=POLICY[a.resample])
     f.init_particles(w["particles"])
     for k, kf in enumerate(w["keyframes"]):
         grid = synth.grid_for_points(kf["points"], GICP_VOXEL, 1.0) if gicp else kf["grid"]
@@ -401,8 +410,9 @@ def run_native(a, world, rank, local):
         "data": "synthetic (seeded procedural corridor + trunk scene, 64x1024 lidar ray-cast)",
         "config": {"workload": f"single session, {P} particles x {N}-point scans x {K} keyframes "
                                + ("(8192 pts, GICP voxel maps at 1 m, knn 10)" if gicp else "(8192 pts, 0.2 m lattice)")
-                               + ", 3 neighbour keyframes, 3 moves/frame",
-                   "model": a.model,
+                               + ", 3 neighbour keyframes, 3 moves/frame"
+                               + ("" if a.resample == "always" else f", resampling policy {a.resample}"),
+                   "model": a.model, "resample": a.resample,
                    "particles": P, "points": N, "keyframes": K, "k_nb": 3, "moves": 3,
                    "table": a.dtype, "l2": "flushed before every timed step (256 MB write)" if not a.no_flush
                    else "not flushed", "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
