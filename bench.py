@@ -34,8 +34,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle×point lik+grad evals/s; frame update ms @100k particles; p50/p99"
 UNIT = "evals/s"
-# FP32 flops of one gradient lookup (FMA = 2); breakdown in the design doc. FP32 tables hold
-# trilinear coefficients (value and gradient in 11 FMAs), 16-bit tables corner values
+# FP32 flops of one gradient lookup (FMA = 2): transform 18, floor and fraction 6, value
+# from the trilinear coefficients 14 and its gradient 8 (16-bit tables, corner values: 21
+# and 12), L + eps, log and reciprocal 3, normalised gradient and weight 4, accumulation 16,
+# moments 7 (19 per point, shared by its 3 lookups)
 FLOPS_GRAD_LOOKUP = {"f32": 76, "bf16": 87, "f16": 87}
 # GICP model: FP32 flops (FMA = 2) of an inlier lookup with the Gauss-Newton terms in
 # the keyframe-frame form the kernel uses, and of a lookup that stops at an empty voxel
