@@ -37,10 +37,10 @@ def _open(srv, w, seed, N=None):
     return sid, f
 
 
-def _serve(names, worlds, interleave=True):
+def _serve(names, worlds, interleave=True, table_dtype=0):
     import paper_2504_18056_b300 as g
     torch_cuda()
-    srv = g.Server(budget_bytes=40 << 30, max_sessions=8, background=True)
+    srv = g.Server(budget_bytes=40 << 30, max_sessions=8, background=True, table_dtype=table_dtype)
     sids = {n: _open(srv, worlds[n], seed=SEEDS[n]) for n in names}
     tickets = {n: [] for n in names}
     for fr in range(FRAMES):
@@ -63,10 +63,12 @@ def _serve(names, worlds, interleave=True):
     return out, stats
 
 
-def test_served_session_equals_plain_step(worlds):
-    served, stats = _serve(["A"], worlds)
+# FP32 tables (pipelined lookup bodies) and BF16 tables (unrolled bodies) in the batched kernels
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_served_session_equals_plain_step(worlds, dtype):
+    served, stats = _serve(["A"], worlds, table_dtype=dtype)
     w = worlds["A"]
-    f = make_filter(w, w["particles"].shape[0], max_points=1024, seed=100)
+    f = make_filter(w, w["particles"].shape[0], dtype=dtype, max_points=1024, seed=100)
     plain = [f.step(w["scans"][fr], w["odometry"][fr], w["cov"]) for fr in range(FRAMES)]
     poses, logw = f.particles()
     f.close()
