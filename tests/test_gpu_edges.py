@@ -13,18 +13,22 @@ pytestmark = pytest.mark.gpu
 # with K >= 3 the three-neighbour pass runs; P, N chosen so that its warps get point
 # chunks of 1 (N = 1, 3), 9 (N = 97) and 10 points with a last chunk of 1 (N = 301):
 # odd and even chunks end the software-pipelined loop at either of its two exits
+@pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("P,N,K", [(1, 1, 1), (1, 512, 4), (33, 7, 2), (65, 300, 3), (40, 1, 4), (40, 3, 4),
                                    (65, 301, 4), (130, 97, 4)])
-def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K):
+def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K, dtype):
+    """FP32 (coefficient records, pipelined passes) and BF16 (corner records,
+    unrolled passes) against the oracle on the same stored values."""
     kfs = box_room["keyframes"][:K]
-    f = make_filter(box_room, P, keyframes=kfs)
+    f = make_filter(box_room, P, dtype=dtype, keyframes=kfs)
+    tables = box_room_tables[:K] if dtype == 0 else [oracle.quantize(t, dtype) for t in box_room_tables[:K]]
     scan = box_room["scans"][2][:N]
     nbr = gpu_nbr(f, P, min(3, K))
     ref_nbr = oracle_nbr(box_room["particles"][:P], box_room["kf_particle_poses"][:K])
     np.testing.assert_array_equal(nbr, ref_nbr)
     ll, g, mom = gpu_eval(f, scan, P)
     o = oracle.eval_batch(box_room["particles"][:P], ref_nbr, box_room["kf_particle_poses"][:K],
-                          box_room_tables[:K], [kf["grid"] for kf in kfs], scan)
+                          tables, [kf["grid"] for kf in kfs], scan)
     assert np.all(np.abs(ll - o["ll"]) <= 1e-4 * np.abs(o["ll"]))
     assert np.all(np.linalg.norm(g - o["g"], axis=1) <= grad_tolerance(o))
     llv, _, _ = gpu_eval(f, scan, P, grad=False)     # the value-only pass
