@@ -132,6 +132,35 @@ def test_eval_matches_oracle(gw):
     f.close()
 
 
+# N >= 7: a scan of fewer points has a rank-deficient covariance whose plane normal is a tie
+@pytest.mark.parametrize("P,N", [(1, 7), (33, 7), (40, 97), (130, 301)])
+def test_small_shapes_match_oracle(gw, P, N):
+    """Small and ragged sizes through the GICP pass (one particle, fewer points
+    than the neighbourhood size, odd point chunks), every particle against the
+    oracle with the tolerances above."""
+    w, grids, covs, maps = gw
+    f = _filter(w, grids, P=P)
+    nbr = np.zeros((P, 3), np.int32)
+    f.select(nbr)
+    scan = np.ascontiguousarray(w["scans"][0][:N])
+    ll = np.zeros(P, np.float32)
+    g = np.zeros((P, 6), np.float32)
+    Hu = np.zeros((P, 22), np.float32)
+    f.eval(scan, ll, g, Hu)
+    scov = oracle.knn_cov(scan, k=min(10, N), eps=EPS)
+    for i in range(P):
+        ks = [int(k) for k in nbr[i]]
+        o = oracle.gicp_eval(w["particles"][i].astype(np.float64), [w["kf_particle_poses"][k][i] for k in ks],
+                             [maps[k] for k in ks], [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4,
+                             gate_delta=1e-3)
+        sl = o["slack"]
+        assert abs(ll[i] - o["ll"]) <= 1e-6 * abs(o["ll"]) + sl[0]
+        gs = np.linalg.norm(o["b"]) * 2
+        assert np.linalg.norm(g[i] - 2 * o["b"]) <= 2e-4 * max(gs, 1e-3 * np.linalg.norm(o["H"])) + 2 * sl[1]
+        assert np.linalg.norm(Hu[i, :21] - _upper(o["H"])) <= 2e-4 * np.linalg.norm(o["H"]) + sl[2] + 1e-6
+    f.close()
+
+
 def test_move_matches_oracle(gw):
     w, grids, covs, maps = gw
     P = 1024
