@@ -12,8 +12,8 @@ from gpu_common import make_filter, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("model", [0, 1])
-def test_resume_is_bit_identical(tmp_path, model):
+@pytest.mark.parametrize("model,dtype", [(0, 0), (0, 1), (1, 0)])
+def test_resume_is_bit_identical(tmp_path, model, dtype):
     import paper_2504_18056_b300 as g
     torch_cuda()
     w = synth.box_room_workload(seed=6, n_particles=1500, n_frames=5)
@@ -24,7 +24,7 @@ def test_resume_is_bit_identical(tmp_path, model):
         kfs = [dict(kf, grid=gr) for kf, gr in zip(w["keyframes"], grids)]
         a = make_filter(w, P, max_points=1024, keyframes=kfs, **cfg)
     else:
-        a = make_filter(w, P, max_points=1024, **cfg)
+        a = make_filter(w, P, dtype=dtype, max_points=1024, **cfg)
     for fr in range(2):
         a.step(w["scans"][fr], w["odometry"][fr], w["cov"])
     path = str(tmp_path / "session.ckpt")
