@@ -48,7 +48,7 @@ GICP_VOXEL = 1.0                # m, voxel edge of the GICP keyframe maps
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes read + written per gradient-pass launch, from one ncu capture of the
 # current kernel at the same particle and point counts (profiles/); None when stale
-TRAFFIC_PER_LAUNCH = {"f32": 32.590e6, "bf16": 30.560e6, "f16": None}
+TRAFFIC_PER_LAUNCH = {"f32": 32.590e6, "bf16": 30.560e6, "f16": 30.522e6}
 
 
 def parse():
