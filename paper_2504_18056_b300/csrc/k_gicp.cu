@@ -354,12 +354,22 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
                 const float i22 = fmaf(a00, a11, -a01 * a01);
                 const float det = fmaf(a00, i00, fmaf(a01, i01, a02 * i02));
                 const float rd = 1.f / det;
-                const float o00 = i00 * rd, o01 = i01 * rd, o02 = i02 * rd;
-                const float o11 = i11 * rd, o12 = i12 * rd, o22 = i22 * rd;
-                const float q0 = fmaf(o00, e0, fmaf(o01, e1, o02 * e2));
-                const float q1 = fmaf(o01, e0, fmaf(o11, e1, o12 * e2));
-                const float q2 = fmaf(o02, e0, fmaf(o12, e1, o22 * e2));
-                const float d2 = fmaf(e0, q0, fmaf(e1, q1, e2 * q2));
+                float o00, o01, o02, o11, o12, o22, q0, q1, q2, d2;
+                if constexpr (GRAD) {
+                    o00 = i00 * rd; o01 = i01 * rd; o02 = i02 * rd;
+                    o11 = i11 * rd; o12 = i12 * rd; o22 = i22 * rd;
+                    q0 = fmaf(o00, e0, fmaf(o01, e1, o02 * e2));
+                    q1 = fmaf(o01, e0, fmaf(o11, e1, o12 * e2));
+                    q2 = fmaf(o02, e0, fmaf(o12, e1, o22 * e2));
+                    d2 = fmaf(e0, q0, fmaf(e1, q1, e2 * q2));
+                } else {
+                    // value only: d^2 = e^T adj(C) e / det, without forming Omega (value
+                    // pass 2.46 -> 2.38 ms)
+                    const float a0 = fmaf(i00, e0, fmaf(i01, e1, i02 * e2));
+                    const float a1 = fmaf(i01, e0, fmaf(i11, e1, i12 * e2));
+                    const float a2 = fmaf(i02, e0, fmaf(i12, e1, i22 * e2));
+                    d2 = fmaf(e0, a0, fmaf(e1, a1, e2 * a2)) * rd;
+                }
                 if (!(d2 < tau)) {
                     lsum -= tau;
                     continue;
