@@ -353,7 +353,10 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
                 const float i12 = fmaf(a01, a02, -a00 * a12);
                 const float i22 = fmaf(a00, a11, -a01 * a01);
                 const float det = fmaf(a00, i00, fmaf(a01, i01, a02 * i02));
-                const float rd = 1.f / det;
+                // C is positive definite (eigenvalues >= ~1e-3), det well inside the
+                // range where the approximate reciprocal (2 ulp) holds; an IEEE division
+                // costs the pass 1.2 % (gradient 4.22 -> 4.27 ms)
+                const float rd = __fdividef(1.f, det);
                 float o00, o01, o02, o11, o12, o22, q0, q1, q2, d2;
                 if constexpr (GRAD) {
                     o00 = i00 * rd; o01 = i01 * rd; o02 = i02 * rd;
