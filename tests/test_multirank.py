@@ -1,4 +1,5 @@
-"""Two CPU ranks (gloo) exercise the replica aggregation of bench.py."""
+"""Two CPU ranks (gloo): the replica aggregation of bench.py, and the exchange
+protocol of a particle set sharded over ranks (paper_2504_18056_b300.shard)."""
 import os
 import socket
 import subprocess
@@ -19,6 +20,15 @@ def test_two_rank_timing_aggregation():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
            os.path.join(HERE, "multirank_worker.py")]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=dict(os.environ, OMP_NUM_THREADS="1"))
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "rank 0 ok" in r.stdout and "rank 1 ok" in r.stdout
+
+
+def test_two_rank_sharded_resampling_matches_single_rank():
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(HERE, "shard_worker.py")]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=dict(os.environ, OMP_NUM_THREADS="1"))
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
     assert "rank 0 ok" in r.stdout and "rank 1 ok" in r.stdout
