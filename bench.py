@@ -45,10 +45,35 @@ FLOPS_GRAD_LOOKUP = {"f32": 76, "bf16": 87, "f16": 87}
 FLOPS_GICP_INLIER = 198
 FLOPS_GICP_MISS = 24
 GICP_VOXEL = 1.0                # m, voxel edge of the GICP keyframe maps
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+FP32_LANES_PER_SM = 128         # FP32 FMA lanes per SM (4 schedulers x 32)
 # DRAM bytes read + written per gradient-pass launch, from one ncu capture of the
 # current kernel at the same particle and point counts (profiles/); None when stale
-TRAFFIC_PER_LAUNCH = {"f32": 32.590e6, "bf16": 30.560e6, "f16": 30.522e6}
+TRAFFIC_PER_LAUNCH = {"f32": None, "bf16": None, "f16": None}
+
+
+def max_sm_mhz(index):
+    """Maximum SM clock of GPU `index` (nvidia-smi), else the driver-measured
+    MEASURED_PEAKS.json figure, else the part's nominal 2032 MHz."""
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        return float(out.splitlines()[0]), "nvidia-smi clocks.max.sm"
+    except Exception:
+        pass
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]), "MEASURED_PEAKS.json"
+    except Exception:
+        return 2032.0, "nominal"
+
+
+def fp32_peak(dev_index, g):
+    """FP32 peak from the unit counts: the SM count read from the device x 128
+    lanes x 2 flop x the maximum SM clock; beside it the measured FMA rate."""
+    ffma, sms = g.probe_ffma()
+    mhz, src = max_sm_mhz(dev_index)
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return peak, (f"{sms} SMs (read from the device) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                  f"({src}); measured FFMA rate {ffma:.1f} TFLOP/s (gmcs_probe_ffma)"), ffma, sms
 
 
 def parse():
@@ -328,6 +353,7 @@ def run_native(a, world, rank, local):
 
     # L2 gather ceiling: random cell-record reads from a 64 MB buffer (fits the 126 MB L2)
     l2_gbs = None if gicp else g.probe_gather(64 << 20, 32 if dtype == 0 else 16)
+    peak_tflops, peak_src_fp32, ffma_tflops, sm_count = fp32_peak(local, g)
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     f.set_profiling(True)
@@ -424,10 +450,12 @@ def run_native(a, world, rank, local):
         "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in kinds.items() if v["launches"]},
         "roofline": {"kernel": "k_gicp gradient pass (GICP terms + Gauss-Newton matrix)" if gicp else
                                "k_pass3 gradient pass (lookup + gradient + moments)", "bound": "alu",
-                     "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                     "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / peak_tflops,
+                     "frac_of_measured_ffma": achieved_tflops / ffma_tflops, "measured_ffma_tflops": ffma_tflops,
+                     "sm_count": sm_count,
                      "traffic": None if gicp else TRAFFIC_PER_LAUNCH.get(a.dtype), "gicp_inlier_frac": inlier_frac,
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz",
+                     "peak_source": peak_src_fp32,
                      "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms},
         "gather": {"algorithmic_bytes_per_launch": lookups_per_launch * rec_bytes, "achieved_gbs": gather_gbs,
                    "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src, "frac_of_hbm": gather_gbs / hbm_peak,

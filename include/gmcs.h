@@ -173,10 +173,14 @@ int gmcs_init_particles(gmcs_ctx* ctx, const float* poses, int P, const double* 
  * pts: n points (n x 3 floats, host or device) in the keyframe's own frame.
  * grid: the table lattice in that frame. The library builds the table on the
  * device (K8: splat of d^2 within r_t, then exp) and stores one 32-byte
- * (FP32) or 16-byte (BF16/FP16) record per lattice cell, in cfg.table_dtype:
- * FP32 records hold the 8 coefficients of the cell's trilinear polynomial
- * (differences of the corner values in float), 16-bit records
- * the 8 corner values rounded to the storage type.
+ * (FP32) or 16-byte (BF16/FP16) record per lattice cell, in cfg.table_dtype,
+ * holding the 8 coefficients of the cell's trilinear polynomial (differences of
+ * the float corner values): FP32 as computed; FP16 rounded to nearest; BF16 as
+ * four 32-bit words, each holding one coefficient as a bfloat16 value (rounded
+ * to nearest) in its low half and another as the word itself read as an FP32
+ * number (the word with that low half nearest to the coefficient: within half a
+ * bfloat16 ulp). gmcs_get_records returns the stored values. A zero record
+ * before the first cell stands for every cell outside the lattice.
  * GICP model: grid is the voxel lattice (n = voxels per axis, voxel (ix,iy,iz)
  * covering origin + h [ix, ix+1) x ...); the library computes every point's
  * plane-regularised covariance from its cfg.knn nearest keyframe points (FP64)
@@ -344,7 +348,9 @@ int gmcs_prune(gmcs_ctx* ctx, const double* x, const double* w, const float* ll,
  *        the call returns without synchronising it
  * P > GMCS_NOALLOC_MAX_P returns GMCS_E_CAPACITY. The first call on a device
  * looks up the array's device address with that device current
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress); make that first call before any stream capture. The
+ * address is kept per device and context: the first call after a
+ * cudaDeviceReset (a new context) looks it up again.
  * Every call shares the one array and leaves its contents behind (each call
  * writes all the scratch it reads): calls whose work can overlap on the GPU --
  * on different streams or from different threads -- race on it and must be
@@ -352,16 +358,6 @@ int gmcs_prune(gmcs_ctx* ctx, const double* x, const double* w, const float* ll,
  */
 #define GMCS_NOALLOC_MAX_P 262144
 int gmcs_resample_noalloc(const double* w, int P, double u, int* anc, void* cuda_stream);
-
-/*
- * Calibration, no counterpart in the paper: the rate (GB/s, into *gbs) of
- * random rec_bytes-sized (16 or 32) record reads from a device buffer of
- * buffer_bytes, with the loads of the lookup pass (one 256-bit load per 32-byte
- * record, one 128-bit load per 16-byte record) -- with a
- * buffer that fits L2 (126 MB), the ceiling for lookups whose cells stay in L2.
- * Allocates and frees the buffer; runs on cuda_stream and synchronises it.
- */
-int gmcs_probe_gather(uint64_t buffer_bytes, int rec_bytes, void* cuda_stream, double* gbs);
 
 /* ---- state access */
 
@@ -383,13 +379,24 @@ int gmcs_overlap(gmcs_ctx* ctx, const float* scan, int N, const double T_rel[12]
  * capacities are at least the saved counts; the context's config becomes the
  * saved one, and the frames that follow are bit-identical to those the saved
  * context would have computed.
- * Errors: GMCS_E_IO (file unreadable, not a checkpoint, or written by another
- * format version: version 1 held FP32 tables as corner values), GMCS_E_STATE (save
- * without particles, load into a context with keyframes), GMCS_E_CAPACITY,
- * GMCS_E_OOM.
+ * gmcs_load checks the whole file on the host before it touches the device:
+ * a config the library would not accept, a table whose storage type does not
+ * match the config, or any size that disagrees with the lattice it belongs to or
+ * with the file's length returns GMCS_E_IO. If the load fails after it began to
+ * restore (device error, out of memory), the context is left empty -- no
+ * particles, no keyframes -- and can be loaded into again.
+ * Errors: GMCS_E_IO (file unreadable, not a checkpoint, inconsistent, or written
+ * by another format version: version 3 stores every field table as coefficient
+ * records after a zero miss record), GMCS_E_STATE (save without particles, load
+ * into a context with keyframes), GMCS_E_CAPACITY (nothing restored), GMCS_E_OOM.
  */
 int gmcs_save(gmcs_ctx* ctx, const char* path);
 int gmcs_load(gmcs_ctx* ctx, const char* path);
+
+/* Check a checkpoint file on the host alone (no device, no context) as gmcs_load
+ * does, and return its config, particle and keyframe counts and frame counter
+ * (any output pointer may be NULL). Errors: GMCS_E_INVALID, GMCS_E_IO. */
+int gmcs_checkpoint_info(const char* path, gmcs_config* cfg, int* P, int* K, uint32_t* frame);
 
 /* Copy current poses (P x 12 floats) and/or log-weights (P doubles) out; NULL skips. */
 int gmcs_get_particles(gmcs_ctx* ctx, float* poses, double* logw);
@@ -412,12 +419,29 @@ int gmcs_get_frame_diag(gmcs_ctx* ctx, float* ll, double* w, int* anc, int* nbr)
  * cov: n x 6 doubles (xx xy xz yy yz zz), host or device. Any model. */
 int gmcs_point_covariances(gmcs_ctx* ctx, const float* pts, int n, double* cov);
 
-/* Copy table k as float vertex values [n2][n1][n0] (unpacked from its cells;
- * from FP32 coefficient records, the sum of the corner's coefficients in double,
- * within a few float roundings of the value the table was built from).
+/* Copy table k as float vertex values [n2][n1][n0], read back from its cell
+ * records: vertex i is the corner of cell min(i, n-2) whose value is the sum of
+ * the cell's stored coefficients (in double, rounded once). With FP32 records
+ * that is within a few float roundings of the value the table was built from.
  * GICP model: the voxel records, 12 floats per voxel [n2][n1][n0]: mean (3),
  * 1 or 0 (voxel holds points), covariance xx xy xz yy yz zz, 0, 0. */
 int gmcs_get_table(gmcs_ctx* ctx, int k, float* vals);
+
+/* A counter of the context's state: every call that can change the particles'
+ * current or keyframe poses, the neighbour sets or the keyframes (gmcs_init_particles,
+ * gmcs_add_keyframe, gmcs_step, gmcs_predict, gmcs_select, gmcs_move,
+ * gmcs_set_kf_poses, gmcs_load, a served frame) increases it. A caller that keeps
+ * results derived from that state (the autograd wrapper's saved forward) compares
+ * it to detect a change. */
+int gmcs_state_version(gmcs_ctx* ctx, uint64_t* version);
+
+/* Copy the stored trilinear coefficients of cells [c0, c0 + n) of field table k
+ * (cells numbered x fastest, (n0-1) x (n1-1) x (n2-1) of them): 8 floats per cell,
+ * c0..c7 of L = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz in the
+ * in-cell fraction (x, y, z) in [0, 1)^3, exactly the values the lookups use
+ * (16-bit records decoded). coef: n x 8 floats, host or device.
+ * Errors: GMCS_E_INVALID for a GICP map or a range past the last cell. */
+int gmcs_get_records(gmcs_ctx* ctx, int k, uint64_t c0, uint64_t n, float* coef);
 /* Current sizes. Any pointer may be NULL. */
 int gmcs_get_sizes(gmcs_ctx* ctx, int* P, int* K, uint32_t* frame);
 

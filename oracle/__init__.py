@@ -23,7 +23,7 @@ _u32p = C.POINTER(C.c_uint32)
 
 
 class Grid(C.Structure):
-    _fields_ = [("origin", C.c_double * 3), ("h", C.c_double), ("n", C.c_int * 3)]
+    _fields_ = [("origin", C.c_double * 3), ("h", C.c_double), ("n", C.c_int * 3), ("coef", C.c_int)]
 
 
 class EvalParams(C.Structure):
@@ -74,12 +74,15 @@ def _f(a):
     return a, a.ctypes.data_as(_fp)
 
 
-def make_grid(g):
+def make_grid(g, table=None):
+    """ora_grid of a lattice dict; a 4-D table (cells x 8 coefficients) marks a
+    coefficient table."""
     gr = Grid()
     for a in range(3):
         gr.origin[a] = float(g["origin"][a])
         gr.n[a] = int(g["dims"][a])
     gr.h = float(g["h"])
+    gr.coef = 1 if (table is not None and np.ndim(table) == 4) else 0
     return gr
 
 
@@ -168,9 +171,84 @@ def quantize(vals, dtype):
     return out
 
 
+def coef_table(vals):
+    """Per-cell coefficients c0..c7 (FP64) of the trilinear interpolation of a
+    vertex table (nz, ny, nx): array (nz-1, ny-1, nx-1, 8) with
+      L = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz
+    in the in-cell fraction, by inclusion-exclusion over the corners."""
+    v = np.asarray(vals, np.float64)
+    V = {(dx, dy, dz): v[dz:v.shape[0] - 1 + dz, dy:v.shape[1] - 1 + dy, dx:v.shape[2] - 1 + dx]
+         for dx in (0, 1) for dy in (0, 1) for dz in (0, 1)}
+    c = np.empty(v[:-1, :-1, :-1].shape + (8,))
+    c[..., 0] = V[0, 0, 0]
+    c[..., 1] = V[1, 0, 0] - V[0, 0, 0]
+    c[..., 2] = V[0, 1, 0] - V[0, 0, 0]
+    c[..., 3] = V[0, 0, 1] - V[0, 0, 0]
+    c[..., 4] = V[1, 1, 0] - V[1, 0, 0] - V[0, 1, 0] + V[0, 0, 0]
+    c[..., 5] = V[1, 0, 1] - V[1, 0, 0] - V[0, 0, 1] + V[0, 0, 0]
+    c[..., 6] = V[0, 1, 1] - V[0, 1, 0] - V[0, 0, 1] + V[0, 0, 0]
+    c[..., 7] = (V[1, 1, 1] - V[1, 1, 0] - V[1, 0, 1] - V[0, 1, 1]
+                 + V[1, 0, 0] + V[0, 1, 0] + V[0, 0, 1] - V[0, 0, 0])
+    return c
+
+
+# Storage of the 16-bit coefficient records (the library's table format, not the
+# paper's): the coefficients are taken in FP32; the record's word e (e = 0..3)
+# holds HI[e] in its high half and LO[e] in its low half.
+_REC_HI = (4, 2, 7, 6)
+_REC_LO = (1, 0, 5, 3)
+
+
+def _bf16_rn_bits(x32):
+    """bfloat16 bits (uint32, in the low half) of float32 values, rounded to nearest even."""
+    b = x32.view(np.uint32).astype(np.uint64)
+    r = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return r.astype(np.uint32)
+
+
+def quantize_coef(coef, dtype):
+    """The coefficients (..., 8) as a 16-bit record stores them, widened to FP64.
+    FP16 (dtype 2): each rounded to nearest even. BF16 (dtype 1): LO[e] rounded to
+    bfloat16; HI[e] becomes the FP32 number whose low 16 bits are those bfloat16
+    bits and whose value is nearest to HI[e] (ties to the candidate that keeps
+    HI[e]'s own high half)."""
+    c32 = np.asarray(coef, np.float64).astype(np.float32)
+    out = c32.astype(np.float64)
+    if dtype == 2:
+        return c32.astype(np.float16).astype(np.float64)
+    assert dtype == 1
+    for hi, lo in zip(_REC_HI, _REC_LO):
+        lo16 = _bf16_rn_bits(np.ascontiguousarray(c32[..., lo]))
+        out[..., lo] = (lo16 << np.uint32(16)).view(np.float32).astype(np.float64)
+        A = c32[..., hi]
+        base = (A.view(np.uint32) & np.uint32(0xFFFF0000)) | lo16
+        mag = (base >> np.uint32(16)) & np.uint32(0x7FFF)
+        best = base.copy()
+        a64 = A.astype(np.float64)
+        err = np.abs(a64 - base.view(np.float32).astype(np.float64))
+        with np.errstate(invalid="ignore", over="ignore"):
+            for cand, ok in ((base - np.uint32(0x10000), mag > 0), (base + np.uint32(0x10000), mag < 0x7F7F)):
+                e = np.abs(a64 - cand.view(np.float32).astype(np.float64))
+                take = ok & (e < err)
+                best = np.where(take, cand, best)
+                err = np.where(take, e, err)
+        out[..., hi] = best.view(np.float32).astype(np.float64)
+    return out
+
+
+def stored_table(vals, dtype):
+    """What the lookups of a table with storage type dtype evaluate, from the FP64
+    vertex table: FP32 (0) the vertex table itself (the FP32 coefficients are
+    differences of the float corners, within ~2.4e-7 of it); BF16 (1) and FP16 (2)
+    the cell coefficients as the 16-bit records store them (quantize_coef)."""
+    if dtype == 0:
+        return np.asarray(vals, np.float64)
+    return quantize_coef(coef_table(vals), dtype)
+
+
 def cell_eval(vals, grid, c, u):
+    gr = make_grid(grid, vals)
     v, pv = _d(vals)
-    gr = make_grid(grid)
     ci = (C.c_int * 3)(*[int(x) for x in c])
     uu = (C.c_double * 3)(*[float(x) for x in u])
     L = C.c_double()
@@ -188,7 +266,7 @@ def eval_particle(Tt, Tk, tables, grids, scan, eps=1e-3, face_delta=1e-3, cells=
     n_nb = Tk.shape[0]
     tabs = [np.ascontiguousarray(t, np.float64) for t in tables]
     tab_ptrs = (_dp * max(n_nb, 1))(*[t.ctypes.data_as(_dp) for t in tabs])
-    grs = (Grid * max(n_nb, 1))(*[make_grid(g) for g in grids])
+    grs = (Grid * max(n_nb, 1))(*[make_grid(g, t) for g, t in zip(grids, tabs)])
     scan, ps = _f(scan)
     N = scan.shape[0]
     prm = EvalParams(eps, face_delta)
@@ -439,7 +517,7 @@ class State:
         P = self.poses.shape[0]
         K = len(self.tables)
         tab_ptrs = (_dp * max(K, 1))(*[t.ctypes.data_as(_dp) for t in self.tables])
-        grs = (Grid * max(K, 1))(*[make_grid(g) for g in self.grids])
+        grs = (Grid * max(K, 1))(*[make_grid(g, t) for g, t in zip(self.grids, self.tables)])
         scan, ps = _f(scan)
         psc = None
         if scov is not None:

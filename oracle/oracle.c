@@ -322,6 +322,16 @@ int ora_cell_eval(const double* vals, const ora_grid* g, const int c[3], const d
     for (int a = 0; a < 3; ++a)
         if (c[a] < 0 || c[a] > g->n[a] - 2) return 0;
     double f[3] = {u[0] - c[0], u[1] - c[1], u[2] - c[2]};
+    if (g->coef) {
+        const size_t cell = ((size_t)c[2] * (g->n[1] - 1) + c[1]) * (size_t)(g->n[0] - 1) + c[0];
+        const double* k = vals + 8 * cell;
+        const double x = f[0], y = f[1], z = f[2];
+        *L = k[0] + k[1] * x + k[2] * y + k[3] * z + k[4] * x * y + k[5] * x * z + k[6] * y * z + k[7] * x * y * z;
+        dLdu[0] = k[1] + k[4] * y + k[5] * z + k[7] * y * z;
+        dLdu[1] = k[2] + k[4] * x + k[6] * z + k[7] * x * z;
+        dLdu[2] = k[3] + k[5] * x + k[6] * y + k[7] * x * y;
+        return 1;
+    }
     for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
             for (int dx = 0; dx < 2; ++dx) {

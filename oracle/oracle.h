@@ -31,6 +31,8 @@ typedef struct {
     double origin[3];
     double h;
     int n[3];
+    int coef;   /* 0: vals holds vertex values [n2][n1][n0]; 1: vals holds per-cell
+                   trilinear coefficients c0..c7 [n2-1][n1-1][n0-1][8] (below) */
 } ora_grid;
 
 /* ---- SE(3) (closed forms: Rodrigues + left Jacobian; Taylor below 1e-4 rad) */
@@ -61,6 +63,10 @@ void ora_build_table_brute(const float* pts, int n, const ora_grid* g, double si
 void ora_quantize(const double* in, size_t n, int dtype, double* out);
 
 /* Trilinear value and gradient (w.r.t. lattice coordinate u) of cell c at u.
+ * Vertex tables: the interpolation of the cell's 8 corner values. Coefficient
+ * tables (g->coef): with f = u - c, the polynomial
+ *   L = c0 + c1 fx + c2 fy + c3 fz + c4 fx fy + c5 fx fz + c6 fy fz + c7 fx fy fz
+ * of the cell's stored coefficients and its derivative.
  * Returns 1 if c is inside the table, else 0 (value and gradient set to 0). */
 int ora_cell_eval(const double* vals, const ora_grid* g, const int c[3], const double u[3],
                   double* L, double dLdu[3]);

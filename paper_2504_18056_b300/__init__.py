@@ -17,6 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgmcs.so")
+DIAG_PATH = os.path.join(HERE, "libgmcs_diag.so")
 
 OK = 0
 E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE, E_BUDGET, E_IO = -1, -2, -3, -4, -5, -6, -7, -8
@@ -101,8 +102,12 @@ _SIGS = {
     "gmcs_get_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmcs_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gmcs_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "gmcs_checkpoint_info": (C.c_int, [C.c_char_p, C.POINTER(Config), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_uint32)]),
     "gmcs_get_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_get_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "gmcs_get_records": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_void_p]),
+    "gmcs_state_version": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "gmcs_point_covariances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "gmcs_overlap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gmcs_set_kf_poses": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -114,7 +119,6 @@ _SIGS = {
     "gmcs_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "gmcs_strerror": (C.c_char_p, [C.c_int]),
     "gmcs_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
-    "gmcs_probe_gather": (C.c_int, [C.c_uint64, C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "gmcs_server_create": (C.c_int, [C.POINTER(Config), C.c_uint64, C.c_int, C.POINTER(C.c_void_p)]),
     "gmcs_server_destroy": (C.c_int, [C.c_void_p]),
     "gmcs_server_start": (C.c_int, [C.c_void_p]),
@@ -189,12 +193,53 @@ def resample_noalloc(w, u, anc, stream=None):
     return anc
 
 
+# diagnostics library (include/gmcs_diag.h): calibration, not the particle-update ABI
+_DIAG_SIGS = {
+    "gmcs_probe_gather": (C.c_int, [C.c_uint64, C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
+    "gmcs_probe_ffma": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+}
+_DIAG = None
+
+
+def diag_lib():
+    """Load libgmcs_diag.so (raises if it has not been built)."""
+    global _DIAG
+    if _DIAG is None:
+        if not os.path.exists(DIAG_PATH):
+            raise ImportError(f"{DIAG_PATH} is missing; build it with `python -m paper_2504_18056_b300.build`")
+        L = C.CDLL(DIAG_PATH)
+        for name, (res, args) in _DIAG_SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _DIAG = L
+    return _DIAG
+
+
+def probe_ffma(stream=None):
+    """(FP32 FMA rate in TFLOP/s, multiprocessor count) of the current device (gmcs_probe_ffma)."""
+    st = _current_stream() if stream is None else C.c_void_p(int(stream))
+    r, n = C.c_double(), C.c_int()
+    _check(diag_lib().gmcs_probe_ffma(st, C.byref(r), C.byref(n)), "gmcs_probe_ffma")
+    return r.value, n.value
+
+
 def probe_gather(buffer_bytes, rec_bytes=32, stream=None):
-    """Random record-gather rate (GB/s) from a device buffer (gmcs_probe_gather)."""
+    """Random record-gather rate (GB/s) from a device buffer (gmcs_probe_gather, diagnostics library)."""
     st = _current_stream() if stream is None else C.c_void_p(int(stream))
     r = C.c_double()
-    _check(lib().gmcs_probe_gather(C.c_uint64(int(buffer_bytes)), int(rec_bytes), st, C.byref(r)), "gmcs_probe_gather")
+    _check(diag_lib().gmcs_probe_gather(C.c_uint64(int(buffer_bytes)), int(rec_bytes), st, C.byref(r)),
+           "gmcs_probe_gather")
     return r.value
+
+
+def checkpoint_info(path):
+    """Check a checkpoint file on the host (gmcs_checkpoint_info, no device needed);
+    returns (config, P, K, frame) or raises GmcsError (E_IO for a bad file)."""
+    cfg, P, K, fr = Config(), C.c_int(), C.c_int(), C.c_uint32()
+    _check(lib().gmcs_checkpoint_info(os.fsencode(path), C.byref(cfg), C.byref(P), C.byref(K), C.byref(fr)),
+           "gmcs_checkpoint_info")
+    return cfg, P.value, K.value, fr.value
 
 
 def default_config(**kw):
@@ -366,6 +411,16 @@ class Filter:
 
     def get_table(self, k, vals):
         _check(lib().gmcs_get_table(self.ctx, int(k), _ptr(vals)), "gmcs_get_table")
+
+    def state_version(self):
+        """Counter bumped by every call that changes poses, neighbours or keyframes."""
+        v = C.c_uint64()
+        _check(lib().gmcs_state_version(self.ctx, C.byref(v)), "gmcs_state_version")
+        return v.value
+
+    def get_records(self, k, c0, n, coef):
+        """Stored coefficients c0..c7 of cells [c0, c0 + n) of table k into coef (n x 8 float32)."""
+        _check(lib().gmcs_get_records(self.ctx, int(k), int(c0), int(n), _ptr(coef)), "gmcs_get_records")
 
     def particles(self):
         P, _, _ = self.sizes()

@@ -6,6 +6,12 @@ pose, neighbour keyframes as last selected). The forward runs the value-only
 lookup pass; the backward runs the lookup pass with gradient at the same poses
 and the chain rule through the SE(3) right Jacobian, both in CUDA
 (gmcs_loglik / gmcs_loglik_backward).
+
+The backward reads T0 and the neighbour sets from the filter again, so it is
+only the derivative of the forward if the filter has not changed in between: the
+forward records the filter's state version (gmcs_state_version) and the backward
+raises if any call since (a step, a move, a new selection or keyframe, ...)
+has changed it.
 """
 import torch
 
@@ -20,12 +26,17 @@ class ScanLogLik(torch.autograd.Function):
         ll = torch.empty(xi.shape[0], dtype=torch.float32, device=xi.device)
         filt.loglik(xi, scan, ll)
         ctx.filt = filt
+        ctx.version = filt.state_version()
         ctx.save_for_backward(xi, scan)
         return ll
 
     @staticmethod
     def backward(ctx, grad_ll):
         xi, scan = ctx.saved_tensors
+        if ctx.filt.state_version() != ctx.version:
+            raise RuntimeError("ScanLogLik backward: the filter's poses, neighbours or keyframes changed since the "
+                               "forward (state version %d -> %d); run the forward again"
+                               % (ctx.version, ctx.filt.state_version()))
         grad_xi = torch.empty_like(xi)
         ctx.filt.loglik_backward(xi, scan, grad_ll.detach().to(torch.float32).contiguous(), grad_xi)
         return grad_xi, None, None

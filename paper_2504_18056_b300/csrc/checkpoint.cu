@@ -11,8 +11,10 @@
 // counter-based on the restored seed and frame counter).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "../../include/gmcs.h"
@@ -24,7 +26,7 @@ using namespace gmcs;
 namespace {
 
 const char kMagic[8] = {'G', 'M', 'C', 'S', 'C', 'K', 'P', 'T'};
-constexpr uint32_t kVersion = 2;   // 2: FP32 field tables hold trilinear coefficients
+constexpr uint32_t kVersion = 3;   // 3: every field table holds coefficients after a zero miss record
 
 struct Header {
     char magic[8];
@@ -34,6 +36,13 @@ struct Header {
     int32_t P, K;
     double path_now;
     double odo[12];
+};
+
+// Per keyframe, before its table bytes.
+struct TableHead {
+    int32_t dtype;
+    gmcs_grid grid;
+    uint64_t bytes;
 };
 
 int st(cudaError_t e) { return e == cudaSuccess ? GMCS_OK : GMCS_E_CUDA; }
@@ -46,7 +55,86 @@ struct File {
     }
     bool put(const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
     bool get(void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+    int64_t tell() { return (int64_t)ftello(f); }
+    bool seek(int64_t off) { return fseeko(f, (off_t)off, SEEK_SET) == 0; }
+    int64_t size() {
+        const int64_t here = tell();
+        if (here < 0 || fseeko(f, 0, SEEK_END) != 0) return -1;
+        const int64_t n = tell();
+        return seek(here) ? n : -1;
+    }
 };
+
+bool finite_grid(const gmcs_grid& g) {
+    return std::isfinite(g.origin[0]) && std::isfinite(g.origin[1]) && std::isfinite(g.origin[2]) &&
+           std::isfinite(g.h) && g.h > 0.0;
+}
+
+// Bytes a keyframe's table must hold for its storage type and lattice, or 0 when
+// the pair is not one the library writes (field tables: one record per cell plus
+// the miss record; GICP voxel maps: 48 bytes per voxel).
+uint64_t expected_table_bytes(const TableHead& t, const gmcs_config& cfg) {
+    if (!finite_grid(t.grid)) return 0;
+    if (t.dtype == 3) {
+        if (cfg.model != GMCS_MODEL_GICP) return 0;
+        uint64_t nv = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (t.grid.n[a] < 1) return 0;
+            nv *= (uint64_t)t.grid.n[a];
+        }
+        return nv < ((uint64_t)1 << 31) ? nv * 48 : 0;
+    }
+    if (t.dtype < 0 || t.dtype > 2 || cfg.model != GMCS_MODEL_FIELD || t.dtype != cfg.table_dtype) return 0;
+    uint64_t nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (t.grid.n[a] < 2 || t.grid.n[a] > (1 << 22)) return 0;
+        nc *= (uint64_t)(t.grid.n[a] - 1);
+    }
+    return nc < ((uint64_t)1 << 31) ? (nc + 1) * (t.dtype == 0 ? 32 : 16) : 0;
+}
+
+uint64_t expected_occ_bytes(const gmcs_grid& g) {
+    if (!finite_grid(g)) return 0;
+    uint64_t nv = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (g.n[a] < 1) return 0;
+        nv *= (uint64_t)g.n[a];
+    }
+    return nv < ((uint64_t)1 << 32) ? nv : 0;
+}
+
+// Walk a whole checkpoint on the host, reading only headers and skipping
+// payloads, and check every size against the lattice it belongs to and the
+// file's length. Leaves the file positioned just after the header.
+int validate(File& in, Header& h) {
+    const int64_t fsize = in.size();
+    if (fsize < 0 || !in.seek(0)) return GMCS_E_IO;
+    if (!in.get(&h, sizeof(h)) || std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != kVersion)
+        return GMCS_E_IO;
+    if (!config_valid(&h.cfg) || h.P <= 0 || h.K < 0 || h.K > (1 << 20) || !std::isfinite(h.path_now))
+        return GMCS_E_IO;
+    const int64_t pose_bytes = (int64_t)sizeof(float) * 12 * h.P;
+    int64_t pos = in.tell() + pose_bytes + (int64_t)sizeof(double) * h.P;
+    for (int k = 0; k < h.K; ++k) {
+        TableHead t;
+        if (pos > fsize || !in.seek(pos) || !in.get(&t, sizeof(t))) return GMCS_E_IO;
+        const uint64_t want = expected_table_bytes(t, h.cfg);
+        if (want == 0 || t.bytes != want) return GMCS_E_IO;
+        pos += (int64_t)sizeof(t) + (int64_t)t.bytes;
+        gmcs_grid og;
+        uint64_t occ_bytes = 0;
+        if (pos > fsize || !in.seek(pos) || !in.get(&og, sizeof(og)) || !in.get(&occ_bytes, sizeof(occ_bytes)))
+            return GMCS_E_IO;
+        const uint64_t want_occ = expected_occ_bytes(og);
+        if (want_occ == 0 || occ_bytes != want_occ) return GMCS_E_IO;
+        pos += (int64_t)(sizeof(og) + sizeof(occ_bytes) + occ_bytes);
+        double d = 0.0;
+        if (pos > fsize || !in.seek(pos) || !in.get(&d, sizeof(d)) || !std::isfinite(d)) return GMCS_E_IO;
+        pos += (int64_t)sizeof(d) + pose_bytes;
+    }
+    if (pos != fsize) return GMCS_E_IO;
+    return in.seek(sizeof(h)) ? GMCS_OK : GMCS_E_IO;
+}
 
 // P x 12 poses from a SoA block of the context to the host.
 int poses_out(gmcs_ctx* c, const float* soa, std::vector<float>& host) {
@@ -75,8 +163,9 @@ int poses_in(gmcs_ctx* c, const std::vector<float>& host, float* soa) {
 
 }  // namespace
 
-extern "C" int gmcs_save(gmcs_ctx* c, const char* path) {
-    if (!c || !path) return GMCS_E_INVALID;
+namespace {
+
+int save_impl(gmcs_ctx* c, const char* path) {
     if (!c->have_particles) return GMCS_E_STATE;
     int rc = st(cudaStreamSynchronize(c->stream));
     if (rc) return rc;
@@ -102,13 +191,16 @@ extern "C" int gmcs_save(gmcs_ctx* c, const char* path) {
     std::vector<unsigned char> buf;
     for (int k = 0; k < c->K; ++k) {
         const HostTable& t = c->tables[k];
-        const int32_t dtype = t.dtype;
-        const uint64_t bytes = t.bytes, occ_bytes = t.occ_bytes;
-        if (!out.put(&dtype, sizeof(dtype)) || !out.put(&t.grid, sizeof(t.grid)) || !out.put(&bytes, sizeof(bytes)))
-            return GMCS_E_IO;
-        buf.resize(bytes);
-        if ((rc = st(cudaMemcpy(buf.data(), t.cells, bytes, cudaMemcpyDeviceToHost)))) return rc;
-        if (!out.put(buf.data(), bytes)) return GMCS_E_IO;
+        TableHead th;
+        std::memset(&th, 0, sizeof(th));
+        th.dtype = t.dtype;
+        th.grid = t.grid;
+        th.bytes = t.bytes;
+        const uint64_t occ_bytes = t.occ_bytes;
+        if (!out.put(&th, sizeof(th))) return GMCS_E_IO;
+        buf.resize(t.bytes);
+        if ((rc = st(cudaMemcpy(buf.data(), t.cells, t.bytes, cudaMemcpyDeviceToHost)))) return rc;
+        if (!out.put(buf.data(), t.bytes)) return GMCS_E_IO;
         if (!out.put(&t.occ_grid, sizeof(t.occ_grid)) || !out.put(&occ_bytes, sizeof(occ_bytes))) return GMCS_E_IO;
         buf.resize(occ_bytes);
         if ((rc = st(cudaMemcpy(buf.data(), t.occ, occ_bytes, cudaMemcpyDeviceToHost)))) return rc;
@@ -121,43 +213,60 @@ extern "C" int gmcs_save(gmcs_ctx* c, const char* path) {
     return std::fflush(out.f) == 0 ? GMCS_OK : GMCS_E_IO;
 }
 
-extern "C" int gmcs_load(gmcs_ctx* c, const char* path) {
-    if (!c || !path) return GMCS_E_INVALID;
-    if (c->K != 0) return GMCS_E_STATE;   // restore into an empty context
+// Drop what a failed load restored: tables, keyframe count, particles.
+void unload(gmcs_ctx* c) {
+    cudaStreamSynchronize(c->stream);
+    for (auto& t : c->tables) {
+        c->dev_bytes -= std::min(c->dev_bytes, t.bytes + t.occ_bytes);
+        cudaFree(t.cells);
+        cudaFree(t.occ);
+    }
+    c->tables.clear();
+    c->kf_path.clear();
+    c->K = 0;
+    c->P = 0;
+    c->have_particles = false;
+    c->last_valid = false;
+    cudaGetLastError();
+}
+
+int load_impl(gmcs_ctx* c, const char* path, bool* touched) {
     File in(std::fopen(path, "rb"));
     if (!in.f) return GMCS_E_IO;
     Header h;
-    if (!in.get(&h, sizeof(h)) || std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != kVersion)
-        return GMCS_E_IO;
-    if (h.P <= 0 || h.K < 0) return GMCS_E_IO;
+    int rc = validate(in, h);
+    if (rc) return rc;
     if (h.P > c->Pmax || h.K > c->Kmax) return GMCS_E_CAPACITY;
     std::vector<float> poses((size_t)12 * h.P);
     std::vector<double> logw(h.P);
     if (!in.get(poses.data(), sizeof(float) * poses.size()) || !in.get(logw.data(), sizeof(double) * logw.size()))
         return GMCS_E_IO;
-    int rc = gmcs_init_particles(c, poses.data(), h.P, logw.data());
+    *touched = true;
+    rc = gmcs_init_particles(c, poses.data(), h.P, logw.data());
     if (rc) return rc;
+    std::vector<unsigned char> buf;
     for (int k = 0; k < h.K; ++k) {
+        TableHead th;
+        if (!in.get(&th, sizeof(th))) return GMCS_E_IO;
         HostTable t;
-        int32_t dtype = 0;
-        uint64_t bytes = 0, occ_bytes = 0;
-        if (!in.get(&dtype, sizeof(dtype)) || !in.get(&t.grid, sizeof(t.grid)) || !in.get(&bytes, sizeof(bytes)))
-            return GMCS_E_IO;
-        t.dtype = dtype;
-        t.bytes = bytes;
-        std::vector<unsigned char> buf(bytes);
-        if (!in.get(buf.data(), bytes)) return GMCS_E_IO;
-        if (cudaMalloc(&t.cells, bytes) != cudaSuccess) {
+        t.dtype = th.dtype;
+        t.grid = th.grid;
+        t.bytes = th.bytes;
+        t.lead = th.dtype == 3 ? 0 : (th.dtype == 0 ? 32 : 16);
+        buf.resize(t.bytes);
+        if (!in.get(buf.data(), t.bytes)) return GMCS_E_IO;
+        if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
             cudaGetLastError();
             return GMCS_E_OOM;
         }
-        rc = st(cudaMemcpy(t.cells, buf.data(), bytes, cudaMemcpyHostToDevice));
+        uint64_t occ_bytes = 0;
+        rc = st(cudaMemcpy(t.cells, buf.data(), t.bytes, cudaMemcpyHostToDevice));
         if (!rc && (!in.get(&t.occ_grid, sizeof(t.occ_grid)) || !in.get(&occ_bytes, sizeof(occ_bytes)))) rc = GMCS_E_IO;
         if (!rc) {
             buf.resize(occ_bytes);
             if (!in.get(buf.data(), occ_bytes)) rc = GMCS_E_IO;
         }
-        if (!rc && cudaMalloc((void**)&t.occ, occ_bytes > 0 ? occ_bytes : 1) != cudaSuccess) {
+        if (!rc && cudaMalloc((void**)&t.occ, occ_bytes) != cudaSuccess) {
             cudaGetLastError();
             t.occ = nullptr;
             rc = GMCS_E_OOM;
@@ -171,7 +280,7 @@ extern "C" int gmcs_load(gmcs_ctx* c, const char* path) {
         if (!rc) {
             TableDesc td;
             std::memset(&td, 0, sizeof(td));
-            td.cells = t.cells;
+            td.cells = table_cells(t);
             td.ox = (float)t.grid.origin[0];
             td.oy = (float)t.grid.origin[1];
             td.oz = (float)t.grid.origin[2];
@@ -201,4 +310,51 @@ extern "C" int gmcs_load(gmcs_ctx* c, const char* path) {
     c->path_now = h.path_now;
     std::memcpy(c->odo, h.odo, sizeof(h.odo));
     return GMCS_OK;
+}
+
+}  // namespace
+
+extern "C" int gmcs_save(gmcs_ctx* c, const char* path) {
+    if (!c || !path) return GMCS_E_INVALID;
+    try {
+        return save_impl(c, path);
+    } catch (const std::bad_alloc&) {
+        return GMCS_E_OOM;
+    } catch (...) {
+        return GMCS_E_IO;
+    }
+}
+
+extern "C" int gmcs_load(gmcs_ctx* c, const char* path) {
+    if (!c || !path) return GMCS_E_INVALID;
+    if (c->K != 0) return GMCS_E_STATE;   // restore into an empty context
+    int rc;
+    bool touched = false;   // the context's particles were replaced
+    try {
+        rc = load_impl(c, path, &touched);
+    } catch (const std::bad_alloc&) {
+        rc = GMCS_E_OOM;
+    } catch (...) {
+        rc = GMCS_E_IO;
+    }
+    if (rc && touched) unload(c);
+    return rc;
+}
+
+extern "C" int gmcs_checkpoint_info(const char* path, gmcs_config* cfg, int* P, int* K, uint32_t* frame) {
+    if (!path) return GMCS_E_INVALID;
+    try {
+        File in(std::fopen(path, "rb"));
+        if (!in.f) return GMCS_E_IO;
+        Header h;
+        const int rc = validate(in, h);
+        if (rc) return rc;
+        if (cfg) *cfg = h.cfg;
+        if (P) *P = h.P;
+        if (K) *K = h.K;
+        if (frame) *frame = h.frame;
+        return GMCS_OK;
+    } catch (...) {
+        return GMCS_E_IO;
+    }
 }

@@ -7,12 +7,13 @@
 //   neighbour indices   int   [k_nb][ld]
 //   log-weights         double[ld]
 //   scan                float4[N]               (x, y, z, 0) in the sensor frame
-//   tables              per keyframe, one record of 8 corner values per lattice
-//                       cell, cells ordered x fastest: FP32 records are 32 B
-//                       (two float4), BF16/FP16 records are 16 B (one uint4).
-//                       Corner (dx, dy, dz) sits at slot dz + 2 dy + 4 dx: the
-//                       x = 0 face first, z pairs adjacent, so the x- and y-
-//                       interpolations run on packed float pairs.
+//   tables              per keyframe, one record per lattice cell, cells ordered
+//                       x fastest, holding the 8 coefficients of the cell's
+//                       trilinear polynomial: FP32 records are 32 B (two float4),
+//                       BF16/FP16 records 16 B (one uint4, two coefficients per
+//                       32-bit word). One all-zero "miss" record sits just before
+//                       cell 0: a lookup outside the lattice reads it (index -1)
+//                       instead of branching around its load.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -207,15 +208,15 @@ __device__ __forceinline__ void normal6(uint64_t seed, uint32_t i, uint32_t t, f
 
 // ---------------------------------------------------------------- table cells
 
-// 16-bit tables: a cell record holds the cell's 8 corner values; slot of corner
-// (dx, dy, dz) within it.
+// Corner (dx, dy, dz) of a cell in the 8-value corner arrays the table build
+// and the vertex read-back use: the x = 0 face first, z pairs adjacent.
 __host__ __device__ constexpr int rec_slot(int dx, int dy, int dz) { return dz + 2 * dy + 4 * dx; }
 
-// FP32 tables: a cell record holds the 8 coefficients of the cell's trilinear
-// polynomial in the in-cell fraction (x, y, z) in [0, 1)^3,
+// A cell record holds the 8 coefficients of the cell's trilinear polynomial in
+// the in-cell fraction (x, y, z) in [0, 1)^3,
 //   L = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz,
-// stored as the pairs (c4, c2), (c7, c6), (c1, c0), (c5, c3) that the packed
-// evaluation reads. Slot of coefficient i:
+// in the order (c4, c2), (c7, c6), (c1, c0), (c5, c3) that the packed evaluation
+// reads as float pairs. Slot of coefficient i in that order:
 __host__ __device__ constexpr int coef_slot(int i) {
     return i == 0 ? 5 : i == 1 ? 4 : i == 2 ? 1 : i == 3 ? 7 : i == 4 ? 0 : i == 5 ? 6 : i == 6 ? 3 : 2;
 }
@@ -240,8 +241,8 @@ __device__ __forceinline__ void corners_to_coef(const float* v, float* rec) {
     for (int i = 0; i < 8; ++i) rec[coef_slot(i)] = c[i];
 }
 
-// The value at corner (dx, dy, dz) of an FP32 coefficient record (in double,
-// rounded once).
+// The value at corner (dx, dy, dz) of a coefficient record in record order (in
+// double, rounded once).
 __host__ __device__ inline float coef_corner(const float* rec, int dx, int dy, int dz) {
     double s = rec[coef_slot(0)];
     if (dx) s += rec[coef_slot(1)];
@@ -254,6 +255,64 @@ __host__ __device__ inline float coef_corner(const float* rec, int dx, int dy, i
     return (float)s;
 }
 
+// 16-bit records: word e (e = 0..3) of the uint4 holds record slots e (high
+// half) and 4 + e (low half). FP16: both halves are binary16 values, rounded to
+// nearest. BF16: the low half is a bfloat16 value B (rounded to nearest), and the
+// whole 32-bit word, read as an FP32 number, is the other coefficient A -- the
+// word is the one with low half B whose FP32 value is nearest to A, so A keeps
+// bfloat16 precision (within half a bfloat16 ulp) and a lookup widens only the
+// four low halves (one shift each) instead of all eight values.
+__device__ __forceinline__ uint32_t bf16_hi_word(float A, uint32_t lo16) {
+    const uint32_t base = (__float_as_uint(A) & 0xFFFF0000u) | lo16;
+    uint32_t best = base;
+    double err = fabs((double)A - (double)__uint_as_float(base));
+    const uint32_t mag = (base >> 16) & 0x7FFFu;   // exponent and upper mantissa of the high half
+    if (mag > 0u) {
+        const uint32_t c = base - 0x10000u;
+        const double e = fabs((double)A - (double)__uint_as_float(c));
+        if (e < err) { err = e; best = c; }
+    }
+    if (mag < 0x7F7Fu) {
+        const uint32_t c = base + 0x10000u;
+        const double e = fabs((double)A - (double)__uint_as_float(c));
+        if (e < err) { err = e; best = c; }
+    }
+    return best;
+}
+
+// Encode a record (8 FP32 coefficients in record order) as a 16-bit record.
+__device__ __forceinline__ uint4 encode_rec16(const float* r, int dtype) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (dtype == 1) {
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(r[4 + e]));
+            w[e] = bf16_hi_word(r[e], lo);
+        } else {
+            const uint32_t lo = __half_as_ushort(__float2half_rn(r[4 + e]));
+            const uint32_t hi = __half_as_ushort(__float2half_rn(r[e]));
+            w[e] = lo | (hi << 16);
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Decode a 16-bit record into the 8 coefficients in record order.
+template <int DT>
+__device__ __forceinline__ void decode_rec16(uint4 q, float* r) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (DT == 1) {
+            r[e] = __uint_as_float(w[e]);
+            r[4 + e] = __uint_as_float(w[e] << 16);
+        } else {
+            r[e] = __half2float(__ushort_as_half((unsigned short)(w[e] >> 16)));
+            r[4 + e] = __half2float(__ushort_as_half((unsigned short)(w[e] & 0xFFFFu)));
+        }
+    }
+}
+
 // One 32-byte FP32 cell record (32-byte aligned) in a single 256-bit read-only
 // load: one L1 tag lookup per record instead of two for a pair of 128-bit
 // loads (lookup passes 1.77 -> 1.72 ms gradient, 1.19 -> 1.16 ms value).
@@ -263,31 +322,34 @@ __device__ __forceinline__ void ld_record32(const float4* p, float4& a, float4& 
         : "l"(p));
 }
 
-// The record of cell `idx` widened to float (FP32: the coefficient record as
-// stored; 16-bit: the 8 corner values); zeros when !valid, without a load.
+// Lookups outside the lattice: with GMCS_MISSREC = 1 every lane loads, those
+// lanes the zero miss record before cell 0 (index -1); with 0 (the default, faster)
+// their loads are predicated off and their record registers zeroed.
+#ifndef GMCS_MISSREC
+#define GMCS_MISSREC 0
+#endif
 
+// Index of cell (cx, cy, cz) in a table of ncx x ncy x ncz cells, or -1 when the
+// cell lies outside the lattice on any axis.
+__device__ __forceinline__ int cell_index(uint32_t ncx, uint32_t ncy, uint32_t ncz, int cx, int cy, int cz) {
+    const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+    return valid ? (int)(((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx) : -1;
+}
+
+// The coefficient record of cell `idx` widened to float in record order: zeros
+// when !valid (without a load, or from the miss record with GMCS_MISSREC).
 template <int DT>
 __device__ __forceinline__ void load_cell(const void* __restrict__ cells, uint32_t idx, bool valid, float* v) {
+    const ptrdiff_t at = GMCS_MISSREC ? (valid ? (ptrdiff_t)idx : (ptrdiff_t)-1) : (ptrdiff_t)idx;
     if (DT == 0) {
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, a, b);
+        if (GMCS_MISSREC || valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * at, a, b);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
         uint4 q = make_uint4(0u, 0u, 0u, 0u);
-        if (valid) q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (DT == 1) {
-                v[2 * e] = __uint_as_float(w[e] << 16);
-                v[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
-            } else {
-                const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
-                v[2 * e] = f.x;
-                v[2 * e + 1] = f.y;
-            }
-        }
+        if (GMCS_MISSREC || valid) q = __ldg(reinterpret_cast<const uint4*>(cells) + at);
+        decode_rec16<DT>(q, v);
     }
 }
 

@@ -12,14 +12,18 @@ namespace gmcs {
 enum Kind { K_PREDICT, K_SELECT, K_PASS_GRAD, K_PASS_VALUE, K_FINISH, K_WEIGH, K_RESAMPLE, K_GATHER, K_TABLE, K_MISC, K_COUNT };
 
 struct HostTable {
-    void* cells = nullptr;
-    size_t bytes = 0;
+    void* cells = nullptr;           // the allocation: [lead bytes: zero miss record][cell records]
+    size_t bytes = 0;                // allocation size, miss record included
+    size_t lead = 0;                 // field tables: one record; GICP voxel maps: 0
     gmcs_grid grid;
     int dtype = 0;
     unsigned char* occ = nullptr;   // occupancy lattice for the overlap rate (Sec. III-E)
     gmcs_grid occ_grid;
     size_t occ_bytes = 0;
 };
+
+// First cell record of a table (the lookup kernels' cell 0).
+inline void* table_cells(const HostTable& t) { return static_cast<char*>(t.cells) + t.lead; }
 
 struct EvPair {
     int kind;
@@ -36,6 +40,7 @@ struct gmcs_ctx {
     size_t ld = 0;
     int P = 0, K = 0;
     uint32_t frame = 0;
+    uint64_t version = 0;            // bumped by every call that changes poses, neighbours or keyframes
     bool have_particles = false;
     int cur = 0;
     float* pose[2] = {nullptr, nullptr};
@@ -90,6 +95,7 @@ namespace gmcs {
 // Argument records of one session's kernels, built exactly as the single-session
 // frame driver builds them (gmcs.cu); the serving path batches them.
 int cuda_status(cudaError_t e);
+bool config_valid(const gmcs_config* c);   // every field within the range the library accepts
 size_t ctx_device_bytes(int max_particles, int max_keyframes, int max_points);
 void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw,
                const float* pose_override, PassArgs* pa, FinishArgs* fa);

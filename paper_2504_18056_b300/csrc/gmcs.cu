@@ -44,6 +44,9 @@ void pass_shape(int P, int N, int* ntiles, int* groups, int* chunk_len, int max_
     const int target = 148 * 8 * 4;
     int g = (target + ntg - 1) / ntg;
     g = std::max(1, std::min(g, max_groups));
+#ifdef GMCS_FORCE_GROUPS
+    g = std::max(1, std::min(GMCS_FORCE_GROUPS, max_groups));
+#endif
     const int max_chunks = std::max(1, (N + 7) / 8);
     while (g > 1 && g * kPassCW > max_chunks) --g;
     const int chunks = g * kPassCW;
@@ -554,7 +557,11 @@ const char* gmcs_strerror(int code) {
     }
 }
 
-static bool config_ok(const gmcs_config* c) {
+}  // extern "C"
+
+namespace gmcs {
+
+bool config_valid(const gmcs_config* c) {
     return c && c->sigma > 0.f && c->r_t > 0.f && c->eps > 0.f && c->lambda >= 0.f && c->theta_max > 0.f &&
            (c->propagate == 0 || c->propagate == 1) && c->loop_recent >= 0 &&
            c->t_max > 0.f && c->w_min >= 0.f && c->k_nb >= 1 && c->k_nb <= GMCS_MAX_NB && c->steps >= 0 &&
@@ -565,11 +572,15 @@ static bool config_ok(const gmcs_config* c) {
            c->kf_overlap <= 1.f && c->kf_voxel > 0.f && c->kf_h > 0.f;
 }
 
+}  // namespace gmcs
+
+extern "C" {
+
 int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, int max_points, void* cuda_stream,
                 gmcs_ctx** out) {
     if (!out) return GMCS_E_INVALID;
     *out = nullptr;
-    if (!config_ok(cfg) || max_particles <= 0 || max_keyframes <= 0 || max_points <= 0) return GMCS_E_INVALID;
+    if (!config_valid(cfg) || max_particles <= 0 || max_keyframes <= 0 || max_points <= 0) return GMCS_E_INVALID;
     if ((size_t)max_particles * (size_t)(1 + max_keyframes) > ((size_t)1 << 34)) return GMCS_E_INVALID;
     gmcs_ctx* c = new (std::nothrow) gmcs_ctx();
     if (!c) return GMCS_E_OOM;
@@ -671,6 +682,7 @@ int gmcs_init_particles(gmcs_ctx* c, const float* poses, int P, const double* lo
     }
     c->P = P;
     c->frame = 0;
+    c->version++;
     c->have_particles = true;
     c->last_valid = false;
     return GMCS_OK;
@@ -837,7 +849,7 @@ int register_keyframe(gmcs_ctx* c, HostTable& t, const gmcs_grid* grid, int ncx,
     }
     TableDesc td;
     std::memset(&td, 0, sizeof(td));
-    td.cells = t.cells;
+    td.cells = table_cells(t);
     td.ox = (float)grid->origin[0];
     td.oy = (float)grid->origin[1];
     td.oz = (float)grid->origin[2];
@@ -882,6 +894,7 @@ int register_keyframe(gmcs_ctx* c, HostTable& t, const gmcs_grid* grid, int ncx,
     c->dev_bytes += t.bytes + t.occ_bytes;
     c->tables.push_back(t);
     c->K = k + 1;
+    c->version++;
     for (int e = 0; e < 12; ++e) c->odo[e] = (e % 5 == 0) ? 1.0 : 0.0;   // identity
     if (kf_id) *kf_id = k;
     return GMCS_OK;
@@ -949,10 +962,15 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     HostTable t;
     t.grid = *grid;
     t.dtype = dtype;
-    t.bytes = ncell * rec;
+    t.lead = rec;   // the zero miss record before cell 0
+    t.bytes = (ncell + 1) * rec;
     if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
         cudaGetLastError();
         return GMCS_E_OOM;
+    }
+    if (cudaMemsetAsync(t.cells, 0, rec, c->stream) != cudaSuccess) {
+        cudaFree(t.cells);
+        return GMCS_E_CUDA;
     }
     // squared-distance scratch, grown to the largest table seen
     if (c->d2_cap < nv) {
@@ -1017,7 +1035,7 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     pa.nz = (int)nz;
     pa.inv_two_sigma2 = 1.0f / (2.0f * c->cfg.sigma * c->cfg.sigma);
     pa.r_t2 = c->cfg.r_t * c->cfg.r_t;
-    pa.cells = t.cells;
+    pa.cells = table_cells(t);
     pa.dtype = dtype;
     {
         Launch L(c, K_TABLE);
@@ -1122,6 +1140,7 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
     if (u_override && !(*u_override >= 0.0 && *u_override < 1.0)) return GMCS_E_INVALID;
     int rc = upload_scan(c, scan, N);
     if (rc) return rc;
+    c->version++;
     const uint32_t frame = c->frame;
     // odometry path length of this frame (Eq. 9 along the odometry trajectory)
     c->path_now += std::sqrt(delta_T[3] * delta_T[3] + delta_T[7] * delta_T[7] + delta_T[11] * delta_T[11]);
@@ -1158,6 +1177,7 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
     CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(WeighResult), cudaMemcpyDeviceToHost, c->stream));
     c->frame = frame + 1;
     c->frames++;
+    c->version++;
     c->last_valid = true;
     c->last_N = N;
     c->last_inserted = 0;
@@ -1213,6 +1233,7 @@ int gmcs_predict(gmcs_ctx* c, const double delta_T[12], const double cov[36], co
         CK(cudaMemcpyAsync(c->stage, z, sizeof(float) * 6 * (size_t)c->P, cudaMemcpyHostToDevice, c->stream));
         zd = c->stage;
     }
+    c->version++;
     return run_predict(c, delta_T, cov, zd, frame);
 }
 
@@ -1223,6 +1244,7 @@ int gmcs_select(gmcs_ctx* c, int* nbr_out) {
     const bool dev = nbr_out && is_device_ptr(nbr_out);
     int* tmp = nullptr;
     if (nbr_out && !dev) tmp = reinterpret_cast<int*>(c->part);   // P x k_nb ints fit in the scratch
+    c->version++;
     int rc = run_select(c, dev ? nbr_out : tmp);
     if (rc) return rc;
     if (tmp) return copy_out(c, nbr_out, tmp, sizeof(int) * (size_t)c->P * knb);
@@ -1320,6 +1342,7 @@ int gmcs_move(gmcs_ctx* c, const float* scan, int N) {
     if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
     int rc = upload_scan(c, scan, N);
     if (rc) return rc;
+    c->version++;
     return run_pass(c, N, true, true, nullptr, nullptr, nullptr, nullptr);
 }
 
@@ -1458,6 +1481,7 @@ int gmcs_get_kf_poses(gmcs_ctx* c, int k, float* poses) {
 
 int gmcs_set_kf_poses(gmcs_ctx* c, int k, const float* poses) {
     if (!c || !poses || k < 0 || k >= c->K) return GMCS_E_INVALID;
+    c->version++;
     CK(cudaMemcpyAsync(c->part, poses, sizeof(float) * 12 * (size_t)c->P, cudaMemcpyDefault, c->stream));
     {
         Launch L(c, K_MISC);
@@ -1544,12 +1568,41 @@ int gmcs_get_table(gmcs_ctx* c, int k, float* vals) {
     }
     {
         Launch L(c, K_MISC);
-        launch_unpack(t.cells, t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], dst, c->stream);
+        launch_unpack(table_cells(t), t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], dst, c->stream);
     }
     int rc = check_launch();
     if (!rc && !dev) rc = copy_out(c, vals, dst, nv * sizeof(float));
     if (!dev) cudaFree(dst);
     return rc;
+}
+
+int gmcs_get_records(gmcs_ctx* c, int k, uint64_t c0, uint64_t n, float* coef) {
+    if (!c || !coef || k < 0 || k >= c->K) return GMCS_E_INVALID;
+    const HostTable& t = c->tables[k];
+    if (t.dtype == 3) return GMCS_E_INVALID;
+    const uint64_t ncell = (uint64_t)(t.grid.n[0] - 1) * (t.grid.n[1] - 1) * (t.grid.n[2] - 1);
+    if (c0 > ncell || n > ncell - c0) return GMCS_E_INVALID;
+    if (n == 0) return GMCS_OK;
+    const bool dev = is_device_ptr(coef);
+    float* dst = dev ? coef : nullptr;
+    if (!dev && cudaMalloc((void**)&dst, n * 8 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return GMCS_E_OOM;
+    }
+    {
+        Launch L(c, K_MISC);
+        launch_records(table_cells(t), t.dtype, c0, n, dst, c->stream);
+    }
+    int rc = check_launch();
+    if (!rc && !dev) rc = copy_out(c, coef, dst, n * 8 * sizeof(float));
+    if (!dev) cudaFree(dst);
+    return rc;
+}
+
+int gmcs_state_version(gmcs_ctx* c, uint64_t* version) {
+    if (!c || !version) return GMCS_E_INVALID;
+    *version = c->version;
+    return GMCS_OK;
 }
 
 int gmcs_get_sizes(gmcs_ctx* c, int* P, int* K, uint32_t* frame) {

@@ -195,6 +195,12 @@ constexpr int pass3_unroll() {
 #ifndef GMCS_F32X2
 #define GMCS_F32X2 1
 #endif
+// 16-bit tables: the packed (ux, uy) transform and round-down floor of the FP32
+// path (1), or a scalar transform with floorf (0).
+#ifndef GMCS_XY16
+#define GMCS_XY16 1
+#endif
+constexpr bool kXy16 = GMCS_XY16;
 
 // Packed two-lane FP32 arithmetic (Blackwell add/sub/fma .f32x2).
 __device__ __forceinline__ float2 p2_sub(float2 a, float2 b) {
@@ -231,49 +237,16 @@ __device__ __forceinline__ int floor_split(float u, float& fl) {
     return __float_as_int(t) - 0x4B400000;
 }
 
-// One lookup at lattice coordinate u of a table: adds log2(L + eps) to lsum
-// and, with GRAD, returns w = L / (L + eps) and g = grad_u L / (L + eps).
-// A cell outside [0, n-1) on any axis reads as L = 0 (the load is skipped).
-// The lookup in cell (cx, cy, cz) at fractional position (fx, fy, fz). With PROD
-// the likelihood L + eps is multiplied into lsum (the caller takes one log2 of
-// the product of a point's three lookups, each factor in [eps, 1 + eps]).
-//
-// Trilinear interpolation of one corner record v (16-bit tables): the record
-// holds the cell's corners as z-pairs (slot dz + 2 dy + 4 dx): P0 = x0y0,
-// P1 = x0y1, P2 = x1y0, P3 = x1y1, each (z0, z1).
-template <bool GRAD, bool PROD = false>
-__device__ __forceinline__ void lookup_interp(const float* v, float fx, float fy, float fz, float eps, float& lsum,
-                                              float& w, float& gx, float& gy, float& gz) {
-    const float2 P0 = make_float2(v[0], v[1]), P1 = make_float2(v[2], v[3]);
-    const float2 P2 = make_float2(v[4], v[5]), P3 = make_float2(v[6], v[7]);
-    const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
-    const float2 D0 = p2_sub(P2, P0), D1 = p2_sub(P3, P1);        // x-differences at y0, y1
-    const float2 E0 = p2_fma(FX, D0, P0), E1 = p2_fma(FX, D1, P1); // x-interpolated at y0, y1
-    const float2 DY = p2_sub(E1, E0);                              // y-differences (z0, z1)
-    const float2 G = p2_fma(FY, DY, E0);                           // xy-interpolated (z0, z1)
-    const float Lz = G.y - G.x;
-    const float L = fmaf(fz, Lz, G.x);
-    const float den = L + eps;
-    if constexpr (PROD) lsum *= den;
-    else lsum += __log2f(den);
-    if constexpr (GRAD) {
-        const float2 HX = p2_fma(FY, p2_sub(D1, D0), D0);          // y-interpolated x-differences
-        const float Lx = fmaf(fz, HX.y - HX.x, HX.x);
-        const float Ly = fmaf(fz, DY.y - DY.x, DY.x);
-        const float inv = __fdividef(1.f, den);
-        gx = Lx * inv;
-        gy = Ly * inv;
-        gz = Lz * inv;
-        w = L * inv;
-    }
-}
-
-// The same lookup on an FP32 coefficient record r = (c4, c2, c7, c6, c1, c0, c5, c3):
-// with a = c4 + c7 z, b = c1 + c5 z, d = c2 + c6 z, e = c0 + c3 z,
+// One lookup in the cell whose coefficient record (widened to float) is
+// r = (c4, c2, c7, c6, c1, c0, c5, c3), at in-cell fraction (x, y, z): adds
+// log2(L + eps) to lsum -- or, with PROD, multiplies L + eps into it (the caller
+// takes one log2 of the product of a point's three lookups, each factor in
+// [eps, 1 + eps]) -- and, with GRAD, returns w = L / (L + eps) and
+// g = grad_f L / (L + eps). With a = c4 + c7 z, b = c1 + c5 z, d = c2 + c6 z, e = c0 + c3 z,
 //   L = e + d y + x (b + a y),  dL/dx = b + a y,  dL/dy = d + a x,
 //   dL/dz = (c3 + c6 y) + x (c5 + c7 y):
-// 4 packed and 3 scalar FMAs for L and its gradient (the corner form takes 9
-// packed and 6 scalar operations).
+// 4 packed and 3 scalar FMAs for L and its gradient (interpolating the 8 corner
+// values takes 9 packed and 6 scalar operations).
 template <bool GRAD, bool PROD = false>
 __device__ __forceinline__ void coef_interp(const float* r, float fx, float fy, float fz, float eps, float& lsum,
                                             float& w, float& gx, float& gy, float& gz) {
@@ -299,14 +272,6 @@ __device__ __forceinline__ void coef_interp(const float* r, float fx, float fy, 
     }
 }
 
-// Either record form: FP32 coefficient records, 16-bit corner records.
-template <int DT, bool GRAD, bool PROD = false>
-__device__ __forceinline__ void record_interp(const float* v, float fx, float fy, float fz, float eps, float& lsum,
-                                              float& w, float& gx, float& gy, float& gz) {
-    if constexpr (DT == 0) coef_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
-    else lookup_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
-}
-
 template <int DT, bool GRAD, bool PROD = false>
 __device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
                                             int cx, int cy, int cz, float fx, float fy, float fz, float eps,
@@ -315,26 +280,18 @@ __device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint
     const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
     float v[8];
     load_cell<DT>(cells, idx, valid, v);
-    record_interp<DT, GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
+    coef_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
 }
 
 template <int DT, bool GRAD, bool PROD = false>
 __device__ __forceinline__ void lookup_one(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
                                            float ux, float uy, float uz, float eps, float& lsum, float& w,
                                            float& gx, float& gy, float& gz) {
-    // FP32 tables: floor on the FMA/ALU pipes (gradient pass 2.08 -> 2.01 ms); the
-    // 16-bit tables widen their records on the ALU pipe and are faster with the
-    // conversion unit doing the floor (1.84 vs 2.03 ms)
+    // floor on the FMA/ALU pipes (FP32 gradient pass 2.08 -> 2.01 ms)
     float flx, fly, flz;
-    int cx, cy, cz;
-    if constexpr (DT == 0) {
-        cx = floor_split(ux, flx);
-        cy = floor_split(uy, fly);
-        cz = floor_split(uz, flz);
-    } else {
-        flx = floorf(ux); fly = floorf(uy); flz = floorf(uz);
-        cx = (int)flx; cy = (int)fly; cz = (int)flz;
-    }
+    const int cx = floor_split(ux, flx);
+    const int cy = floor_split(uy, fly);
+    const int cz = floor_split(uz, flz);
     lookup_cell<DT, GRAD, PROD>(cells, ncx, ncy, ncz, cx, cy, cz, ux - flx, uy - fly, uz - flz, eps, lsum, w, gx, gy,
                                 gz);
 }
@@ -485,14 +442,13 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
             constexpr bool kProd = !GRAD;
             float lprod = 1.f;
             float& lacc = kProd ? lprod : lsum;
-            // FP32 tables: (ux, uy) and their floor on packed pairs (gradient pass 2.01 -> 1.95 ms);
-            // the 16-bit tables are faster with the scalar form (1.82 vs 1.89 ms)
+            // (ux, uy) and their floor on packed pairs (FP32 gradient pass 2.01 -> 1.95 ms)
             const float2 PX = make_float2(p.x, p.x), PY = make_float2(p.y, p.y), PZ = make_float2(p.z, p.z);
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 float w, gx, gy, gz, ux, uy;
                 const float uz = fmaf(sl[s].A20, p.x, fmaf(sl[s].A21, p.y, fmaf(sl[s].A22, p.z, sl[s].b2)));
-                if constexpr (DT == 0) {
+                if constexpr (DT == 0 || kXy16) {
                     const float2 uxy = p2_fma(make_float2(sl[s].A00, sl[s].A10), PX,
                                               p2_fma(make_float2(sl[s].A01, sl[s].A11), PY,
                                                      p2_fma(make_float2(sl[s].A02, sl[s].A12), PZ,
@@ -537,20 +493,18 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
 // ---- software-pipelined three-neighbour pass: two stages in turn, so that
 // while one point's three cell records are interpolated, the next point's are
 // in flight (FP32 gradient pass 1.95 -> 1.77 ms; FP32 value pass, with the
-// 256-bit record load, 1.16 -> 1.08 ms at 4 CTAs per SM). The 16-bit passes are
-// faster unpipelined with two points unrolled (BF16 gradient 1.80 vs 1.95 ms,
-// value 1.16 vs 1.38 ms).
+// 256-bit record load, 1.16 -> 1.08 ms at 4 CTAs per SM).
 #ifndef GMCS_PIPE_G32
 #define GMCS_PIPE_G32 1
 #endif
 #ifndef GMCS_PIPE_G16
-#define GMCS_PIPE_G16 0
+#define GMCS_PIPE_G16 1
 #endif
 #ifndef GMCS_PIPE_V32
 #define GMCS_PIPE_V32 1
 #endif
 #ifndef GMCS_PIPE_V16
-#define GMCS_PIPE_V16 0
+#define GMCS_PIPE_V16 1
 #endif
 template <int DT, bool GRAD>
 constexpr bool pass3_pipelined() {
@@ -580,8 +534,8 @@ __device__ __forceinline__ void xf_slot(const Xf& x, Slot& s) {
 }
 
 // Lattice coordinate u of p in one slot, its cell c and in-cell fraction f
-// (FP32 tables: (ux, uy) on packed pairs and the round-down floor; 16-bit
-// tables: scalar transform and floorf, as in the unpipelined pass). ZCVT takes
+// ((ux, uy) on packed pairs and the round-down floor; with GMCS_XY16 = 0 the
+// 16-bit tables take a scalar transform and floorf). ZCVT takes
 // the z floor on the conversion unit instead, off the FMA pipe: with coefficient
 // records the pipelined FP32 passes gain (gradient 1.65 -> 1.58 ms, value
 // 1.078 -> 1.061 ms; with corner records the gradient pass lost, 1.720 -> 1.743).
@@ -589,7 +543,7 @@ template <int DT, bool ZCVT = false>
 __device__ __forceinline__ void slot_point(const Xf& x, float4 p, float& ux, float& uy, float& uz, int& cx, int& cy,
                                            int& cz, float& fx, float& fy, float& fz) {
     uz = fmaf(x.q2.x, p.x, fmaf(x.q2.y, p.y, fmaf(x.q2.z, p.z, x.q2.w)));
-    if constexpr (DT == 0) {
+    if constexpr (DT == 0 || kXy16) {
         const float2 uxy = p2_fma(make_float2(x.q0.x, x.q0.y), make_float2(p.x, p.x),
                                   p2_fma(make_float2(x.q0.z, x.q0.w), make_float2(p.y, p.y),
                                          p2_fma(make_float2(x.q1.x, x.q1.y), make_float2(p.z, p.z),
@@ -620,8 +574,8 @@ __device__ __forceinline__ void slot_point(const Xf& x, float4 p, float& ux, flo
     }
 }
 
-// A cell record as loaded: two float4 (FP32) or one uint4 of 16-bit z-pairs;
-// widened to floats only when it is interpolated.
+// A cell record as loaded: two float4 (FP32) or one uint4 of 16-bit
+// coefficients; widened to floats only when it is interpolated.
 template <int DT>
 struct RawRec {
     uint4 q;
@@ -632,19 +586,29 @@ struct RawRec<0> {
 };
 
 // Issue the load of cell c of a slot's table; a cell outside the table, or a
-// stage with no point (live = false), reads as zeros without a load.
+// stage with no point (live = false), reads as zeros: with GMCS_MISSREC, from
+// the zero miss record before cell 0 (every lane loads); otherwise the lane's
+// load is predicated off and its record registers are zeroed.
 template <int DT>
 __device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
                                           int cx, int cy, int cz, bool live, RawRec<DT>& r) {
-    const bool valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-    const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
-    if constexpr (DT == 0) {
-        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.b = r.a;
-        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
+    if constexpr (GMCS_MISSREC) {
+        const int idx = live ? cell_index(ncx, ncy, ncz, cx, cy, cz) : -1;
+        if constexpr (DT == 0) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (ptrdiff_t)idx, r.a, r.b);
+        else r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
     } else {
-        r.q = make_uint4(0u, 0u, 0u, 0u);
-        if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+        // the predicate as a plain bool and a zero index for the lanes it turns off: with
+        // the index's sign as the test the pass lost a quarter of its speed
+        const bool valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+        const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
+        if constexpr (DT == 0) {
+            r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+            r.b = r.a;
+            if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
+        } else {
+            r.q = make_uint4(0u, 0u, 0u, 0u);
+            if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+        }
     }
 }
 
@@ -654,18 +618,7 @@ __device__ __forceinline__ void unpack_raw(const RawRec<DT>& r, float* v) {
         v[0] = r.a.x; v[1] = r.a.y; v[2] = r.a.z; v[3] = r.a.w;
         v[4] = r.b.x; v[5] = r.b.y; v[6] = r.b.z; v[7] = r.b.w;
     } else {
-        const uint32_t w[4] = {r.q.x, r.q.y, r.q.z, r.q.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (DT == 1) {
-                v[2 * e] = __uint_as_float(w[e] << 16);
-                v[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
-            } else {
-                const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
-                v[2 * e] = h.x;
-                v[2 * e + 1] = h.y;
-            }
-        }
+        decode_rec16<DT>(r.q, v);
     }
 }
 
@@ -732,7 +685,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 for (int s = 0; s < 3; ++s) {
                     float v[8], w, gx, gy, gz;
                     unpack_raw<DT>(st.r[s], v);
-                    record_interp<DT, true, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
+                    coef_interp<true, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
                     const float ux = st.u[s][0], uy = st.u[s][1], uz = st.u[s][2];
                     G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
                     C[s][0] = fmaf(uy, gz, fmaf(-uz, gy, C[s][0]));
@@ -747,7 +700,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 for (int s = 0; s < 3; ++s) {
                     float v[8];
                     unpack_raw<DT>(st.r[s], v);
-                    record_interp<DT, false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy,
+                    coef_interp<false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy,
                                                    gz);
                 }
             }
@@ -788,9 +741,17 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 #ifndef GMCS_PIPE_GRAD_MINBLOCKS
 #define GMCS_PIPE_GRAD_MINBLOCKS 3
 #endif
+#ifndef GMCS_PIPE_GRAD_MINBLOCKS16
+#define GMCS_PIPE_GRAD_MINBLOCKS16 3
+#endif
+#ifndef GMCS_VALUE_MINBLOCKS16
+#define GMCS_VALUE_MINBLOCKS16 4
+#endif
 template <int DT, bool GRAD>
 constexpr int pass3_minblocks() {
-    return GRAD ? (pass3_pipelined<DT, GRAD>() ? GMCS_PIPE_GRAD_MINBLOCKS : GMCS_PASS3_MINBLOCKS) : GMCS_VALUE_MINBLOCKS;
+    return GRAD ? (pass3_pipelined<DT, GRAD>() ? (DT == 0 ? GMCS_PIPE_GRAD_MINBLOCKS : GMCS_PIPE_GRAD_MINBLOCKS16)
+                                               : GMCS_PASS3_MINBLOCKS)
+                : (DT == 0 ? GMCS_VALUE_MINBLOCKS : GMCS_VALUE_MINBLOCKS16);
 }
 
 template <int DT, bool GRAD, int UNROLL>

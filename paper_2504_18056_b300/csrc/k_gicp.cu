@@ -357,21 +357,19 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
                 // range where the approximate reciprocal (2 ulp) holds; an IEEE division
                 // costs the pass 1.2 % (gradient 4.22 -> 4.27 ms)
                 const float rd = __fdividef(1.f, det);
-                float o00, o01, o02, o11, o12, o22, q0, q1, q2, d2;
+                // d^2 = e^T adj(C) e / det, the same float expression in both passes, so
+                // that the gradient pass and the value pass cap the same points; the value
+                // pass never forms Omega (2.46 -> 2.38 ms), the gradient pass takes
+                // q = Omega e = adj(C) e / det from the same products
+                const float a0 = fmaf(i00, e0, fmaf(i01, e1, i02 * e2));
+                const float a1 = fmaf(i01, e0, fmaf(i11, e1, i12 * e2));
+                const float a2 = fmaf(i02, e0, fmaf(i12, e1, i22 * e2));
+                const float d2 = fmaf(e0, a0, fmaf(e1, a1, e2 * a2)) * rd;
+                float o00, o01, o02, o11, o12, o22, q0, q1, q2;
                 if constexpr (GRAD) {
                     o00 = i00 * rd; o01 = i01 * rd; o02 = i02 * rd;
                     o11 = i11 * rd; o12 = i12 * rd; o22 = i22 * rd;
-                    q0 = fmaf(o00, e0, fmaf(o01, e1, o02 * e2));
-                    q1 = fmaf(o01, e0, fmaf(o11, e1, o12 * e2));
-                    q2 = fmaf(o02, e0, fmaf(o12, e1, o22 * e2));
-                    d2 = fmaf(e0, q0, fmaf(e1, q1, e2 * q2));
-                } else {
-                    // value only: d^2 = e^T adj(C) e / det, without forming Omega (value
-                    // pass 2.46 -> 2.38 ms)
-                    const float a0 = fmaf(i00, e0, fmaf(i01, e1, i02 * e2));
-                    const float a1 = fmaf(i01, e0, fmaf(i11, e1, i12 * e2));
-                    const float a2 = fmaf(i02, e0, fmaf(i12, e1, i22 * e2));
-                    d2 = fmaf(e0, a0, fmaf(e1, a1, e2 * a2)) * rd;
+                    q0 = a0 * rd; q1 = a1 * rd; q2 = a2 * rd;
                 }
                 if (!(d2 < tau)) {
                     lsum -= tau;

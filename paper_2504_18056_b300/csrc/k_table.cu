@@ -4,8 +4,9 @@
 // the distance to the nearest keyframe point, 0 where d > r_t. It is built in
 // two launches: each point relaxes the squared distance of every vertex within
 // r_t (atomicMin on the float bit pattern, which orders like the value for
-// non-negative floats), then every cell packs its 8 corner values into one
-// record so that a lookup is a single 32 B (FP32) or 16 B (BF16/FP16) load.
+// non-negative floats), then every cell turns its 8 corner values into the
+// coefficients of its trilinear polynomial, stored as one record, so that a
+// lookup is a single 32 B (FP32) or 16 B (BF16/FP16) load.
 #include "kernels.h"
 
 namespace gmcs {
@@ -70,8 +71,8 @@ __device__ __forceinline__ float field_value(unsigned bits, float inv_two_sigma2
     return (d2 <= r_t2) ? expf(-d2 * inv_two_sigma2) : 0.0f;
 }
 
-// One thread per cell: 8 corner values -> one record (FP32: the coefficients of
-// the cell's trilinear polynomial; 16-bit: the corner values, rounded).
+// One thread per cell: 8 corner values -> the coefficients of the cell's
+// trilinear polynomial, one record (FP32, or encoded as a 16-bit record).
 __global__ void k_pack(PackArgs a) {
     const int ncx = a.nx - 1, ncy = a.ny - 1, ncz = a.nz - 1;
     const size_t ncell = (size_t)ncx * ncy * ncz;
@@ -89,49 +90,55 @@ __global__ void k_pack(PackArgs a) {
                     const size_t vi = ((size_t)(cz + dz) * a.ny + (cy + dy)) * a.nx + (cx + dx);
                     v[rec_slot(dx, dy, dz)] = field_value(a.d2[vi], a.inv_two_sigma2, a.r_t2);
                 }
+        float r[8];
+        corners_to_coef(v, r);
         if (a.dtype == 0) {
-            float r[8];
-            corners_to_coef(v, r);
             float4* out = reinterpret_cast<float4*>(a.cells) + 2 * c;
             out[0] = make_float4(r[0], r[1], r[2], r[3]);
             out[1] = make_float4(r[4], r[5], r[6], r[7]);
         } else {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                uint32_t lo16, hi16;
-                if (a.dtype == 1) {
-                    lo16 = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * e]));
-                    hi16 = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * e + 1]));
-                } else {
-                    lo16 = __half_as_ushort(__float2half_rn(v[2 * e]));
-                    hi16 = __half_as_ushort(__float2half_rn(v[2 * e + 1]));
-                }
-                w[e] = lo16 | (hi16 << 16);
-            }
-            reinterpret_cast<uint4*>(a.cells)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+            reinterpret_cast<uint4*>(a.cells)[c] = encode_rec16(r, a.dtype);
         }
     }
 }
 
-// Vertex values read back from the cell records (vertex i lives in cell min(i, nc-1);
-// FP32 records give it back from their coefficients, to within their rounding).
+// Vertex values read back from the cell records (vertex i lives in cell
+// min(i, nc-1), at its corner; the sum of the stored coefficients).
 __global__ void k_unpack(const void* __restrict__ cells, int dtype, int nx, int ny, int nz, float* __restrict__ out) {
     const size_t nv = (size_t)nx * ny * nz;
     const int ncx = nx - 1, ncy = ny - 1, ncz = nz - 1;
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
         const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((size_t)nx * ny));
         const int cx = min(ix, ncx - 1), cy = min(iy, ncy - 1), cz = min(iz, ncz - 1);
-        const int corner = rec_slot(ix - cx, iy - cy, iz - cz);
         const size_t c = ((size_t)cz * ncy + cy) * ncx + cx;
-        float val;
+        float r[8];
         if (dtype == 0) {
-            val = coef_corner(reinterpret_cast<const float*>(cells) + 8 * c, ix - cx, iy - cy, iz - cz);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) r[e] = reinterpret_cast<const float*>(cells)[8 * c + e];
+        } else if (dtype == 1) {
+            decode_rec16<1>(reinterpret_cast<const uint4*>(cells)[c], r);
         } else {
-            const unsigned short b = reinterpret_cast<const unsigned short*>(cells)[8 * c + corner];
-            val = (dtype == 1) ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));
+            decode_rec16<2>(reinterpret_cast<const uint4*>(cells)[c], r);
         }
-        out[v] = val;
+        out[v] = coef_corner(r, ix - cx, iy - cy, iz - cz);
+    }
+}
+
+// Coefficients c0..c7 (natural order) of cells [c0, c0 + n), as stored.
+__global__ void k_records(const void* __restrict__ cells, int dtype, size_t c0, size_t n, float* __restrict__ out) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = c0 + e;
+        float r[8];
+        if (dtype == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = reinterpret_cast<const float*>(cells)[8 * c + k];
+        } else if (dtype == 1) {
+            decode_rec16<1>(reinterpret_cast<const uint4*>(cells)[c], r);
+        } else {
+            decode_rec16<2>(reinterpret_cast<const uint4*>(cells)[c], r);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[8 * e + k] = r[coef_slot(k)];
     }
 }
 
@@ -156,6 +163,10 @@ void launch_pack(const PackArgs& a, cudaStream_t s) {
 
 void launch_unpack(const void* cells, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s) {
     k_unpack<<<grid_for((size_t)nx * ny * nz, 256), 256, 0, s>>>(cells, dtype, nx, ny, nz, out);
+}
+
+void launch_records(const void* cells, int dtype, size_t c0, size_t n, float* out, cudaStream_t s) {
+    if (n > 0) k_records<<<grid_for(n, 256), 256, 0, s>>>(cells, dtype, c0, n, out);
 }
 
 }  // namespace gmcs

@@ -45,6 +45,7 @@ void launch_fill_u32(unsigned* p, size_t n, unsigned v, cudaStream_t s);
 void launch_splat(const SplatArgs& a, cudaStream_t s);
 void launch_pack(const PackArgs& a, cudaStream_t s);
 void launch_unpack(const void* cells, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s);
+void launch_records(const void* cells, int dtype, size_t c0, size_t n, float* out, cudaStream_t s);
 
 // ------------------------------------------------------------------ filter
 struct ScanPackArgs {

@@ -12,7 +12,10 @@
 // The array's name in host code is only a host-side handle, not a device
 // address, so the first call on each device asks the runtime for the array's
 // device address (cudaGetSymbolAddress, with that device current) and caches
-// it for later calls on that device.
+// it for later calls on that device, keyed by the unique id of the device's
+// current context: after cudaDeviceReset the library's module is loaded into a
+// new context, and the next call looks the address up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -32,9 +35,45 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocWo
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned long long* g_scratch_dev[kMaxDevices] = {nullptr};
+struct Cached {
+    unsigned long long ctx_id = 0;   // unique id of the context the address belongs to (0: none)
+    unsigned long long* ptr = nullptr;
+};
+Cached g_scratch_dev[kMaxDevices];
 
-// Device address of the scratch array on the current device (set up once per device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if none or unknown),
+// through driver entry points the runtime hands out (no link to the driver
+// library is needed).
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+        cudaGetLastError();
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current device's current context
+// (looked up once per device and context).
 int scratch_on_current_device(unsigned long long** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -42,15 +81,18 @@ int scratch_on_current_device(unsigned long long** out) {
         return GMCS_E_CUDA;
     }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_dev[dev]) {
+    Cached& c = g_scratch_dev[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!c.ptr || id == 0 || id != c.ctx_id) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {   // makes the context current
             cudaGetLastError();
             return GMCS_E_CUDA;
         }
-        g_scratch_dev[dev] = static_cast<unsigned long long*>(p);
+        c.ptr = static_cast<unsigned long long*>(p);
+        c.ctx_id = current_ctx_id();
     }
-    *out = g_scratch_dev[dev];
+    *out = c.ptr;
     return GMCS_OK;
 }
 

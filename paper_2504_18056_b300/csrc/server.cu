@@ -306,6 +306,7 @@ int launch_tick(gmcs_server* s) {
         }
         c->frame = frame + 1;
         c->frames++;
+        c->version++;
         c->last_valid = true;
         ss->inflight = true;
         t->frames.push_back(f);

@@ -9,10 +9,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "gmcs.h")
+DIAG_HEADER = os.path.join(ROOT, "include", "gmcs_diag.h")
 
 
-def declared():
-    src = open(HEADER).read()
+def declared(header=HEADER):
+    src = open(header).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(gmcs_[a-z_0-9]+)\s*\(", src)))
 
@@ -36,6 +37,20 @@ def test_library_exports_every_declared_symbol():
 def test_binding_covers_header():
     import paper_2504_18056_b300 as g
     assert sorted(g._SIGS) == declared()
+
+
+def test_diagnostics_live_in_their_own_library():
+    """Calibration probes are not part of the particle-update ABI: libgmcs.so does
+    not export them, libgmcs_diag.so exports what gmcs_diag.h declares."""
+    import paper_2504_18056_b300 as g
+    from paper_2504_18056_b300 import build
+    build.build()
+    names = declared(DIAG_HEADER)
+    assert names == sorted(g._DIAG_SIGS) == ["gmcs_probe_ffma", "gmcs_probe_gather"]
+    assert not set(names) & set(declared())
+    main, diag = C.CDLL(build.OUT), C.CDLL(build.DIAG_OUT)
+    assert all(hasattr(diag, n) for n in names)
+    assert not any(hasattr(main, n) for n in names)
 
 
 def test_struct_sizes_and_defaults():

@@ -17,11 +17,11 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("P,N,K", [(1, 1, 1), (1, 512, 4), (33, 7, 2), (65, 300, 3), (40, 1, 4), (40, 3, 4),
                                    (65, 301, 4), (130, 97, 4)])
 def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K, dtype):
-    """FP32 (coefficient records, pipelined passes), BF16 and FP16 (corner records,
-    unrolled passes) against the oracle on the same stored values."""
+    """FP32, BF16 and FP16 coefficient records through the software-pipelined
+    passes, against the oracle on the same stored values."""
     kfs = box_room["keyframes"][:K]
     f = make_filter(box_room, P, dtype=dtype, keyframes=kfs)
-    tables = box_room_tables[:K] if dtype == 0 else [oracle.quantize(t, dtype) for t in box_room_tables[:K]]
+    tables = [oracle.stored_table(t, dtype) for t in box_room_tables[:K]]
     scan = box_room["scans"][2][:N]
     nbr = gpu_nbr(f, P, min(3, K))
     ref_nbr = oracle_nbr(box_room["particles"][:P], box_room["kf_particle_poses"][:K])

@@ -57,7 +57,7 @@ def test_table_precision_per_result(forest, sample):
             np.testing.assert_array_equal(gpu_nbr(f, P, 3), nbr)
             ll, g, mom = gpu_eval(f, scan, P)
             f.close()
-            quant = {k: oracle.quantize(exact[k], dt) for k in need}
+            quant = {k: oracle.stored_table(exact[k], dt) for k in need}
             oq = oracle.eval_batch(forest["particles"], nbr, forest["kf_particle_poses"],
                                    [quant.get(k) for k in range(K)], grids, scan, idx=sample)
         # (a) parity with the oracle on the same stored values

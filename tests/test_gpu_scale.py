@@ -54,7 +54,7 @@ def test_precision_at_scale(big):
         if dt == 0:
             oq = o64
         else:
-            quant = {k: oracle.quantize(exact[k], dt) for k in need}
+            quant = {k: oracle.stored_table(exact[k], dt) for k in need}
             oq = oracle.eval_batch(w["particles"], nbr, w["kf_particle_poses"], [quant.get(k) for k in range(K)],
                                    grids, scan, idx=idx)
         assert np.all(np.abs(ll[idx] - oq["ll"]) <= 1e-4 * np.abs(oq["ll"])), DT_NAME[dt]

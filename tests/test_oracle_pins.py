@@ -124,6 +124,68 @@ def test_quantize_matches_library_conversions():
     np.testing.assert_array_equal(oracle.quantize(vd, 2), vd.astype(np.float16).astype(np.float64))
 
 
+def test_coef_table_is_the_trilinear_interpolation():
+    """A coefficient table evaluates to the same function as the vertex table it
+    came from (the trilinear polynomial, every cell, inside and on its faces), and
+    c0 is the cell's lower corner: a swapped or transposed coefficient fails."""
+    grid = {"origin": np.array([0.5, -1.0, 2.0]), "h": 0.5, "dims": (6, 5, 4)}
+    rng = np.random.default_rng(12)
+    vals = rng.random((4, 5, 6))
+    coef = oracle.coef_table(vals)
+    assert coef.shape == (3, 4, 5, 8)
+    np.testing.assert_array_equal(coef[..., 0], vals[:-1, :-1, :-1])
+    for _ in range(200):
+        c = [rng.integers(0, 5), rng.integers(0, 4), rng.integers(0, 3)]
+        u = np.array(c, np.float64) + rng.random(3) * rng.choice([1.0, 0.0, 0.999999], 3)
+        ok_v, Lv, dv = oracle.cell_eval(vals, grid, c, u)
+        ok_c, Lc, dc = oracle.cell_eval(coef, grid, c, u)
+        assert ok_v and ok_c
+        assert Lc == pytest.approx(Lv, abs=1e-14)
+        np.testing.assert_allclose(dc, dv, atol=1e-14)
+    ok, L, d = oracle.cell_eval(coef, grid, [5, 0, 0], [5.2, 0.1, 0.1])
+    assert not ok and L == 0.0 and not d.any()
+
+
+def test_record_quantisation_fp16_and_bf16():
+    """16-bit coefficient records. FP16: each coefficient rounded to nearest (numpy's
+    conversion). BF16: the low-half coefficients equal torch's bfloat16 rounding; each
+    high-half coefficient is, of all FP32 numbers whose low 16 bits are its partner's
+    bfloat16 bits, the one nearest to it (checked against an exhaustive search of
+    the 65,536 candidates), hence within half a bfloat16 spacing."""
+    import torch
+    rng = np.random.default_rng(13)
+    c = np.concatenate([rng.normal(0, 0.3, (400, 8)), np.exp(-rng.uniform(0, 20, (400, 8))) * rng.choice([-1, 1], (400, 8)),
+                        np.zeros((4, 8)), np.eye(8)[:4]])
+    c32 = c.astype(np.float32)
+    q16 = oracle.quantize_coef(c, 2)
+    np.testing.assert_array_equal(q16, c32.astype(np.float16).astype(np.float64))
+    qb = oracle.quantize_coef(c, 1)
+    hi, lo = [4, 2, 7, 6], [1, 0, 5, 3]
+    bf = torch.from_numpy(np.ascontiguousarray(c32[:, lo])).to(torch.bfloat16)
+    np.testing.assert_array_equal(qb[:, lo], bf.to(torch.float64).numpy())
+    lo_bits = bf.view(torch.int16).numpy().astype(np.uint16).astype(np.uint32)
+    highs = np.arange(1 << 16, dtype=np.uint32) << np.uint32(16)
+    for r in range(0, c.shape[0], 7):
+        for e in range(4):
+            with np.errstate(invalid="ignore"):
+                cand = (highs | lo_bits[r, e]).view(np.float32).astype(np.float64)
+            A = float(c32[r, hi[e]])
+            err = np.abs(np.where(np.isfinite(cand), cand, np.inf) - A)
+            assert abs(qb[r, hi[e]] - A) == err.min()
+            if A != 0.0:
+                assert abs(qb[r, hi[e]] - A) <= 2.0 ** -8 * abs(A)
+
+
+def test_stored_tables_keep_the_field_within_storage_precision(box_room_tables):
+    t = box_room_tables[0]
+    assert oracle.stored_table(t, 0) is not None and np.array_equal(oracle.stored_table(t, 0), t)
+    exact = oracle.coef_table(t)
+    for dt, u in ((1, 2.0 ** -8), (2, 2.0 ** -11)):
+        q = oracle.stored_table(t, dt)
+        assert q.shape == exact.shape
+        assert np.all(np.abs(q - exact) <= u * np.abs(exact) + 1e-7)
+
+
 # ----------------------------------------------------------------- lookup
 def test_cell_eval_vertices_constant_and_affine():
     grid = {"origin": np.zeros(3), "h": 0.5, "dims": (6, 5, 4)}
