@@ -34,11 +34,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle×point lik+grad evals/s; frame update ms @100k particles; p50/p99"
 UNIT = "evals/s"
-# FP32 flops of one gradient lookup (FMA = 2): transform 18, floor and fraction 6, value
-# from the trilinear coefficients 14 and its gradient 8 (16-bit tables, corner values: 21
-# and 12), L + eps, log and reciprocal 3, normalised gradient and weight 4, accumulation 16,
-# moments 7 (19 per point, shared by its 3 lookups)
-FLOPS_GRAD_LOOKUP = {"f32": 76, "bf16": 87, "f16": 87}
+# FP32 flops of one gradient lookup of a move (FMA = 2): transform 18, floor and
+# fraction 6, value from the trilinear coefficients 14 and its gradient 8, L + eps and
+# the reciprocal 2, normalised gradient and weight 4, accumulation 16, moments 19 per
+# point shared by its 3 lookups; the moves do not need the log-likelihood. Every
+# table type stores coefficients (16-bit records are widened, which is no flop).
+FLOPS_GRAD_LOOKUP = {"f32": 74, "bf16": 74, "f16": 74}
 # GICP model: FP32 flops (FMA = 2) of an inlier lookup with the Gauss-Newton terms in
 # the keyframe-frame form the kernel uses, and of a lookup that stops at an empty voxel
 # (transform and cell only); lookups rejected by the cap are counted as the latter
@@ -107,6 +108,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-at-a-time plain FP32 comparison")
     ap.add_argument("--serve-dtype", default="bf16", choices=["f32", "bf16", "f16"],
                     help="table storage of the served sessions")
+    ap.add_argument("--tick-work", type=float, default=None,
+                    help="server cap on the evals a tick gathers (default: the library's; 0 lifts it)")
     return ap.parse_args()
 
 
@@ -407,8 +410,7 @@ def run_native(a, world, rank, local):
     lookups_per_launch = float(P) * N * 3
     rec_bytes = 32 if dtype == 0 else 16
     avg_ms = pg["ms"] / max(pg["launches"], 1)
-    # algorithmic work of one gradient lookup: 76 (FP32 tables) / 87 (16-bit) FP32 flops
-    # (FMA = 2), one cell record read;
+    # algorithmic work of one gradient lookup: 74 FP32 flops (FMA = 2), one cell record read;
     # GICP: 198 per inlier, 24 per other lookup, 48 B voxel record per lookup
     if gicp:
         flops_per_launch = lookups_per_launch * (inlier_frac * FLOPS_GICP_INLIER + (1 - inlier_frac) * FLOPS_GICP_MISS)
@@ -544,6 +546,9 @@ def run_serve(a):
     rec = 32 if sdt == 0 else 16        # bytes per cell record
     srv = g.Server(budget_bytes=int(a.budget_gb * (1 << 30)), max_sessions=a.sessions, background=True,
                    table_dtype=sdt)
+    if a.tick_work is not None:
+        srv.set_tick_work(a.tick_work)
+    lat_by_work = []                    # (P x N of the session, server latency of one frame)
     waiting = list(range(len(specs)))
     active = {}
     e2e_lat = []
@@ -581,6 +586,7 @@ def run_serve(a):
                 if r is None:
                     break
                 e2e_lat.append(st["late"][st["done"]] + r[1])
+                lat_by_work.append((spec["P"] * spec["N"], r[1]))
                 st["done"] += 1
             if st["done"] == len(spec["arrivals"]):
                 srv.close_session(sid)
@@ -631,6 +637,18 @@ def run_serve(a):
             plain_by_session.append((spec, dt))
         f.close()
     served_rate = stats["evals"] / stats["span_s"] if stats["span_s"] > 0 else 0.0
+    # latency by session size: frames of the smallest and the largest quarter of the
+    # sessions (by particles x points), to show how much a small frame waits for large ones
+    works = np.array(sorted({sp["P"] * sp["N"] for sp in specs}))
+    q1, q3 = np.percentile(works, 25), np.percentile(works, 75)
+    small = np.array([l for wk, l in lat_by_work if wk <= q1]) * 1e3
+    large = np.array([l for wk, l in lat_by_work if wk >= q3]) * 1e3
+    by_size = {"small_quarter": {"p50": float(np.percentile(small, 50)), "p99": float(np.percentile(small, 99)),
+                                 "frames": int(small.size), "max_particles_x_points": float(q1)} if small.size else None,
+               "large_quarter": {"p50": float(np.percentile(large, 50)), "p99": float(np.percentile(large, 99)),
+                                 "frames": int(large.size), "min_particles_x_points": float(q3)} if large.size else None}
+    if small.size and large.size:
+        by_size["small_over_large_p50"] = by_size["small_quarter"]["p50"] / by_size["large_quarter"]["p50"]
     sat_ids = {sp["seed"] for _, sp in sat_sids}
     sat_plain = [(spec, t) for spec, t in plain_by_session if spec["seed"] in sat_ids]
     sat_plain_rate = (sum(sp["P"] * sp["N"] * 3 for sp, _ in sat_plain) / sum(t for _, t in sat_plain)
@@ -645,6 +663,7 @@ def run_serve(a):
         "latency_ms": {"p50": stats["latency_p50_s"] * 1e3, "p99": stats["latency_p99_s"] * 1e3,
                        "max": stats["latency_max_s"] * 1e3, "mean": stats["latency_mean_s"] * 1e3,
                        "measured": "submission to completion (server clock)"},
+        "latency_by_session_size_ms": by_size, "tick_work_cap": a.tick_work,
         "latency_from_arrival_ms": {"p50": float(np.percentile(e2e_lat, 50)) * 1e3,
                                     "p99": float(np.percentile(e2e_lat, 99)) * 1e3,
                                     "measured": "scheduled Poisson arrival to completion"},

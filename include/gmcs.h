@@ -179,8 +179,7 @@ int gmcs_init_particles(gmcs_ctx* ctx, const float* poses, int P, const double* 
  * four 32-bit words, each holding one coefficient as a bfloat16 value (rounded
  * to nearest) in its low half and another as the word itself read as an FP32
  * number (the word with that low half nearest to the coefficient: within half a
- * bfloat16 ulp). gmcs_get_records returns the stored values. A zero record
- * before the first cell stands for every cell outside the lattice.
+ * bfloat16 ulp). gmcs_get_records returns the stored values.
  * GICP model: grid is the voxel lattice (n = voxels per axis, voxel (ix,iy,iz)
  * covering origin + h [ix, ix+1) x ...); the library computes every point's
  * plane-regularised covariance from its cfg.knn nearest keyframe points (FP64)
@@ -386,8 +385,8 @@ int gmcs_overlap(gmcs_ctx* ctx, const float* scan, int N, const double T_rel[12]
  * restore (device error, out of memory), the context is left empty -- no
  * particles, no keyframes -- and can be loaded into again.
  * Errors: GMCS_E_IO (file unreadable, not a checkpoint, inconsistent, or written
- * by another format version: version 3 stores every field table as coefficient
- * records after a zero miss record), GMCS_E_STATE (save without particles, load
+ * by another format version: version 3 stores 16-bit field tables as coefficient
+ * records), GMCS_E_STATE (save without particles, load
  * into a context with keyframes), GMCS_E_CAPACITY (nothing restored), GMCS_E_OOM.
  */
 int gmcs_save(gmcs_ctx* ctx, const char* path);
@@ -496,6 +495,13 @@ int gmcs_server_pump(gmcs_server* srv);
 /* Ticks allowed on the GPU at once: 2 (default; a tick starts while another runs)
  * or 1 (one after another). */
 int gmcs_server_set_inflight(gmcs_server* srv, int ticks);
+/* Work cap of a tick, in evaluations (particles x points x cfg.steps): a tick
+ * takes the oldest pending frame, then further frames, oldest first, only while
+ * its total stays within max_evals, so that a frame is not held until a much
+ * larger one in the same tick finishes; the rest go to the next tick, which runs
+ * beside it. 0 lifts the cap (every ready session joins the tick). Default 4e8
+ * (about 4 ms of lookups). Errors: GMCS_E_INVALID. */
+int gmcs_server_set_tick_work(gmcs_server* srv, double max_evals);
 /* Admission: open a session if its context (capacities) plus table_bytes fit the
  * remaining budget, else GMCS_E_BUDGET (retry after another session closes).
  * Then fill it through its context (gmcs_server_context: gmcs_init_particles,

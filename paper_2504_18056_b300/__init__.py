@@ -125,6 +125,7 @@ _SIGS = {
     "gmcs_server_stop": (C.c_int, [C.c_void_p]),
     "gmcs_server_pump": (C.c_int, [C.c_void_p]),
     "gmcs_server_set_inflight": (C.c_int, [C.c_void_p, C.c_int]),
+    "gmcs_server_set_tick_work": (C.c_int, [C.c_void_p, C.c_double]),
     "gmcs_server_open": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_int)]),
     "gmcs_server_context": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "gmcs_server_ready": (C.c_int, [C.c_void_p, C.c_int]),
@@ -511,6 +512,10 @@ class Server:
 
     def set_inflight(self, ticks):
         _check(lib().gmcs_server_set_inflight(self.srv, int(ticks)), "gmcs_server_set_inflight")
+
+    def set_tick_work(self, max_evals):
+        """Cap (particles x points x steps) on the frames a tick gathers; 0 lifts it."""
+        _check(lib().gmcs_server_set_tick_work(self.srv, float(max_evals)), "gmcs_server_set_tick_work")
 
     def drain(self):
         _check(lib().gmcs_server_drain(self.srv), "gmcs_server_drain")

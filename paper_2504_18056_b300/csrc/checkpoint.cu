@@ -26,7 +26,7 @@ using namespace gmcs;
 namespace {
 
 const char kMagic[8] = {'G', 'M', 'C', 'S', 'C', 'K', 'P', 'T'};
-constexpr uint32_t kVersion = 3;   // 3: every field table holds coefficients after a zero miss record
+constexpr uint32_t kVersion = 3;   // 3: 16-bit field tables hold coefficient records too
 
 struct Header {
     char magic[8];
@@ -71,8 +71,8 @@ bool finite_grid(const gmcs_grid& g) {
 }
 
 // Bytes a keyframe's table must hold for its storage type and lattice, or 0 when
-// the pair is not one the library writes (field tables: one record per cell plus
-// the miss record; GICP voxel maps: 48 bytes per voxel).
+// the pair is not one the library writes (field tables: one record per cell;
+// GICP voxel maps: 48 bytes per voxel).
 uint64_t expected_table_bytes(const TableHead& t, const gmcs_config& cfg) {
     if (!finite_grid(t.grid)) return 0;
     if (t.dtype == 3) {
@@ -90,7 +90,7 @@ uint64_t expected_table_bytes(const TableHead& t, const gmcs_config& cfg) {
         if (t.grid.n[a] < 2 || t.grid.n[a] > (1 << 22)) return 0;
         nc *= (uint64_t)(t.grid.n[a] - 1);
     }
-    return nc < ((uint64_t)1 << 31) ? (nc + 1) * (t.dtype == 0 ? 32 : 16) : 0;
+    return nc < ((uint64_t)1 << 31) ? nc * (t.dtype == 0 ? 32 : 16) : 0;
 }
 
 uint64_t expected_occ_bytes(const gmcs_grid& g) {
@@ -252,7 +252,6 @@ int load_impl(gmcs_ctx* c, const char* path, bool* touched) {
         t.dtype = th.dtype;
         t.grid = th.grid;
         t.bytes = th.bytes;
-        t.lead = th.dtype == 3 ? 0 : (th.dtype == 0 ? 32 : 16);
         buf.resize(t.bytes);
         if (!in.get(buf.data(), t.bytes)) return GMCS_E_IO;
         if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
@@ -280,7 +279,7 @@ int load_impl(gmcs_ctx* c, const char* path, bool* touched) {
         if (!rc) {
             TableDesc td;
             std::memset(&td, 0, sizeof(td));
-            td.cells = table_cells(t);
+            td.cells = t.cells;
             td.ox = (float)t.grid.origin[0];
             td.oy = (float)t.grid.origin[1];
             td.oz = (float)t.grid.origin[2];

@@ -11,9 +11,7 @@
 //                       x fastest, holding the 8 coefficients of the cell's
 //                       trilinear polynomial: FP32 records are 32 B (two float4),
 //                       BF16/FP16 records 16 B (one uint4, two coefficients per
-//                       32-bit word). One all-zero "miss" record sits just before
-//                       cell 0: a lookup outside the lattice reads it (index -1)
-//                       instead of branching around its load.
+//                       32-bit word).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -322,33 +320,18 @@ __device__ __forceinline__ void ld_record32(const float4* p, float4& a, float4& 
         : "l"(p));
 }
 
-// Lookups outside the lattice: with GMCS_MISSREC = 1 every lane loads, those
-// lanes the zero miss record before cell 0 (index -1); with 0 (the default, faster)
-// their loads are predicated off and their record registers zeroed.
-#ifndef GMCS_MISSREC
-#define GMCS_MISSREC 0
-#endif
-
-// Index of cell (cx, cy, cz) in a table of ncx x ncy x ncz cells, or -1 when the
-// cell lies outside the lattice on any axis.
-__device__ __forceinline__ int cell_index(uint32_t ncx, uint32_t ncy, uint32_t ncz, int cx, int cy, int cz) {
-    const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-    return valid ? (int)(((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx) : -1;
-}
-
-// The coefficient record of cell `idx` widened to float in record order: zeros
-// when !valid (without a load, or from the miss record with GMCS_MISSREC).
+// The coefficient record of cell `idx` widened to float in record order; zeros
+// without a load when !valid.
 template <int DT>
 __device__ __forceinline__ void load_cell(const void* __restrict__ cells, uint32_t idx, bool valid, float* v) {
-    const ptrdiff_t at = GMCS_MISSREC ? (valid ? (ptrdiff_t)idx : (ptrdiff_t)-1) : (ptrdiff_t)idx;
     if (DT == 0) {
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if (GMCS_MISSREC || valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * at, a, b);
+        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, a, b);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
         uint4 q = make_uint4(0u, 0u, 0u, 0u);
-        if (GMCS_MISSREC || valid) q = __ldg(reinterpret_cast<const uint4*>(cells) + at);
+        if (valid) q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
         decode_rec16<DT>(q, v);
     }
 }

@@ -12,18 +12,14 @@ namespace gmcs {
 enum Kind { K_PREDICT, K_SELECT, K_PASS_GRAD, K_PASS_VALUE, K_FINISH, K_WEIGH, K_RESAMPLE, K_GATHER, K_TABLE, K_MISC, K_COUNT };
 
 struct HostTable {
-    void* cells = nullptr;           // the allocation: [lead bytes: zero miss record][cell records]
-    size_t bytes = 0;                // allocation size, miss record included
-    size_t lead = 0;                 // field tables: one record; GICP voxel maps: 0
+    void* cells = nullptr;           // cell records (field) or voxel records (GICP)
+    size_t bytes = 0;
     gmcs_grid grid;
     int dtype = 0;
     unsigned char* occ = nullptr;   // occupancy lattice for the overlap rate (Sec. III-E)
     gmcs_grid occ_grid;
     size_t occ_bytes = 0;
 };
-
-// First cell record of a table (the lookup kernels' cell 0).
-inline void* table_cells(const HostTable& t) { return static_cast<char*>(t.cells) + t.lead; }
 
 struct EvPair {
     int kind;

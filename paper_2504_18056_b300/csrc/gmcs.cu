@@ -228,6 +228,7 @@ void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* o
     pa.groups = groups;
     pa.chunk_len = chunk;
     pa.eps = c->cfg.eps;
+    pa.want_ll = (!grad || out_ll) ? 1 : 0;
     FinishArgs fa;
     fa.part = c->part;
     fa.pose = c->pose[c->cur];
@@ -849,7 +850,7 @@ int register_keyframe(gmcs_ctx* c, HostTable& t, const gmcs_grid* grid, int ncx,
     }
     TableDesc td;
     std::memset(&td, 0, sizeof(td));
-    td.cells = table_cells(t);
+    td.cells = t.cells;
     td.ox = (float)grid->origin[0];
     td.oy = (float)grid->origin[1];
     td.oz = (float)grid->origin[2];
@@ -962,15 +963,10 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     HostTable t;
     t.grid = *grid;
     t.dtype = dtype;
-    t.lead = rec;   // the zero miss record before cell 0
-    t.bytes = (ncell + 1) * rec;
+    t.bytes = ncell * rec;
     if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
         cudaGetLastError();
         return GMCS_E_OOM;
-    }
-    if (cudaMemsetAsync(t.cells, 0, rec, c->stream) != cudaSuccess) {
-        cudaFree(t.cells);
-        return GMCS_E_CUDA;
     }
     // squared-distance scratch, grown to the largest table seen
     if (c->d2_cap < nv) {
@@ -1035,7 +1031,7 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     pa.nz = (int)nz;
     pa.inv_two_sigma2 = 1.0f / (2.0f * c->cfg.sigma * c->cfg.sigma);
     pa.r_t2 = c->cfg.r_t * c->cfg.r_t;
-    pa.cells = table_cells(t);
+    pa.cells = t.cells;
     pa.dtype = dtype;
     {
         Launch L(c, K_TABLE);
@@ -1568,7 +1564,7 @@ int gmcs_get_table(gmcs_ctx* c, int k, float* vals) {
     }
     {
         Launch L(c, K_MISC);
-        launch_unpack(table_cells(t), t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], dst, c->stream);
+        launch_unpack(t.cells, t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], dst, c->stream);
     }
     int rc = check_launch();
     if (!rc && !dev) rc = copy_out(c, vals, dst, nv * sizeof(float));
@@ -1591,7 +1587,7 @@ int gmcs_get_records(gmcs_ctx* c, int k, uint64_t c0, uint64_t n, float* coef) {
     }
     {
         Launch L(c, K_MISC);
-        launch_records(table_cells(t), t.dtype, c0, n, dst, c->stream);
+        launch_records(t.cells, t.dtype, c0, n, dst, c->stream);
     }
     int rc = check_launch();
     if (!rc && !dev) rc = copy_out(c, coef, dst, n * 8 * sizeof(float));

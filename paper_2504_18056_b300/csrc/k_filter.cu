@@ -35,7 +35,7 @@ __device__ __forceinline__ void scan_pack_body(const ScanPackArgs& a, int vb, in
     for (int j = vb * blockDim.x + threadIdx.x; j < a.n; j += vg * blockDim.x) {
         float x = a.xyz[3 * j], y = a.xyz[3 * j + 1], z = a.xyz[3 * j + 2];
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) x = y = z = 1e30f;
-        a.out[j] = make_float4(x, y, z, 0.f);
+        a.out[j] = make_float4(x, y, z, 1.f);   // w = 1: the moments' (z, 1) pair
     }
 }
 
@@ -201,6 +201,10 @@ constexpr int pass3_unroll() {
 #define GMCS_XY16 1
 #endif
 constexpr bool kXy16 = GMCS_XY16;
+// packed Gauss-Newton moments in the pipelined passes (Moments, below)
+#ifndef GMCS_PMOM
+#define GMCS_PMOM 1
+#endif
 
 // Packed two-lane FP32 arithmetic (Blackwell add/sub/fma .f32x2).
 __device__ __forceinline__ float2 p2_sub(float2 a, float2 b) {
@@ -211,6 +215,28 @@ __device__ __forceinline__ float2 p2_sub(float2 a, float2 b) {
     return *reinterpret_cast<float2*>(&d);
 #else
     return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+
+__device__ __forceinline__ float2 p2_add(float2 a, float2 b) {
+#if GMCS_F32X2
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&d);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+
+__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) {
+#if GMCS_F32X2
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&d);
+#else
+    return make_float2(a.x * b.x, a.y * b.y);
 #endif
 }
 
@@ -247,7 +273,7 @@ __device__ __forceinline__ int floor_split(float u, float& fl) {
 //   dL/dz = (c3 + c6 y) + x (c5 + c7 y):
 // 4 packed and 3 scalar FMAs for L and its gradient (interpolating the 8 corner
 // values takes 9 packed and 6 scalar operations).
-template <bool GRAD, bool PROD = false>
+template <bool GRAD, bool PROD = false, bool LL = true>
 __device__ __forceinline__ void coef_interp(const float* r, float fx, float fy, float fz, float eps, float& lsum,
                                             float& w, float& gx, float& gy, float& gz) {
     const float2 Q0 = make_float2(r[0], r[1]), Q1 = make_float2(r[2], r[3]);   // (c4, c2), (c7, c6)
@@ -258,8 +284,10 @@ __device__ __forceinline__ void coef_interp(const float* r, float fx, float fy, 
     const float2 XE = p2_fma(YY, AD, BE);                          // (dL/dx, L at x = 0)
     const float L = fmaf(fx, XE.x, XE.y);
     const float den = L + eps;
-    if constexpr (PROD) lsum *= den;
-    else lsum += __log2f(den);
+    if constexpr (LL) {
+        if constexpr (PROD) lsum *= den;
+        else lsum += __log2f(den);
+    }
     if constexpr (GRAD) {
         const float2 TS = p2_fma(Q1, YY, Q3);                      // (c5 + c7 y, c3 + c6 y)
         const float Ly = fmaf(fx, AD.x, AD.y);
@@ -586,29 +614,23 @@ struct RawRec<0> {
 };
 
 // Issue the load of cell c of a slot's table; a cell outside the table, or a
-// stage with no point (live = false), reads as zeros: with GMCS_MISSREC, from
-// the zero miss record before cell 0 (every lane loads); otherwise the lane's
-// load is predicated off and its record registers are zeroed.
+// stage with no point (live = false), reads as zeros: the lane's load is
+// predicated off and its record registers are zeroed. (Loading a zero record
+// stored before cell 0 instead, with no predicate, cost the FP32 gradient pass
+// 1.57 -> 1.69 ms: the extra sector in many warp requests; taking the sign of
+// a -1 index as the predicate cost 1.57 -> 2.12 ms.)
 template <int DT>
 __device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
                                           int cx, int cy, int cz, bool live, RawRec<DT>& r) {
-    if constexpr (GMCS_MISSREC) {
-        const int idx = live ? cell_index(ncx, ncy, ncz, cx, cy, cz) : -1;
-        if constexpr (DT == 0) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (ptrdiff_t)idx, r.a, r.b);
-        else r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+    const bool valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+    const uint32_t idx = ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx;   // used only when valid
+    if constexpr (DT == 0) {
+        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.b = r.a;
+        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
     } else {
-        // the predicate as a plain bool and a zero index for the lanes it turns off: with
-        // the index's sign as the test the pass lost a quarter of its speed
-        const bool valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-        const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
-        if constexpr (DT == 0) {
-            r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-            r.b = r.a;
-            if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
-        } else {
-            r.q = make_uint4(0u, 0u, 0u, 0u);
-            if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
-        }
+        r.q = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
     }
 }
 
@@ -630,9 +652,45 @@ struct Stage {
     RawRec<DT> r[3];
 };
 
-template <int DT, bool GRAD>
+// Gauss-Newton moments of the field model (W, S = sum w p, Q = sum w p p^T) in
+// packed pairs: with the scan point stored as (x, y, z, 1), (Sx, Sy) += w (x, y),
+// (Sz, W) += w (z, 1), (Qxx, Qyy) += (wx, wy) (x, y), (Qxz, Qyz) += (wx, wy) (z, z):
+// 4 packed and 3 scalar operations per point instead of 13 scalar ones.
+struct Moments {
+    float2 sxy, szw, qd, qz;
+    float qxy, qzz;
+};
+
+__device__ __forceinline__ void moments_zero(Moments& m) {
+    m.sxy = m.szw = m.qd = m.qz = make_float2(0.f, 0.f);
+    m.qxy = m.qzz = 0.f;
+}
+
+__device__ __forceinline__ void moments_add(Moments& m, float w, float4 p) {
+    const float2 WW = make_float2(w, w), XY = make_float2(p.x, p.y);
+    const float2 wxy = p2_mul(WW, XY);
+    m.sxy = p2_add(m.sxy, wxy);
+    m.szw = p2_fma(WW, make_float2(p.z, p.w), m.szw);
+    m.qd = p2_fma(wxy, XY, m.qd);
+    m.qz = p2_fma(wxy, make_float2(p.z, p.z), m.qz);
+    m.qxy = fmaf(wxy.x, p.y, m.qxy);
+    m.qzz = fmaf(w * p.z, p.z, m.qzz);
+}
+
+// Into the accumulator layout [.., W, Sx, Sy, Sz, Qxx, Qxy, Qxz, Qyy, Qyz, Qzz].
+__device__ __forceinline__ void moments_store(const Moments& m, float* acc) {
+    acc[7] = m.szw.y;
+    acc[8] = m.sxy.x; acc[9] = m.sxy.y; acc[10] = m.szw.x;
+    acc[11] = m.qd.x; acc[12] = m.qxy; acc[13] = m.qz.x;
+    acc[14] = m.qd.y; acc[15] = m.qz.y; acc[16] = m.qzz;
+}
+
+// LL: the gradient pass also accumulates the log-likelihood (a caller asked for
+// it); the moves of a frame need only the gradient and the moments.
+template <int DT, bool GRAD, bool LL = true>
 __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
     constexpr int NACC = GRAD ? kAccGrad : 1;
+    constexpr bool kLL = LL || !GRAD;
     const WarpWork ww = warp_work(a, vb);
     const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
 
@@ -664,6 +722,8 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
         for (int s = 0; s < 3; ++s)
 #pragma unroll
             for (int d = 0; d < 3; ++d) G[s][d] = C[s][d] = 0.f;
+        Moments mom;
+        moments_zero(mom);
 
         auto issue = [&](Stage<DT>& st, int j, bool live) {
             st.p = __ldg(a.scan + j);
@@ -685,7 +745,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 for (int s = 0; s < 3; ++s) {
                     float v[8], w, gx, gy, gz;
                     unpack_raw<DT>(st.r[s], v);
-                    coef_interp<true, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
+                    coef_interp<true, true, kLL>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
                     const float ux = st.u[s][0], uy = st.u[s][1], uz = st.u[s][2];
                     G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
                     C[s][0] = fmaf(uy, gz, fmaf(-uz, gy, C[s][0]));
@@ -693,18 +753,21 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                     C[s][2] = fmaf(ux, gy, fmaf(-uy, gx, C[s][2]));
                     wsum += w;
                 }
+#if GMCS_PMOM
+                moments_add(mom, wsum, st.p);
+#else
                 add_moments(wsum, st.p, acc);
+#endif
             } else {
                 float w, gx, gy, gz;
 #pragma unroll
                 for (int s = 0; s < 3; ++s) {
                     float v[8];
                     unpack_raw<DT>(st.r[s], v);
-                    coef_interp<false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy,
-                                                   gz);
+                    coef_interp<false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
                 }
             }
-            lsum += __log2f(lprod);
+            if constexpr (kLL) lsum += __log2f(lprod);
         };
         Stage<DT> SA, SB;
         issue(SA, j0, true);
@@ -725,6 +788,9 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 xf_slot(xf[s], sl);
                 fold_slot(sl, a.tables[ks[s]].h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
             }
+#if GMCS_PMOM
+            moments_store(mom, acc);
+#endif
         }
         acc[0] = lsum * 0.69314718055994531f;
     }
@@ -754,15 +820,15 @@ constexpr int pass3_minblocks() {
                 : (DT == 0 ? GMCS_VALUE_MINBLOCKS : GMCS_VALUE_MINBLOCKS16);
 }
 
-template <int DT, bool GRAD, int UNROLL>
+template <int DT, bool GRAD, int UNROLL, bool LL = true>
 __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
-    if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD>(a, vb);
+    if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL>(a, vb);
     else pass3_body<DT, GRAD, UNROLL>(a, vb);
 }
 
-template <int DT, bool GRAD, int UNROLL>
+template <int DT, bool GRAD, int UNROLL, bool LL = true>
 __global__ void __launch_bounds__(kPassThreads, pass3_minblocks<DT, GRAD>()) k_pass3(PassArgs a) {
-    pass3_any<DT, GRAD, UNROLL>(a, blockIdx.x);
+    pass3_any<DT, GRAD, UNROLL, LL>(a, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ finish: sums, move (Eq. 5-7)
@@ -1004,9 +1070,10 @@ constexpr int pass3_b_minblocks() {
     return pass3_minblocks<DT, GRAD>() < 3 ? 3 : pass3_minblocks<DT, GRAD>();
 }
 
+// served frames never ask the gradient passes for the log-likelihood
 template <int DT, bool GRAD, int UNROLL>
 __global__ void __launch_bounds__(kPassThreads, pass3_b_minblocks<DT, GRAD>()) k_pass3_b(const BatchList<PassArgs>* L) {
-    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_any<DT, GRAD, UNROLL>(a, vb)));
+    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_any<DT, GRAD, UNROLL, !GRAD>(a, vb)));
 }
 
 template <bool GRAD, bool GICP>
@@ -1147,7 +1214,8 @@ void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s) {
     // three neighbours (every particle then has all three slots filled): the fused kernel
     const bool three = GMCS_PASS3 && a.k_nb == 3;
 #define GMCS_PASS(DT, G)                                                                            \
-    (three ? k_pass3<DT, G, pass3_unroll<DT, G>()><<<grid, kPassThreads, 0, s>>>(a)                \
+    (three ? ((G && !a.want_ll) ? k_pass3<DT, G, pass3_unroll<DT, G>(), false><<<grid, kPassThreads, 0, s>>>(a) \
+                                : k_pass3<DT, G, pass3_unroll<DT, G>(), true><<<grid, kPassThreads, 0, s>>>(a)) \
            : k_pass<DT, G><<<grid, kPassThreads, 0, s>>>(a))
     if (grad) {
         if (dtype == 0) GMCS_PASS(0, true); else if (dtype == 1) GMCS_PASS(1, true); else GMCS_PASS(2, true);

@@ -89,6 +89,7 @@ struct PassArgs {
     int P, N, k_nb;
     int ntiles, groups, chunk_len;   // groups: chunk groups (kPassCW chunks each)
     float eps;
+    int want_ll;            // gradient pass: also accumulate the log-likelihood (the moves do not need it)
 };
 
 struct FinishArgs {

@@ -144,6 +144,7 @@ struct gmcs_server {
     uint64_t frames_done = 0, ticks = 0, slots_used = 0;
     double evals = 0.0, t_first = 0.0, t_last = 0.0;
     int max_inflight = 2;            // ticks on the GPU at once (1: strictly one after another)
+    double tick_work = 4e8;          // evals (P x N x steps) a tick gathers beyond its oldest frame; 0: no cap
     std::thread worker;
     std::atomic<bool> running{false};
 };
@@ -248,6 +249,21 @@ int launch_tick(gmcs_server* s) {
     std::sort(cand.begin(), cand.end(),
               [](Session* a, Session* b) { return a->pending.front().t_arrive < b->pending.front().t_arrive; });
     if ((int)cand.size() > kMaxSlots) cand.resize(kMaxSlots);
+    // a tick's persistent launches end when its largest frame is done, so every
+    // session in it waits for that frame: after the oldest frame, add frames (oldest
+    // first) only while the tick's work stays under the cap. The frames left out go
+    // to the next tick, which runs beside this one on the other stream.
+    if (s->tick_work > 0.0) {
+        std::vector<Session*> keep;
+        double work = 0.0;
+        for (Session* ss : cand) {
+            const double wk = (double)ss->ctx->P * ss->pending.front().N * std::max(s->cfg.steps, 1);
+            if (!keep.empty() && work + wk > s->tick_work) continue;
+            keep.push_back(ss);
+            work += wk;
+        }
+        cand.swap(keep);
+    }
     TickDesc& D = *t->h_desc;
     list_clear(D.pack); list_clear(D.knn); list_clear(D.pred); list_clear(D.sel); list_clear(D.pgrad); list_clear(D.fgrad);
     list_clear(D.pval); list_clear(D.fval); list_clear(D.weigh); list_clear(D.scan); list_clear(D.tot);
@@ -388,6 +404,13 @@ int gmcs_server_set_inflight(gmcs_server* s, int ticks) {
     if (!s || ticks < 1 || ticks > 2) return GMCS_E_INVALID;
     std::lock_guard<std::mutex> lock(s->mu);
     s->max_inflight = ticks;
+    return GMCS_OK;
+}
+
+int gmcs_server_set_tick_work(gmcs_server* s, double max_evals) {
+    if (!s || !(max_evals >= 0.0)) return GMCS_E_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->tick_work = max_evals;
     return GMCS_OK;
 }
 

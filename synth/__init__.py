@@ -339,17 +339,18 @@ def _odometry(traj):
 
 def box_room_workload(seed=0, n_particles=1024, n_frames=10, n_keyframes=4, h=0.25,
                       surface_spacing=0.05, kf_radius=10.0, init_trans=0.3, init_rot_deg=5.0,
-                      motion_std=(0.02, np.deg2rad(0.5)), kf_pert=(0.0, 0.0)):
+                      motion_std=(0.02, np.deg2rad(0.5)), kf_pert=(0.0, 0.0), lidar=(16, 32)):
     """Plain tiny case: box room, 4 keyframe grids at 0.25 m built from surface
     samples (5 cm spacing, 1 cm noise), 512-point scans from a 16 x 32 lidar
-    with 1 cm range noise, particles spread N(0, 0.3 m / 5 deg)."""
+    (lidar = (beams, azimuths) for other scan sizes; the room is closed, so every
+    ray returns) with 1 cm range noise, particles spread N(0, 0.3 m / 5 deg)."""
     rng = np.random.default_rng(seed)
     scene = box_room(seed)
     world = sample_surfaces(scene, surface_spacing, 0.01, rng)
     traj = room_walk(seed + 1, n_keyframes + n_frames + 1)
     kf_poses = traj[:n_keyframes]
     frames = traj[n_keyframes:]
-    dirs = lidar_dirs(16, 32, -15.0, 15.0)
+    dirs = lidar_dirs(lidar[0], lidar[1], -15.0, 15.0)
     keyframes = []
     for k in range(n_keyframes):
         Tk = kf_poses[k]

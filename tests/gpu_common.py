@@ -73,3 +73,40 @@ def rel_pose_error(A, B):
     ang = np.where(ang < 1e-3, np.linalg.norm(skew, axis=1), ang)
     tr = np.linalg.norm(A[:, :, 3] - B[:, :, 3], axis=1)
     return ang, tr
+
+
+def set_state(f, st):
+    """Load the oracle state st (rounded to float32) into the filter: poses,
+    log-weights and every keyframe's per-particle poses; frame counter 0."""
+    st.poses[:] = st.poses.astype(np.float32)
+    st.kf_poses[:] = st.kf_poses.astype(np.float32)
+    f.init_particles(st.poses.astype(np.float32), st.logw.copy())
+    for k in range(st.kf_poses.shape[0]):
+        f.set_kf_poses(k, np.ascontiguousarray(st.kf_poses[k].astype(np.float32)))
+
+
+def check_moved_frame(ll, poses, nbr, ref, ref_poses, st, scan, grids, tables, label=""):
+    """One frame without resampling, GPU against oracle from the same state.
+    The moved poses may diverge by the rounding of three moves (d_i, the norm of
+    log(T_oracle^-1 T_gpu)); every particle's value-pass log-likelihood must then
+    agree within 1e-4 relative plus what that divergence can change it by:
+    1.5 * d_i * sum_jk |d l_jk / d xi| at the oracle's pose (a Lipschitz bound of
+    l over the lookups). Returns the divergences."""
+    P = ll.shape[0]
+    same_nbr = (nbr == ref["nbr"]).all(axis=1)
+    assert same_nbr.mean() >= 0.99, (label, same_nbr.mean())
+    ang, tr = rel_pose_error(poses, ref_poses)
+    d = np.hypot(ang, tr)
+    assert np.median(d) <= 1e-5 and d.max() <= 1e-2, (label, np.median(d), d.max())
+    lip = np.zeros(P)
+    for i in range(P):
+        ks = [int(k) for k in ref["nbr"][i] if k >= 0]
+        o = oracle.eval_particle(ref_poses[i], [st.kf_poses[k][i] for k in ks], [tables[k] for k in ks],
+                                 [grids[k] for k in ks], scan)
+        lip[i] = o["gabs"]
+    bound = 1e-4 * np.abs(ref["ll"]) + 1.5 * d * lip
+    err = np.abs(ll - ref["ll"])
+    ok = err <= bound
+    # a particle whose neighbour set differs (a near-tie of keyframe distances) reads other tables
+    assert np.all(ok | ~same_nbr), (label, np.nonzero(~ok & same_nbr)[0][:10], (err / bound)[~ok].max())
+    return d

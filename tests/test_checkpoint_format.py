@@ -57,7 +57,7 @@ def write(path, P=5, tables=((0, (4, 3, 2)),), cfg=None, frame=7, tweak=None):
         th.dtype = dt
         th.grid = grid((0.0, 0.0, 0.0), 0.2, n)
         rec = 48 if dt == 3 else (32 if dt == 0 else 16)
-        cells = int(np.prod(n)) if dt == 3 else int(np.prod([v - 1 for v in n])) + 1
+        cells = int(np.prod(n)) if dt == 3 else int(np.prod([v - 1 for v in n]))
         th.bytes = cells * rec
         if tweak:
             tweak("table", th)

@@ -6,8 +6,9 @@ and sessions are admitted by the device-memory budget."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from gpu_common import make_filter, torch_cuda
+from gpu_common import check_moved_frame, make_filter, set_state, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -119,4 +120,57 @@ def test_admission_by_budget(worlds):
     assert srv.stats()["used_bytes"] == 0
     s2 = srv.open(P, K, 1024, table_bytes=one, seed=2)                 # admitted once memory is back
     assert s2 is not None
+    srv.close()
+
+
+def test_served_mix_of_uneven_sessions_matches_oracle():
+    """Three sessions of different particle counts (1,000, 2,500, 257) and scan
+    sizes (512, 1,024, 3,000 points) served together in every tick, each compared
+    with the FP64 oracle frame by frame: before every frame each session is set to
+    its oracle state (rounded to float32), then the three frames share a tick and
+    every session's neighbours, moved poses and log-likelihoods must meet the
+    whole-frame bound of the plain path (check_moved_frame)."""
+    import paper_2504_18056_b300 as g
+    torch_cuda()
+    specs = {"A": (0, 1000, (16, 32)), "B": (1, 2500, (16, 64)), "C": (2, 257, (30, 100))}
+    worlds, tables, grids, states = {}, {}, {}, {}
+    for n, (seed, P, lidar) in specs.items():
+        w = synth.box_room_workload(seed=seed, n_particles=P, n_frames=3, lidar=lidar)
+        worlds[n] = w
+        grids[n] = [kf["grid"] for kf in w["keyframes"]]
+        tables[n] = [oracle.build_table(kf["points"], kf["grid"], 0.2, 1.0) for kf in w["keyframes"]]
+        states[n] = oracle.State(w["particles"], np.stack(w["kf_particle_poses"]), tables[n], grids[n])
+    assert [worlds[n]["scans"][0].shape[0] for n in "ABC"] == [512, 1024, 3000]
+    srv = g.Server(budget_bytes=40 << 30, max_sessions=4, background=False, resample=g.RESAMPLE_NEVER)
+    sids = {}
+    for n, w in worlds.items():
+        P, K = w["particles"].shape[0], len(w["keyframes"])
+        sid = srv.open(P, K, 4096, table_bytes=0, seed=0)
+        f = srv.session(sid)
+        f.init_particles(np.ascontiguousarray(w["particles"]))
+        for k, kf in enumerate(w["keyframes"]):
+            f.add_keyframe(kf["points"], kf["grid"], np.ascontiguousarray(w["kf_particle_poses"][k]))
+        srv.ready(sid)
+        sids[n] = (sid, f)
+    for fr in range(3):
+        tickets = {}
+        for n in "ABC":
+            set_state(sids[n][1], states[n])
+        for n in "ABC":
+            w = worlds[n]
+            tickets[n] = srv.submit(sids[n][0], w["scans"][fr], w["odometry"][fr], w["cov"])
+        srv.drain()
+        st = srv.stats()
+        assert st["mean_sessions_per_tick"] > 1.0
+        for n in "ABC":
+            w, (sid, f) = worlds[n], sids[n]
+            assert srv.poll(tickets[n]) is not None
+            P = w["particles"].shape[0]
+            ll = np.zeros(P, np.float32)
+            nbr = np.zeros((P, 3), np.int32)
+            f.frame_diag(ll, None, None, nbr)
+            moved, _ = f.particles()
+            ref = states[n].step(w["scans"][fr], w["odometry"][fr], w["cov"], frame=0, resample=2)
+            check_moved_frame(ll, moved, nbr, ref, states[n].poses, states[n], w["scans"][fr], grids[n], tables[n],
+                              f"session {n} frame {fr}")
     srv.close()
