@@ -797,6 +797,116 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
     store_partials<NACC>(a, acc, ww);
 }
 
+// ---- the same pass with the pipeline interleaved per neighbour slot: while
+// slot s of point j is interpolated, slot s of point j + 1 is issued, so at
+// most four slots' records (instead of six) and two points are in flight at a
+// time -- fewer live registers for the same look-ahead.
+#ifndef GMCS_QPIPE
+#define GMCS_QPIPE 0
+#endif
+
+template <int DT>
+struct SlotStage {
+    float u[3], f[3];
+    RawRec<DT> r;
+};
+
+template <int DT, bool GRAD, bool LL = true>
+__device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
+    constexpr int NACC = GRAD ? kAccGrad : 1;
+    constexpr bool kLL = LL || !GRAD;
+    const WarpWork ww = warp_work(a, vb);
+    const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
+
+    float acc[NACC];
+#pragma unroll
+    for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
+
+    if (i < a.P && j0 < j1) {
+        Xf xf[3];
+        const void* cells[3];
+        uint32_t ncx[3], ncy[3], ncz[3];
+        {
+            float Tt[12];
+            load_pose(a.pose, a.ld, i, Tt);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const Slot sl = make_slot(a, i, a.nbr[(size_t)s * a.ld + i], Tt);
+                xf[s] = slot_xf(sl);
+                cells[s] = sl.cells;
+                ncx[s] = sl.ncx; ncy[s] = sl.ncy; ncz[s] = sl.ncz;
+            }
+        }
+        const float eps = a.eps;
+        float lsum = 0.f;
+        float G[3][3], C[3][3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) G[s][d] = C[s][d] = 0.f;
+        Moments mom;
+        moments_zero(mom);
+
+        auto issue = [&](SlotStage<DT>& st, float4 p, int s, bool live) {
+            int cx, cy, cz;
+            slot_point<DT, true>(xf[s], p, st.u[0], st.u[1], st.u[2], cx, cy, cz, st.f[0], st.f[1], st.f[2]);
+            fetch_raw<DT>(cells[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r);
+        };
+        // interpolate one slot of a point; returns its weight (gradient pass)
+        auto use = [&](const SlotStage<DT>& st, int s, float& lprod) -> float {
+            float v[8], w = 0.f, gx, gy, gz;
+            unpack_raw<DT>(st.r, v);
+            if constexpr (GRAD) {
+                coef_interp<true, true, kLL>(v, st.f[0], st.f[1], st.f[2], eps, lprod, w, gx, gy, gz);
+                G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
+                C[s][0] = fmaf(st.u[1], gz, fmaf(-st.u[2], gy, C[s][0]));
+                C[s][1] = fmaf(st.u[2], gx, fmaf(-st.u[0], gz, C[s][1]));
+                C[s][2] = fmaf(st.u[0], gy, fmaf(-st.u[1], gx, C[s][2]));
+            } else {
+                coef_interp<false, true>(v, st.f[0], st.f[1], st.f[2], eps, lprod, w, gx, gy, gz);
+            }
+            return w;
+        };
+        SlotStage<DT> A[3], B[3];
+        float4 pA = __ldg(a.scan + j0);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) issue(A[s], pA, s, true);
+        // one point: its three slots used while the next point's are issued
+        auto step = [&](SlotStage<DT>* cur, float4 pc, SlotStage<DT>* nxt, float4 pn, bool live) {
+            float lprod = 1.f, wsum = 0.f;
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                issue(nxt[s], pn, s, live);
+                wsum += use(cur[s], s, lprod);
+            }
+            if constexpr (GRAD) moments_add(mom, wsum, pc);
+            if constexpr (kLL) lsum += __log2f(lprod);
+        };
+        for (int j = j0;; j += 2) {   // j1 and the exits are uniform across the warp
+            const bool m1 = j + 1 < j1;
+            const float4 pB = __ldg(a.scan + (m1 ? j + 1 : j));
+            step(A, pA, B, pB, m1);
+            if (!m1) break;
+            const bool m2 = j + 2 < j1;
+            pA = __ldg(a.scan + (m2 ? j + 2 : j + 1));
+            step(B, pB, A, pA, m2);
+            if (!m2) break;
+        }
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                Slot sl;
+                xf_slot(xf[s], sl);
+                const int k = a.nbr[(size_t)s * a.ld + i];
+                fold_slot(sl, a.tables[k].h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
+            }
+            moments_store(mom, acc);
+        }
+        acc[0] = lsum * 0.69314718055994531f;
+    }
+    store_partials<NACC>(a, acc, ww);
+}
+
 // CTAs per SM the register allocation is sized for: the pipelined gradient
 // pass fits 168 registers at 3 CTAs per SM; the unpipelined one uses ~150 and
 // capping it at 128 costs 4 %; the value passes fit 128 at 4 CTAs per SM
@@ -822,7 +932,8 @@ constexpr int pass3_minblocks() {
 
 template <int DT, bool GRAD, int UNROLL, bool LL = true>
 __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
-    if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL>(a, vb);
+    if constexpr (GMCS_QPIPE && pass3_pipelined<DT, GRAD>()) pass3q_body<DT, GRAD, LL>(a, vb);
+    else if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL>(a, vb);
     else pass3_body<DT, GRAD, UNROLL>(a, vb);
 }
 

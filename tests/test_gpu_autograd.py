@@ -139,3 +139,25 @@ def test_forward_backward_timing(setup):
          "backward_lookups_per_s": lookups / (np.median(bwd) * 1e-3)}
     print("\nAUTOGRAD_TIMING " + json.dumps(t))
     assert 0 < t["forward_ms"] < 1e3 and 0 < t["backward_ms"] < 1e3
+
+
+def test_backward_refuses_a_changed_filter(box_room):
+    """The backward re-reads the base poses and neighbours from the filter: a
+    call that changed them after the forward (a new selection, a step) makes it
+    raise instead of returning the gradient of another function."""
+    torch = torch_cuda()
+    from paper_2504_18056_b300.autograd import scan_loglik
+    P = 256
+    f = make_filter(box_room, P, max_points=1024)
+    f.select()
+    scan_d = torch.from_numpy(box_room["scans"][0]).cuda()
+    xi = torch.zeros((P, 6), dtype=torch.float32, device="cuda", requires_grad=True)
+    scan_loglik(xi, f, scan_d).sum().backward()          # unchanged filter: fine
+    assert xi.grad is not None and torch.isfinite(xi.grad).all()
+    for change in (lambda: f.select(), lambda: f.step(box_room["scans"][0], box_room["odometry"][0], box_room["cov"])):
+        xi.grad = None
+        ll = scan_loglik(xi, f, scan_d)
+        change()
+        with pytest.raises(RuntimeError, match="changed since the forward"):
+            ll.sum().backward()
+    f.close()

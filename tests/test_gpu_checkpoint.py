@@ -60,14 +60,25 @@ def test_refusals(tmp_path, box_room):
     with pytest.raises(g.GmcsError) as e:
         b.load(str(bad))
     assert e.value.code == g.E_IO
-    old = tmp_path / "v1.ckpt"             # a file of the earlier format (FP32 tables as corners)
+    old = tmp_path / "v2.ckpt"             # a file of the earlier format (16-bit tables as corners)
     raw = bytearray(open(path, "rb").read())
-    assert raw[:8] == b"GMCSCKPT" and int.from_bytes(raw[8:12], "little") == 2
-    raw[8:12] = (1).to_bytes(4, "little")
+    assert raw[:8] == b"GMCSCKPT" and int.from_bytes(raw[8:12], "little") == 3
+    raw[8:12] = (2).to_bytes(4, "little")
     old.write_bytes(bytes(raw))
     with pytest.raises(g.GmcsError) as e:
         b.load(str(old))
     assert e.value.code == g.E_IO
+    # a table block cut short: refused on the host, before any device state changes
+    cut = tmp_path / "cut.ckpt"
+    cut.write_bytes(open(path, "rb").read()[:-4096])
+    with pytest.raises(g.GmcsError) as e:
+        b.load(str(cut))
+    assert e.value.code == g.E_IO
+    assert b.sizes()[1] == 0                # b is still empty and usable
+    b.load(path)
+    assert b.sizes()[:2] == a.sizes()[:2]
+    b.close()
+    b = g.Filter(256, 8, 1024)
     small = g.Filter(128, 8, 1024)
     with pytest.raises(g.GmcsError) as e:
         small.load(path)                    # 256 particles do not fit 128
