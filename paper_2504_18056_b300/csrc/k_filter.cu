@@ -801,9 +801,16 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 // slot s of point j is interpolated, slot s of point j + 1 is issued, so at
 // most four slots' records (instead of six) and two points are in flight at a
 // time -- fewer live registers for the same look-ahead.
-#ifndef GMCS_QPIPE
-#define GMCS_QPIPE 0
+// (BF16 gradient pass 1.542 -> 1.521 ms; FP32 1.566 -> 1.607 ms, so FP32 keeps the
+// two whole stages)
+#ifndef GMCS_QPIPE32
+#define GMCS_QPIPE32 0
 #endif
+#ifndef GMCS_QPIPE16
+#define GMCS_QPIPE16 1
+#endif
+template <int DT>
+constexpr bool qpipe() { return DT == 0 ? GMCS_QPIPE32 : GMCS_QPIPE16; }
 
 template <int DT>
 struct SlotStage {
@@ -932,7 +939,7 @@ constexpr int pass3_minblocks() {
 
 template <int DT, bool GRAD, int UNROLL, bool LL = true>
 __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
-    if constexpr (GMCS_QPIPE && pass3_pipelined<DT, GRAD>()) pass3q_body<DT, GRAD, LL>(a, vb);
+    if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>()) pass3q_body<DT, GRAD, LL>(a, vb);
     else if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL>(a, vb);
     else pass3_body<DT, GRAD, UNROLL>(a, vb);
 }

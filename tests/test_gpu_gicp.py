@@ -17,6 +17,11 @@ pytestmark = pytest.mark.gpu
 EPS = 1e-3
 H_VOX = 1.0
 TAU = 20.0
+# relative band around the cap tau inside which the oracle counts a term as either
+# inlier or capped (slack): the GPU forms d^2 in FP32 from the adjugate of a
+# covariance of condition ~1e3, a relative rounding of ~1e3 x 6e-8 per term over
+# a few terms, 2e-4 at most
+GATE = 2e-4
 
 
 @pytest.fixture(scope="module")
@@ -113,7 +118,7 @@ def test_eval_matches_oracle(gw):
         ks = [int(k) for k in nbr[i]]
         o = oracle.gicp_eval(w["particles"][i].astype(np.float64), [w["kf_particle_poses"][k][i] for k in ks],
                              [maps[k] for k in ks], [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4,
-                             gate_delta=1e-3)
+                             gate_delta=GATE)
         sl = o["slack"]
         r_ll.append(abs(ll[i] - o["ll"]) / (1e-6 * abs(o["ll"]) + sl[0]))
         gs = np.linalg.norm(o["b"]) * 2
@@ -152,7 +157,7 @@ def test_small_shapes_match_oracle(gw, P, N):
         ks = [int(k) for k in nbr[i]]
         o = oracle.gicp_eval(w["particles"][i].astype(np.float64), [w["kf_particle_poses"][k][i] for k in ks],
                              [maps[k] for k in ks], [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4,
-                             gate_delta=1e-3)
+                             gate_delta=GATE)
         sl = o["slack"]
         assert abs(ll[i] - o["ll"]) <= 1e-6 * abs(o["ll"]) + sl[0]
         gs = np.linalg.norm(o["b"]) * 2
@@ -162,6 +167,11 @@ def test_small_shapes_match_oracle(gw, P, N):
 
 
 def test_move_matches_oracle(gw):
+    """One move, every 16th particle against the oracle's move from its own b
+    and H. Where no lookup sits near a voxel face or the cap, the poses agree to
+    1e-3 of the step; elsewhere the bound is what the slack on b and H can move
+    the damped solve by: |d psi| <= 1.1 |(H + lambda diag H)^-1| (|db| + |dH| |psi|),
+    with db and dH the eval test's tolerances plus the slack."""
     w, grids, covs, maps = gw
     P = 1024
     f = _filter(w, grids, P=P)
@@ -171,21 +181,30 @@ def test_move_matches_oracle(gw):
     f.move(scan)
     poses, _ = f.particles()
     scov = oracle.knn_cov(scan, k=10, eps=EPS)
-    moved = 0
+    moved = slacked = 0
     for i in range(0, P, 16):
         ks = [int(k) for k in nbr[i]]
         T0 = w["particles"][i].astype(np.float64)
         o = oracle.gicp_eval(T0, [w["kf_particle_poses"][k][i] for k in ks], [maps[k] for k in ks],
-                             [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4, gate_delta=1e-3)
-        if o["slack"].sum() > 0:
-            continue
+                             [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4, gate_delta=GATE)
         T1, psi = oracle.move_h(T0, o["b"], o["H"], lambda_=1e-3)
         ang, tr = rel_pose_error(poses[i], T1)
         step = np.linalg.norm(psi[3:]) + np.linalg.norm(psi[:3])
-        assert ang[0] <= 1e-3 * max(np.linalg.norm(psi[:3]), 1e-3) + 2e-6, (i, ang, psi)
-        assert tr[0] <= 1e-3 * max(np.linalg.norm(psi[3:]), 1e-3) + 2e-6, (i, tr, psi)
+        sl = o["slack"]
+        if sl.sum() > 0:
+            H = o["H"]
+            Hd = H + 1e-3 * np.diag(np.diag(H))
+            db = 1e-4 * max(2 * np.linalg.norm(o["b"]), 1e-3 * np.linalg.norm(H)) + sl[1]
+            dH = 2e-4 * np.linalg.norm(H) + sl[2] + 1e-6
+            bound = 1.1 * np.linalg.norm(np.linalg.inv(Hd), 2) * (db + dH * np.linalg.norm(psi)) + 2e-6
+            assert np.hypot(ang[0], tr[0]) <= bound, (i, ang, tr, bound)
+            slacked += 1
+        else:
+            assert ang[0] <= 1e-3 * max(np.linalg.norm(psi[:3]), 1e-3) + 2e-6, (i, ang, psi)
+            assert tr[0] <= 1e-3 * max(np.linalg.norm(psi[3:]), 1e-3) + 2e-6, (i, tr, psi)
         moved += step > 0
     assert moved >= 20
+    print(f"\nGICP_MOVE checked {P // 16} particles, {slacked} with slack bounds")
     f.close()
 
 
@@ -255,7 +274,7 @@ def test_full_size_eval_sampled():
         ks = [int(k) for k in nbr[i]]
         o = oracle.gicp_eval(w["particles"][i].astype(np.float64), [w["kf_particle_poses"][k][i] for k in ks],
                              [maps[k] for k in ks], [grids[k] for k in ks], scan, scov, tau=TAU, face_delta=1e-4,
-                             gate_delta=1e-3)
+                             gate_delta=GATE)
         sl = o["slack"]
         worst = max(worst, abs(ll[i] - o["ll"]) / (1e-6 * abs(o["ll"]) + sl[0]),
                     np.linalg.norm(gg[i] - 2 * o["b"]) / (2e-4 * max(2 * np.linalg.norm(o["b"]), 1e-3 * np.linalg.norm(o["H"]))

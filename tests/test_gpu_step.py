@@ -7,7 +7,7 @@ import pytest
 import oracle
 import synth
 from gpu_common import (check_moved_frame, grad_tolerance, gpu_eval, gpu_nbr, make_filter, moment_scales,
-                        rel_pose_error, set_state, torch_cuda)
+                        oracle_nbr, rel_pose_error, set_state, torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
@@ -99,6 +99,9 @@ def test_full_size_eval_sampled(forest):
     nbr = gpu_nbr(f, P, 3)
     ll, g, mom = gpu_eval(f, scan, P)
     idx = np.unique(np.concatenate([np.linspace(0, P - 1, 22).astype(int), [31, 99_999]]))
+    # the neighbour selection at this size: the oracle's own choice on the sampled particles
+    ref_nbr = oracle_nbr(forest["particles"][idx], [kp[idx] for kp in forest["kf_particle_poses"]])
+    np.testing.assert_array_equal(nbr[idx], ref_nbr)
     need = sorted(set(int(k) for k in nbr[idx].ravel()))
     tabs = {k: oracle.build_table(forest["keyframes"][k]["points"], forest["keyframes"][k]["grid"], 0.2, 1.0)
             for k in need}
