@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--points", type=int, default=2048)
     ap.add_argument("--keyframes", type=int, default=20)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--layout", default="dense", choices=["dense", "columns"],
+                    help="likelihood tables: dense lattices, or column-sparse (only each (x, y) column's run of "
+                         "nonzero cells)")
     ap.add_argument("--model", default="field", choices=["field", "gicp"],
                     help="likelihood: voxel field (the benchmark's) or GICP distribution-to-distribution (Eq. 2-6)")
     ap.add_argument("--resample", default="always", choices=["always", "ess", "never", "prune"],
@@ -340,8 +343,9 @@ def run_native(a, world, rank, local):
     dtype = {"f32": 0, "bf16": 1, "f16": 2}[a.dtype]
     gicp = a.model == "gicp"
     stream = torch.cuda.current_stream(dev)
+    layout = g.LAYOUT_COLUMNS if a.layout == "columns" else g.LAYOUT_DENSE
     f = g.Filter(P, K, N, stream=stream.cuda_stream, table_dtype=dtype, seed=rank,
-                 model=g.MODEL_GICP if gicp else g.MODEL_FIELD, resample=POLICY[a.resample])
+                 model=g.MODEL_GICP if gicp else g.MODEL_FIELD, resample=POLICY[a.resample], table_layout=layout)
     f.init_particles(w["particles"])
     for k, kf in enumerate(w["keyframes"]):
         grid = synth.grid_for_points(kf["points"], GICP_VOXEL, 1.0) if gicp else kf["grid"]
@@ -441,10 +445,12 @@ def run_native(a, world, rank, local):
         "config": {"workload": f"single session, {P} particles x {N}-point scans x {K} keyframes "
                                + ("(8192 pts, GICP voxel maps at 1 m, knn 10)" if gicp else "(8192 pts, 0.2 m lattice)")
                                + ", 3 neighbour keyframes, 3 moves/frame"
+                               + (", column-sparse tables" if a.layout == "columns" else "")
                                + ("" if a.resample == "always" else f", resampling policy {a.resample}"),
                    "model": a.model, "resample": a.resample,
                    "particles": P, "points": N, "keyframes": K, "k_nb": 3, "moves": 3,
-                   "table": a.dtype, "l2": "flushed before every timed step (256 MB write)" if not a.no_flush
+                   "table": a.dtype, "layout": a.layout,
+                   "l2": "flushed before every timed step (256 MB write)" if not a.no_flush
                    else "not flushed", "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "frame_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                      "min": float(step_ms.min()), "max": float(step_ms.max())},
@@ -544,8 +550,12 @@ def run_serve(a):
 
     sdt = {"f32": 0, "bf16": 1, "f16": 2}[a.serve_dtype]
     rec = 32 if sdt == 0 else 16        # bytes per cell record
+    slayout = g.LAYOUT_COLUMNS if a.layout == "columns" else g.LAYOUT_DENSE
+    # admission estimate of a keyframe's table: the dense lattice, or for column-sparse
+    # tables a fifth of it (the server charges the actual bytes once the session is set up)
+    table_share = 0.2 if a.layout == "columns" else 1.0
     srv = g.Server(budget_bytes=int(a.budget_gb * (1 << 30)), max_sessions=a.sessions, background=True,
-                   table_dtype=sdt)
+                   table_dtype=sdt, table_layout=slayout)
     if a.tick_work is not None:
         srv.set_tick_work(a.tick_work)
     lat_by_work = []                    # (P x N of the session, server latency of one frame)
@@ -560,8 +570,8 @@ def run_serve(a):
         while waiting:
             spec = specs[waiting[0]]
             P, K, N = spec["P"], spec["K"], spec["N"]
-            tb = K * (pool["keyframes"][0]["grid"]["dims"][0] * pool["keyframes"][0]["grid"]["dims"][1] *
-                      pool["keyframes"][0]["grid"]["dims"][2]) * rec
+            tb = int(K * (pool["keyframes"][0]["grid"]["dims"][0] * pool["keyframes"][0]["grid"]["dims"][1] *
+                          pool["keyframes"][0]["grid"]["dims"][2]) * rec * table_share)
             sid = srv.open(P, K, N, table_bytes=tb, seed=spec["seed"])
             if sid is None:
                 break
@@ -600,7 +610,7 @@ def run_serve(a):
     srv.reset_stats()
     sat_sids = []
     for spec in specs:
-        tb = spec["K"] * int(np.prod(pool["keyframes"][0]["grid"]["dims"])) * rec
+        tb = int(spec["K"] * int(np.prod(pool["keyframes"][0]["grid"]["dims"])) * rec * table_share)
         sid = srv.open(spec["P"], spec["K"], spec["N"], table_bytes=tb, seed=spec["seed"])
         if sid is None:
             break

@@ -53,6 +53,8 @@ extern "C" {
 #define GMCS_E_IO (-8)        /* checkpoint file cannot be written, read or is not a checkpoint */
 #define GMCS_PENDING 1        /* serving: the frame has not completed yet */
 
+#define GMCS_LAYOUT_DENSE 0     /* one record per lattice cell */
+#define GMCS_LAYOUT_COLUMNS 1   /* per (x, y) column only the run of cells whose polynomial is not zero */
 #define GMCS_TABLE_F32 0
 #define GMCS_TABLE_BF16 1
 #define GMCS_TABLE_F16 2
@@ -99,7 +101,7 @@ typedef struct {
                           with the last keyframe falls below this (Sec. III-E: 0.7); 0: off */
     float kf_voxel;    /* voxel edge (m) of the keyframes' occupancy lattices (1.0) */
     float kf_h;        /* lattice step (field) or voxel edge (GICP) of inserted keyframes (0.2) */
-    int reserved;
+    int table_layout;  /* GMCS_LAYOUT_* of the field tables: dense lattice, or column-sparse */
     uint64_t seed;     /* key of the Philox4x32-10 draws (motion noise, resampling offset) */
 } gmcs_config;
 

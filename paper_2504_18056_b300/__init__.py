@@ -23,6 +23,7 @@ OK = 0
 E_INVALID, E_OOM, E_CUDA, E_CAPACITY, E_STATE, E_NONFINITE, E_BUDGET, E_IO = -1, -2, -3, -4, -5, -6, -7, -8
 PENDING = 1
 TABLE_F32, TABLE_BF16, TABLE_F16 = 0, 1, 2
+LAYOUT_DENSE, LAYOUT_COLUMNS = 0, 1
 RESAMPLE_ALWAYS, RESAMPLE_ESS_HALF, RESAMPLE_NEVER, RESAMPLE_PRUNE = 0, 1, 2, 3
 MAX_NB = 8
 MODEL_FIELD, MODEL_GICP = 0, 1
@@ -41,7 +42,7 @@ class Config(C.Structure):
                 ("steps", C.c_int), ("table_dtype", C.c_int), ("resample", C.c_int), ("propagate", C.c_int),
                 ("loop_recent", C.c_int), ("prune_w", C.c_float), ("prune_lr", C.c_float), ("model", C.c_int),
                 ("knn", C.c_int), ("cov_eps", C.c_float), ("gicp_tau", C.c_float), ("kf_overlap", C.c_float),
-                ("kf_voxel", C.c_float), ("kf_h", C.c_float), ("reserved", C.c_int), ("seed", C.c_uint64)]
+                ("kf_voxel", C.c_float), ("kf_h", C.c_float), ("table_layout", C.c_int), ("seed", C.c_uint64)]
 
 
 class Grid(C.Structure):

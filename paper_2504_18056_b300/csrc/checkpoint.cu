@@ -11,6 +11,7 @@
 // counter-based on the restored seed and frame counter).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,9 +42,11 @@ struct Header {
 // Per keyframe, before its table bytes.
 struct TableHead {
     int32_t dtype;
+    int32_t layout;   // GMCS_LAYOUT_* (field tables)
     gmcs_grid grid;
     uint64_t bytes;
 };
+static_assert(sizeof(TableHead) == 64, "checkpoint table header");
 
 int st(cudaError_t e) { return e == cudaSuccess ? GMCS_OK : GMCS_E_CUDA; }
 
@@ -70,27 +73,53 @@ bool finite_grid(const gmcs_grid& g) {
            std::isfinite(g.h) && g.h > 0.0;
 }
 
-// Bytes a keyframe's table must hold for its storage type and lattice, or 0 when
-// the pair is not one the library writes (field tables: one record per cell;
-// GICP voxel maps: 48 bytes per voxel).
-uint64_t expected_table_bytes(const TableHead& t, const gmcs_config& cfg) {
-    if (!finite_grid(t.grid)) return 0;
+// Directory bytes of a column-sparse table (the records start 256-byte aligned).
+uint64_t dir_bytes_of(const gmcs_grid& g) { return ((uint64_t)(g.n[0] - 1) * (g.n[1] - 1) * 8 + 255) / 256 * 256; }
+
+// Whether a keyframe's table size fits its storage type, layout and lattice as
+// the library writes them: GICP voxel maps 48 bytes per voxel; dense field tables
+// one record per cell; column-sparse field tables the directory and then between
+// one record and one per cell (the directory itself is checked once read).
+bool table_bytes_ok(const TableHead& t, const gmcs_config& cfg) {
+    if (!finite_grid(t.grid)) return false;
     if (t.dtype == 3) {
-        if (cfg.model != GMCS_MODEL_GICP) return 0;
+        if (cfg.model != GMCS_MODEL_GICP || t.layout != GMCS_LAYOUT_DENSE) return false;
         uint64_t nv = 1;
         for (int a = 0; a < 3; ++a) {
-            if (t.grid.n[a] < 1) return 0;
+            if (t.grid.n[a] < 1) return false;
             nv *= (uint64_t)t.grid.n[a];
         }
-        return nv < ((uint64_t)1 << 31) ? nv * 48 : 0;
+        return nv < ((uint64_t)1 << 31) && t.bytes == nv * 48;
     }
-    if (t.dtype < 0 || t.dtype > 2 || cfg.model != GMCS_MODEL_FIELD || t.dtype != cfg.table_dtype) return 0;
+    if (t.dtype < 0 || t.dtype > 2 || cfg.model != GMCS_MODEL_FIELD || t.dtype != cfg.table_dtype ||
+        t.layout != cfg.table_layout)
+        return false;
     uint64_t nc = 1;
     for (int a = 0; a < 3; ++a) {
-        if (t.grid.n[a] < 2 || t.grid.n[a] > (1 << 22)) return 0;
+        if (t.grid.n[a] < 2 || t.grid.n[a] > (1 << 22)) return false;
         nc *= (uint64_t)(t.grid.n[a] - 1);
     }
-    return nc < ((uint64_t)1 << 31) ? nc * (t.dtype == 0 ? 32 : 16) : 0;
+    if (nc >= ((uint64_t)1 << 31)) return false;
+    const uint64_t rec = t.dtype == 0 ? 32 : 16;
+    if (t.layout == GMCS_LAYOUT_DENSE) return t.bytes == nc * rec;
+    if (t.layout != GMCS_LAYOUT_COLUMNS || t.grid.n[2] > 65536) return false;
+    const uint64_t db = dir_bytes_of(t.grid);
+    return t.bytes >= db + rec && (t.bytes - db) % rec == 0 && t.bytes - db <= std::max<uint64_t>(nc, 1) * rec;
+}
+
+// A column directory read from a file: every run inside the lattice's z range
+// and inside the records that follow.
+bool directory_ok(const unsigned char* buf, const TableHead& t) {
+    const uint64_t ncol = (uint64_t)(t.grid.n[0] - 1) * (t.grid.n[1] - 1);
+    const uint64_t nrec = (t.bytes - dir_bytes_of(t.grid)) / (t.dtype == 0 ? 32 : 16);
+    const uint32_t ncz = (uint32_t)(t.grid.n[2] - 1);
+    for (uint64_t k = 0; k < ncol; ++k) {
+        uint2 d;
+        std::memcpy(&d, buf + 8 * k, sizeof(d));
+        const uint32_t zlo = d.y & 0xFFFFu, cnt = d.y >> 16;
+        if ((uint64_t)zlo + cnt > ncz || (uint64_t)d.x + cnt > nrec) return false;
+    }
+    return true;
 }
 
 uint64_t expected_occ_bytes(const gmcs_grid& g) {
@@ -118,8 +147,13 @@ int validate(File& in, Header& h) {
     for (int k = 0; k < h.K; ++k) {
         TableHead t;
         if (pos > fsize || !in.seek(pos) || !in.get(&t, sizeof(t))) return GMCS_E_IO;
-        const uint64_t want = expected_table_bytes(t, h.cfg);
-        if (want == 0 || t.bytes != want) return GMCS_E_IO;
+        if (!table_bytes_ok(t, h.cfg)) return GMCS_E_IO;
+        if (t.dtype != 3 && t.layout == GMCS_LAYOUT_COLUMNS) {   // read and check the column directory
+            const uint64_t db = dir_bytes_of(t.grid);
+            if (pos + (int64_t)sizeof(t) + (int64_t)db > fsize) return GMCS_E_IO;
+            std::vector<unsigned char> dbuf(db);
+            if (!in.get(dbuf.data(), db) || !directory_ok(dbuf.data(), t)) return GMCS_E_IO;
+        }
         pos += (int64_t)sizeof(t) + (int64_t)t.bytes;
         gmcs_grid og;
         uint64_t occ_bytes = 0;
@@ -194,6 +228,7 @@ int save_impl(gmcs_ctx* c, const char* path) {
         TableHead th;
         std::memset(&th, 0, sizeof(th));
         th.dtype = t.dtype;
+        th.layout = t.layout;
         th.grid = t.grid;
         th.bytes = t.bytes;
         const uint64_t occ_bytes = t.occ_bytes;
@@ -250,10 +285,13 @@ int load_impl(gmcs_ctx* c, const char* path, bool* touched) {
         if (!in.get(&th, sizeof(th))) return GMCS_E_IO;
         HostTable t;
         t.dtype = th.dtype;
+        t.layout = th.layout;
         t.grid = th.grid;
         t.bytes = th.bytes;
+        t.dir_bytes = (th.dtype != 3 && th.layout == GMCS_LAYOUT_COLUMNS) ? dir_bytes_of(th.grid) : 0;
         buf.resize(t.bytes);
         if (!in.get(buf.data(), t.bytes)) return GMCS_E_IO;
+        if (t.dir_bytes && !directory_ok(buf.data(), th)) return GMCS_E_IO;
         if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
             cudaGetLastError();
             return GMCS_E_OOM;
@@ -279,7 +317,8 @@ int load_impl(gmcs_ctx* c, const char* path, bool* touched) {
         if (!rc) {
             TableDesc td;
             std::memset(&td, 0, sizeof(td));
-            td.cells = t.cells;
+            td.cells = table_records(t);
+            td.dir = table_dir(t);
             td.ox = (float)t.grid.origin[0];
             td.oy = (float)t.grid.origin[1];
             td.oz = (float)t.grid.origin[2];

@@ -25,6 +25,7 @@ constexpr int kMaxNb = 8;
 
 struct TableDesc {
     const void* cells;   // packed cell records
+    const uint2* dir;    // column-sparse tables: per (x, y) column (first record, zlo | count << 16); dense: null
     float ox, oy, oz;    // lattice origin in the keyframe frame
     float inv_h;         // 1 / h
     int ncx, ncy, ncz;   // cells per axis (vertices - 1)
@@ -32,7 +33,7 @@ struct TableDesc {
     float h;
     int pad;
 };
-static_assert(sizeof(TableDesc) == 48, "TableDesc layout");
+static_assert(sizeof(TableDesc) == 56, "TableDesc layout");
 
 // ---------------------------------------------------------------- pose algebra
 
@@ -318,6 +319,21 @@ __device__ __forceinline__ void ld_record32(const float4* p, float4& a, float4& 
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
+}
+
+// Column-sparse tables store, for every (x, y) column of cells, only the cells
+// from the lowest to the highest one whose polynomial is not zero (the field is
+// zero farther than r_t from every keyframe point, so a column holds one short
+// run of cells near the surfaces it crosses); dir[cy * ncx + cx] = (index of the
+// run's first record, zlo | count << 16). A cell outside the run reads as zero.
+// Returns whether (cx, cy, cz) is stored, and its record index.
+__device__ __forceinline__ bool col_cell(const uint2* __restrict__ dir, uint32_t ncx, uint32_t ncy, int cx, int cy,
+                                         int cz, uint32_t& idx) {
+    if (!(((uint32_t)cx < ncx) & ((uint32_t)cy < ncy))) return false;
+    const uint2 d = __ldg(dir + ((uint32_t)cy * ncx + (uint32_t)cx));
+    const uint32_t rel = (uint32_t)cz - (d.y & 0xFFFFu);
+    idx = d.x + rel;
+    return rel < (d.y >> 16);
 }
 
 // The coefficient record of cell `idx` widened to float in record order; zeros

@@ -12,14 +12,22 @@ namespace gmcs {
 enum Kind { K_PREDICT, K_SELECT, K_PASS_GRAD, K_PASS_VALUE, K_FINISH, K_WEIGH, K_RESAMPLE, K_GATHER, K_TABLE, K_MISC, K_COUNT };
 
 struct HostTable {
-    void* cells = nullptr;           // cell records (field) or voxel records (GICP)
-    size_t bytes = 0;
+    void* cells = nullptr;           // the allocation: [column directory][cell records] (field) or voxel records (GICP)
+    size_t bytes = 0;                // allocation size
+    size_t dir_bytes = 0;            // column-sparse field tables: directory bytes (256-byte aligned); dense: 0
+    int layout = 0;                  // GMCS_LAYOUT_*
     gmcs_grid grid;
     int dtype = 0;
     unsigned char* occ = nullptr;   // occupancy lattice for the overlap rate (Sec. III-E)
     gmcs_grid occ_grid;
     size_t occ_bytes = 0;
 };
+
+// First cell record and column directory of a table (dense: no directory).
+inline void* table_records(const HostTable& t) { return static_cast<char*>(t.cells) + t.dir_bytes; }
+inline const uint2* table_dir(const HostTable& t) {
+    return t.dir_bytes ? static_cast<const uint2*>(t.cells) : nullptr;
+}
 
 struct EvPair {
     int kind;

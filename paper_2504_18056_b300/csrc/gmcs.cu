@@ -229,6 +229,7 @@ void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* o
     pa.chunk_len = chunk;
     pa.eps = c->cfg.eps;
     pa.want_ll = (!grad || out_ll) ? 1 : 0;
+    pa.sparse = c->cfg.table_layout == GMCS_LAYOUT_COLUMNS ? 1 : 0;
     FinishArgs fa;
     fa.part = c->part;
     fa.pose = c->pose[c->cur];
@@ -570,7 +571,9 @@ bool config_valid(const gmcs_config* c) {
            c->prune_w >= 0.f && c->prune_w < 1.f && c->prune_lr >= 0.f && c->prune_lr < 1.f &&
            (c->model == GMCS_MODEL_FIELD || c->model == GMCS_MODEL_GICP) && c->knn >= 1 && c->knn <= kKnnMax &&
            c->cov_eps > 0.f && c->cov_eps <= 1.f && c->gicp_tau > 0.f && c->kf_overlap >= 0.f &&
-           c->kf_overlap <= 1.f && c->kf_voxel > 0.f && c->kf_h > 0.f;
+           c->kf_overlap <= 1.f && c->kf_voxel > 0.f && c->kf_h > 0.f &&
+           (c->table_layout == GMCS_LAYOUT_DENSE ||
+            (c->table_layout == GMCS_LAYOUT_COLUMNS && c->model == GMCS_MODEL_FIELD));
 }
 
 }  // namespace gmcs
@@ -850,7 +853,8 @@ int register_keyframe(gmcs_ctx* c, HostTable& t, const gmcs_grid* grid, int ncx,
     }
     TableDesc td;
     std::memset(&td, 0, sizeof(td));
-    td.cells = t.cells;
+    td.cells = table_records(t);
+    td.dir = table_dir(t);
     td.ox = (float)grid->origin[0];
     td.oy = (float)grid->origin[1];
     td.oz = (float)grid->origin[2];
@@ -946,6 +950,60 @@ int add_keyframe_gicp(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
 
 }  // namespace
 
+namespace {
+
+// Column-sparse layout of a table whose squared distances are in c->d2: the
+// per-column runs (device), read back to build the directory of first-record
+// offsets on the host; allocates the table (directory, then the records) into t.
+int build_columns(gmcs_ctx* c, HostTable& t, int nx, int ny, int nz, float inv_two_sigma2, float r_t2, size_t rec) {
+    const size_t ncol = (size_t)(nx - 1) * (ny - 1);
+    uint32_t* d_run = nullptr;
+    if (cudaMalloc((void**)&d_run, ncol * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return GMCS_E_OOM;
+    }
+    {
+        Launch L(c, K_TABLE);
+        launch_col_range(c->d2, nx, ny, nz, inv_two_sigma2, r_t2, d_run, c->stream);
+    }
+    int rc = check_launch();
+    std::vector<uint32_t> run;
+    std::vector<uint2> dir;
+    try {
+        run.resize(ncol);
+        dir.resize(ncol);
+    } catch (...) {
+        rc = GMCS_E_OOM;
+    }
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(run.data(), d_run, ncol * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                              c->stream));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    cudaFree(d_run);
+    if (rc) return rc;
+    uint64_t total = 0;
+    for (size_t k = 0; k < ncol; ++k) {
+        dir[k] = make_uint2((uint32_t)total, run[k]);
+        total += run[k] >> 16;
+    }
+    if (total >= ((uint64_t)1 << 31)) return GMCS_E_INVALID;
+    t.dir_bytes = (ncol * sizeof(uint2) + 255) / 256 * 256;   // records start 256-byte aligned
+    t.bytes = t.dir_bytes + (size_t)std::max<uint64_t>(total, 1) * rec;
+    if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        t.cells = nullptr;
+        return GMCS_E_OOM;
+    }
+    rc = cuda_status(cudaMemcpyAsync(t.cells, dir.data(), ncol * sizeof(uint2), cudaMemcpyHostToDevice, c->stream));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));   // dir lives on this stack frame
+    if (rc) {
+        cudaFree(t.cells);
+        t.cells = nullptr;
+    }
+    return rc;
+}
+
+}  // namespace
+
 int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* grid, const float* kf_poses, int* kf_id) {
     if (!c || !grid || n < 0 || (n > 0 && !pts)) return GMCS_E_INVALID;
     if (!c->have_particles) return GMCS_E_STATE;
@@ -954,6 +1012,8 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     for (int a = 0; a < 3; ++a)   // the lookup's floor is exact below 2^22 cells per axis
         if (grid->n[a] < 2 || grid->n[a] > (1 << 22) || !std::isfinite(grid->origin[a])) return GMCS_E_INVALID;
     if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return GMCS_E_INVALID;
+    const bool cols = c->cfg.table_layout == GMCS_LAYOUT_COLUMNS;
+    if (cols && grid->n[2] > 65536) return GMCS_E_INVALID;   // a column run is 16-bit
     const size_t nx = grid->n[0], ny = grid->n[1], nz = grid->n[2];
     const size_t nv = nx * ny * nz;
     const size_t ncell = (nx - 1) * (ny - 1) * (nz - 1);
@@ -963,11 +1023,7 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
     HostTable t;
     t.grid = *grid;
     t.dtype = dtype;
-    t.bytes = ncell * rec;
-    if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return GMCS_E_OOM;
-    }
+    t.layout = cols ? GMCS_LAYOUT_COLUMNS : GMCS_LAYOUT_DENSE;
     // squared-distance scratch, grown to the largest table seen
     if (c->d2_cap < nv) {
         if (c->d2) {
@@ -979,29 +1035,32 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
         }
         if (cudaMalloc((void**)&c->d2, nv * sizeof(unsigned)) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(t.cells);
             return GMCS_E_OOM;
         }
         c->d2_cap = nv;
         c->dev_bytes += nv * sizeof(unsigned);
     }
-    // points: device pointer used in place, host points staged (grows the stage if needed)
+    // points: device pointer used in place, host points staged
     const float* dpts = pts;
     float* tmp = nullptr;
     if (n > 0 && !is_device_ptr(pts)) {
         if (cudaMalloc((void**)&tmp, sizeof(float) * 3 * (size_t)n) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(t.cells);
             return GMCS_E_OOM;
         }
         if (cudaMemcpyAsync(tmp, pts, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
             cudaFree(tmp);
-            cudaFree(t.cells);
             return GMCS_E_CUDA;
         }
         dpts = tmp;
     }
-    int rc = GMCS_OK;
+    auto release_tmp = [&]() {
+        if (tmp) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(tmp);
+            tmp = nullptr;
+        }
+    };
     {
         Launch L(c, K_TABLE);
         launch_fill_u32(c->d2, nv, 0x7f800000u, c->stream);
@@ -1024,33 +1083,47 @@ int gmcs_add_keyframe(gmcs_ctx* c, const float* pts, int n, const gmcs_grid* gri
         Launch L(c, K_TABLE);
         launch_splat(sa, c->stream);
     }
+    int rc = check_launch();
+    const float inv_two_sigma2 = 1.0f / (2.0f * c->cfg.sigma * c->cfg.sigma);
+    const float r_t2 = c->cfg.r_t * c->cfg.r_t;
+    if (!rc) {
+        if (cols) {
+            rc = build_columns(c, t, (int)nx, (int)ny, (int)nz, inv_two_sigma2, r_t2, rec);
+        } else {
+            t.bytes = ncell * rec;
+            if (cudaMalloc(&t.cells, t.bytes) != cudaSuccess) {
+                cudaGetLastError();
+                t.cells = nullptr;
+                rc = GMCS_E_OOM;
+            }
+        }
+    }
+    if (rc) {
+        release_tmp();
+        return rc;
+    }
     PackArgs pa;
     pa.d2 = c->d2;
     pa.nx = (int)nx;
     pa.ny = (int)ny;
     pa.nz = (int)nz;
-    pa.inv_two_sigma2 = 1.0f / (2.0f * c->cfg.sigma * c->cfg.sigma);
-    pa.r_t2 = c->cfg.r_t * c->cfg.r_t;
-    pa.cells = t.cells;
+    pa.inv_two_sigma2 = inv_two_sigma2;
+    pa.r_t2 = r_t2;
+    pa.cells = table_records(t);
     pa.dtype = dtype;
+    pa.dir = table_dir(t);
     {
         Launch L(c, K_TABLE);
         launch_pack(pa, c->stream);
     }
     rc = check_launch();
     if (rc) {
-        if (tmp) {
-            cudaStreamSynchronize(c->stream);
-            cudaFree(tmp);
-        }
+        release_tmp();
         cudaFree(t.cells);
         return rc;
     }
     rc = register_keyframe(c, t, grid, (int)nx - 1, (int)ny - 1, (int)nz - 1, kf_poses, kf_id, dpts, n);
-    if (tmp) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(tmp);
-    }
+    release_tmp();
     return rc;
 }
 
@@ -1564,7 +1637,7 @@ int gmcs_get_table(gmcs_ctx* c, int k, float* vals) {
     }
     {
         Launch L(c, K_MISC);
-        launch_unpack(t.cells, t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], dst, c->stream);
+        launch_unpack(table_records(t), table_dir(t), t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], dst, c->stream);
     }
     int rc = check_launch();
     if (!rc && !dev) rc = copy_out(c, vals, dst, nv * sizeof(float));
@@ -1587,7 +1660,8 @@ int gmcs_get_records(gmcs_ctx* c, int k, uint64_t c0, uint64_t n, float* coef) {
     }
     {
         Launch L(c, K_MISC);
-        launch_records(t.cells, t.dtype, c0, n, dst, c->stream);
+        launch_records(table_records(t), table_dir(t), t.dtype, t.grid.n[0], t.grid.n[1], t.grid.n[2], c0, n, dst,
+                       c->stream);
     }
     int rc = check_launch();
     if (!rc && !dev) rc = copy_out(c, coef, dst, n * 8 * sizeof(float));

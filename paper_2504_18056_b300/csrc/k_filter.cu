@@ -301,26 +301,33 @@ __device__ __forceinline__ void coef_interp(const float* r, float fx, float fy, 
 }
 
 template <int DT, bool GRAD, bool PROD = false>
-__device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
+__device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, const uint2* __restrict__ dir,
+                                            uint32_t ncx, uint32_t ncy, uint32_t ncz,
                                             int cx, int cy, int cz, float fx, float fy, float fz, float eps,
                                             float& lsum, float& w, float& gx, float& gy, float& gz) {
-    const bool valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-    const uint32_t idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
+    bool valid;
+    uint32_t idx = 0u;
+    if (dir) {
+        valid = col_cell(dir, ncx, ncy, cx, cy, cz, idx);
+    } else {
+        valid = ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+        idx = valid ? ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx : 0u;
+    }
     float v[8];
     load_cell<DT>(cells, idx, valid, v);
     coef_interp<GRAD, PROD>(v, fx, fy, fz, eps, lsum, w, gx, gy, gz);
 }
 
 template <int DT, bool GRAD, bool PROD = false>
-__device__ __forceinline__ void lookup_one(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
-                                           float ux, float uy, float uz, float eps, float& lsum, float& w,
-                                           float& gx, float& gy, float& gz) {
+__device__ __forceinline__ void lookup_one(const void* __restrict__ cells, const uint2* __restrict__ dir, uint32_t ncx,
+                                           uint32_t ncy, uint32_t ncz, float ux, float uy, float uz, float eps,
+                                           float& lsum, float& w, float& gx, float& gy, float& gz) {
     // floor on the FMA/ALU pipes (FP32 gradient pass 2.08 -> 2.01 ms)
     float flx, fly, flz;
     const int cx = floor_split(ux, flx);
     const int cy = floor_split(uy, fly);
     const int cz = floor_split(uz, flz);
-    lookup_cell<DT, GRAD, PROD>(cells, ncx, ncy, ncz, cx, cy, cz, ux - flx, uy - fly, uz - flz, eps, lsum, w, gx, gy,
+    lookup_cell<DT, GRAD, PROD>(cells, dir, ncx, ncy, ncz, cx, cy, cz, ux - flx, uy - fly, uz - flz, eps, lsum, w, gx, gy,
                                 gz);
 }
 
@@ -336,6 +343,7 @@ __device__ __forceinline__ float2 p2_add_rm(float2 a, float2 b) {
 struct Slot {
     float A00, A01, A02, A10, A11, A12, A20, A21, A22, b0, b1, b2;
     const void* cells;
+    const uint2* dir;    // column-sparse table: its column directory (dense: null)
     uint32_t ncx, ncy, ncz;
 };
 
@@ -352,6 +360,7 @@ __device__ __forceinline__ Slot make_slot(const PassArgs& a, int i, int k, const
     s.b1 = (rel[7] - td.oy) * td.inv_h;
     s.b2 = (rel[11] - td.oz) * td.inv_h;
     s.cells = td.cells;
+    s.dir = td.dir;
     s.ncx = (uint32_t)td.ncx;
     s.ncy = (uint32_t)td.ncy;
     s.ncz = (uint32_t)td.ncz;
@@ -410,7 +419,7 @@ __global__ void __launch_bounds__(kPassThreads, GMCS_PASS_MINBLOCKS) k_pass(Pass
                 const float uy = fmaf(sl.A10, p.x, fmaf(sl.A11, p.y, fmaf(sl.A12, p.z, sl.b1)));
                 const float uz = fmaf(sl.A20, p.x, fmaf(sl.A21, p.y, fmaf(sl.A22, p.z, sl.b2)));
                 float w, gx, gy, gz;
-                lookup_one<DT, GRAD>(sl.cells, sl.ncx, sl.ncy, sl.ncz, ux, uy, uz, eps, lsum, w, gx, gy, gz);
+                lookup_one<DT, GRAD>(sl.cells, sl.dir, sl.ncx, sl.ncy, sl.ncz, ux, uy, uz, eps, lsum, w, gx, gy, gz);
                 if constexpr (GRAD) {
                     Gx += gx; Gy += gy; Gz += gz;
                     Cx = fmaf(uy, gz, fmaf(-uz, gy, Cx));
@@ -488,13 +497,13 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
                     const float2 f2 = p2_sub(uxy, p2_sub(t2, C2));
                     float flz;
                     const int cz = floor_split(uz, flz);
-                    lookup_cell<DT, GRAD, kProd>(sl[s].cells, sl[s].ncx, sl[s].ncy, sl[s].ncz,
+                    lookup_cell<DT, GRAD, kProd>(sl[s].cells, sl[s].dir, sl[s].ncx, sl[s].ncy, sl[s].ncz,
                                           __float_as_int(t2.x) - 0x4B400000, __float_as_int(t2.y) - 0x4B400000, cz,
                                           f2.x, f2.y, uz - flz, eps, lacc, w, gx, gy, gz);
                 } else {
                     ux = fmaf(sl[s].A00, p.x, fmaf(sl[s].A01, p.y, fmaf(sl[s].A02, p.z, sl[s].b0)));
                     uy = fmaf(sl[s].A10, p.x, fmaf(sl[s].A11, p.y, fmaf(sl[s].A12, p.z, sl[s].b1)));
-                    lookup_one<DT, GRAD, kProd>(sl[s].cells, sl[s].ncx, sl[s].ncy, sl[s].ncz, ux, uy,
+                    lookup_one<DT, GRAD, kProd>(sl[s].cells, sl[s].dir, sl[s].ncx, sl[s].ncy, sl[s].ncz, ux, uy,
                                                               uz, eps, lacc, w, gx, gy, gz);
                 }
                 if constexpr (GRAD) {
@@ -619,11 +628,19 @@ struct RawRec<0> {
 // stored before cell 0 instead, with no predicate, cost the FP32 gradient pass
 // 1.57 -> 1.69 ms: the extra sector in many warp requests; taking the sign of
 // a -1 index as the predicate cost 1.57 -> 2.12 ms.)
-template <int DT>
-__device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, uint32_t ncx, uint32_t ncy, uint32_t ncz,
-                                          int cx, int cy, int cz, bool live, RawRec<DT>& r) {
-    const bool valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
-    const uint32_t idx = ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx;   // used only when valid
+template <int DT, bool SP = false>
+__device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, const uint2* __restrict__ dir, uint32_t ncx,
+                                          uint32_t ncy, uint32_t ncz, int cx, int cy, int cz, bool live,
+                                          RawRec<DT>& r) {
+    bool valid;
+    uint32_t idx;
+    if constexpr (SP) {
+        // column-sparse: the record index comes from the column's directory entry
+        valid = live && col_cell(dir, ncx, ncy, cx, cy, cz, idx);
+    } else {
+        valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
+        idx = ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx;   // used only when valid
+    }
     if constexpr (DT == 0) {
         r.a = make_float4(0.f, 0.f, 0.f, 0.f);
         r.b = r.a;
@@ -687,7 +704,7 @@ __device__ __forceinline__ void moments_store(const Moments& m, float* acc) {
 
 // LL: the gradient pass also accumulates the log-likelihood (a caller asked for
 // it); the moves of a frame need only the gradient and the moments.
-template <int DT, bool GRAD, bool LL = true>
+template <int DT, bool GRAD, bool LL = true, bool SP = false>
 __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
     constexpr int NACC = GRAD ? kAccGrad : 1;
     constexpr bool kLL = LL || !GRAD;
@@ -701,6 +718,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
     if (i < a.P && j0 < j1) {
         Xf xf[3];
         const void* cells[3];
+        const uint2* dirs[3];
         uint32_t ncx[3], ncy[3], ncz[3];
         int ks[3];
         {
@@ -712,6 +730,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 const Slot sl = make_slot(a, i, ks[s], Tt);
                 xf[s] = slot_xf(sl);
                 cells[s] = sl.cells;
+                dirs[s] = sl.dir;
                 ncx[s] = sl.ncx; ncy[s] = sl.ncy; ncz[s] = sl.ncz;
             }
         }
@@ -732,7 +751,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 int cx, cy, cz;
                 slot_point<DT, true>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0],
                                       st.f[s][1], st.f[s][2]);
-                fetch_raw<DT>(cells[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
+                fetch_raw<DT, SP>(cells[s], dirs[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
             }
         };
         auto use = [&](const Stage<DT>& st) {
@@ -818,7 +837,7 @@ struct SlotStage {
     RawRec<DT> r;
 };
 
-template <int DT, bool GRAD, bool LL = true>
+template <int DT, bool GRAD, bool LL = true, bool SP = false>
 __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
     constexpr int NACC = GRAD ? kAccGrad : 1;
     constexpr bool kLL = LL || !GRAD;
@@ -832,6 +851,7 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
     if (i < a.P && j0 < j1) {
         Xf xf[3];
         const void* cells[3];
+        const uint2* dirs[3];
         uint32_t ncx[3], ncy[3], ncz[3];
         {
             float Tt[12];
@@ -841,6 +861,7 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
                 const Slot sl = make_slot(a, i, a.nbr[(size_t)s * a.ld + i], Tt);
                 xf[s] = slot_xf(sl);
                 cells[s] = sl.cells;
+                dirs[s] = sl.dir;
                 ncx[s] = sl.ncx; ncy[s] = sl.ncy; ncz[s] = sl.ncz;
             }
         }
@@ -857,7 +878,7 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
         auto issue = [&](SlotStage<DT>& st, float4 p, int s, bool live) {
             int cx, cy, cz;
             slot_point<DT, true>(xf[s], p, st.u[0], st.u[1], st.u[2], cx, cy, cz, st.f[0], st.f[1], st.f[2]);
-            fetch_raw<DT>(cells[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r);
+            fetch_raw<DT, SP>(cells[s], dirs[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r);
         };
         // interpolate one slot of a point; returns its weight (gradient pass)
         auto use = [&](const SlotStage<DT>& st, int s, float& lprod) -> float {
@@ -937,16 +958,16 @@ constexpr int pass3_minblocks() {
                 : (DT == 0 ? GMCS_VALUE_MINBLOCKS : GMCS_VALUE_MINBLOCKS16);
 }
 
-template <int DT, bool GRAD, int UNROLL, bool LL = true>
+template <int DT, bool GRAD, int UNROLL, bool LL = true, bool SP = false>
 __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
-    if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>()) pass3q_body<DT, GRAD, LL>(a, vb);
-    else if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL>(a, vb);
+    if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>()) pass3q_body<DT, GRAD, LL, SP>(a, vb);
+    else if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL, SP>(a, vb);
     else pass3_body<DT, GRAD, UNROLL>(a, vb);
 }
 
-template <int DT, bool GRAD, int UNROLL, bool LL = true>
+template <int DT, bool GRAD, int UNROLL, bool LL = true, bool SP = false>
 __global__ void __launch_bounds__(kPassThreads, pass3_minblocks<DT, GRAD>()) k_pass3(PassArgs a) {
-    pass3_any<DT, GRAD, UNROLL, LL>(a, blockIdx.x);
+    pass3_any<DT, GRAD, UNROLL, LL, SP>(a, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ finish: sums, move (Eq. 5-7)
@@ -1189,9 +1210,9 @@ constexpr int pass3_b_minblocks() {
 }
 
 // served frames never ask the gradient passes for the log-likelihood
-template <int DT, bool GRAD, int UNROLL>
+template <int DT, bool GRAD, int UNROLL, bool SP = false>
 __global__ void __launch_bounds__(kPassThreads, pass3_b_minblocks<DT, GRAD>()) k_pass3_b(const BatchList<PassArgs>* L) {
-    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_any<DT, GRAD, UNROLL, !GRAD>(a, vb)));
+    GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_any<DT, GRAD, UNROLL, !GRAD, SP>(a, vb)));
 }
 
 template <bool GRAD, bool GICP>
@@ -1225,9 +1246,9 @@ static int grid_select_b() {
     static const int g = persistent_grid(k_select_b, 128);
     return g;
 }
-template <int DT, bool G>
+template <int DT, bool G, bool SP>
 static int grid_pass3_b() {
-    static const int g = persistent_grid(k_pass3_b<DT, G, pass3_unroll<DT, G>()>, kPassThreads);
+    static const int g = persistent_grid(k_pass3_b<DT, G, pass3_unroll<DT, G>(), SP>, kPassThreads);
     return g;
 }
 template <bool G, bool GICP>
@@ -1246,17 +1267,23 @@ void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s) {
     k_select_b<<<grid_select_b(), 128, 0, s>>>(L);
 }
 
-template <int DT, bool G>
+template <int DT, bool G, bool SP>
 static void pass3_b(const BatchList<PassArgs>* L, cudaStream_t s) {
-    k_pass3_b<DT, G, pass3_unroll<DT, G>()><<<grid_pass3_b<DT, G>(), kPassThreads, 0, s>>>(L);
+    k_pass3_b<DT, G, pass3_unroll<DT, G>(), SP><<<grid_pass3_b<DT, G, SP>(), kPassThreads, 0, s>>>(L);
 }
 
-void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStream_t s) {
+template <bool SP>
+static void pass3_b_any(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStream_t s) {
     if (grad) {
-        if (dtype == 0) pass3_b<0, true>(L, s); else if (dtype == 1) pass3_b<1, true>(L, s); else pass3_b<2, true>(L, s);
+        if (dtype == 0) pass3_b<0, true, SP>(L, s); else if (dtype == 1) pass3_b<1, true, SP>(L, s); else pass3_b<2, true, SP>(L, s);
     } else {
-        if (dtype == 0) pass3_b<0, false>(L, s); else if (dtype == 1) pass3_b<1, false>(L, s); else pass3_b<2, false>(L, s);
+        if (dtype == 0) pass3_b<0, false, SP>(L, s); else if (dtype == 1) pass3_b<1, false, SP>(L, s); else pass3_b<2, false, SP>(L, s);
     }
+}
+
+void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, bool sparse, cudaStream_t s) {
+    if (sparse) pass3_b_any<true>(L, dtype, grad, s);
+    else pass3_b_any<false>(L, dtype, grad, s);
 }
 
 void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, bool gicp, cudaStream_t s) {
@@ -1274,12 +1301,18 @@ void prepare_filter_batched() {
     grid_scan_pack_b();
     grid_predict_b();
     grid_select_b();
-    grid_pass3_b<0, true>();
-    grid_pass3_b<1, true>();
-    grid_pass3_b<2, true>();
-    grid_pass3_b<0, false>();
-    grid_pass3_b<1, false>();
-    grid_pass3_b<2, false>();
+    grid_pass3_b<0, true, false>();
+    grid_pass3_b<1, true, false>();
+    grid_pass3_b<2, true, false>();
+    grid_pass3_b<0, false, false>();
+    grid_pass3_b<1, false, false>();
+    grid_pass3_b<2, false, false>();
+    grid_pass3_b<0, true, true>();
+    grid_pass3_b<1, true, true>();
+    grid_pass3_b<2, true, true>();
+    grid_pass3_b<0, false, true>();
+    grid_pass3_b<1, false, true>();
+    grid_pass3_b<2, false, true>();
     grid_finish_b<true, false>();
     grid_finish_b<false, false>();
     grid_finish_b<true, true>();
@@ -1331,9 +1364,11 @@ void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s) {
     if (grid <= 0) return;
     // three neighbours (every particle then has all three slots filled): the fused kernel
     const bool three = GMCS_PASS3 && a.k_nb == 3;
-#define GMCS_PASS(DT, G)                                                                            \
-    (three ? ((G && !a.want_ll) ? k_pass3<DT, G, pass3_unroll<DT, G>(), false><<<grid, kPassThreads, 0, s>>>(a) \
-                                : k_pass3<DT, G, pass3_unroll<DT, G>(), true><<<grid, kPassThreads, 0, s>>>(a)) \
+#define GMCS_PASS3(DT, G, SP)                                                                                   \
+    ((G && !a.want_ll) ? k_pass3<DT, G, pass3_unroll<DT, G>(), false, SP><<<grid, kPassThreads, 0, s>>>(a)     \
+                       : k_pass3<DT, G, pass3_unroll<DT, G>(), true, SP><<<grid, kPassThreads, 0, s>>>(a))
+#define GMCS_PASS(DT, G)                                                                                        \
+    (three ? (a.sparse ? GMCS_PASS3(DT, G, true) : GMCS_PASS3(DT, G, false))                                   \
            : k_pass<DT, G><<<grid, kPassThreads, 0, s>>>(a))
     if (grad) {
         if (dtype == 0) GMCS_PASS(0, true); else if (dtype == 1) GMCS_PASS(1, true); else GMCS_PASS(2, true);
@@ -1341,6 +1376,7 @@ void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s) {
         if (dtype == 0) GMCS_PASS(0, false); else if (dtype == 1) GMCS_PASS(1, false); else GMCS_PASS(2, false);
     }
 #undef GMCS_PASS
+#undef GMCS_PASS3
 }
 
 void launch_finish(const FinishArgs& a, bool grad, cudaStream_t s) {

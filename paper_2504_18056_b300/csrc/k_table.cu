@@ -71,72 +71,136 @@ __device__ __forceinline__ float field_value(unsigned bits, float inv_two_sigma2
     return (d2 <= r_t2) ? expf(-d2 * inv_two_sigma2) : 0.0f;
 }
 
-// One thread per cell: 8 corner values -> the coefficients of the cell's
-// trilinear polynomial, one record (FP32, or encoded as a 16-bit record).
+// The 8 corner values of cell (cx, cy, cz) -> its coefficient record at `out`.
+__device__ __forceinline__ void pack_cell(const PackArgs& a, int cx, int cy, int cz, size_t out) {
+    float v[8];
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const size_t vi = ((size_t)(cz + dz) * a.ny + (cy + dy)) * a.nx + (cx + dx);
+                v[rec_slot(dx, dy, dz)] = field_value(a.d2[vi], a.inv_two_sigma2, a.r_t2);
+            }
+    float r[8];
+    corners_to_coef(v, r);
+    if (a.dtype == 0) {
+        float4* o = reinterpret_cast<float4*>(a.cells) + 2 * out;
+        o[0] = make_float4(r[0], r[1], r[2], r[3]);
+        o[1] = make_float4(r[4], r[5], r[6], r[7]);
+    } else {
+        reinterpret_cast<uint4*>(a.cells)[out] = encode_rec16(r, a.dtype);
+    }
+}
+
+// Dense tables: one thread per cell. Column-sparse tables: one thread per (x, y)
+// column, packing the cells of its run.
 __global__ void k_pack(PackArgs a) {
     const int ncx = a.nx - 1, ncy = a.ny - 1, ncz = a.nz - 1;
+    if (a.dir) {
+        const size_t ncol = (size_t)ncx * ncy;
+        for (size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x; col < ncol; col += (size_t)gridDim.x * blockDim.x) {
+            const uint2 d = a.dir[col];
+            const int cx = (int)(col % ncx), cy = (int)(col / ncx);
+            const int zlo = (int)(d.y & 0xFFFFu), cnt = (int)(d.y >> 16);
+            for (int k = 0; k < cnt; ++k) pack_cell(a, cx, cy, zlo + k, (size_t)d.x + k);
+        }
+        return;
+    }
     const size_t ncell = (size_t)ncx * ncy * ncz;
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < ncell; c += (size_t)gridDim.x * blockDim.x) {
         const int cx = (int)(c % ncx);
         const int cy = (int)((c / ncx) % ncy);
         const int cz = (int)(c / ((size_t)ncx * ncy));
-        float v[8];
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx)
+        pack_cell(a, cx, cy, cz, c);
+    }
+}
+
+// Column-sparse tables: per (x, y) column, the run from its lowest to its highest
+// cell with a nonzero corner value, as zlo | count << 16 (count 0: empty column).
+__global__ void k_col_range(const unsigned* __restrict__ d2, int nx, int ny, int nz, float inv_two_sigma2,
+                            float r_t2, uint32_t* __restrict__ out) {
+    const int ncx = nx - 1, ncy = ny - 1, ncz = nz - 1;
+    const size_t ncol = (size_t)ncx * ncy;
+    for (size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x; col < ncol; col += (size_t)gridDim.x * blockDim.x) {
+        const int cx = (int)(col % ncx), cy = (int)(col / ncx);
+        // vertex layer iz of the column is nonzero if any of its 4 vertices is
+        int lo = -1, hi = -2;
+        bool prev = false;
+        for (int iz = 0; iz < nz; ++iz) {
+            bool nzv = false;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-                for (int dz = 0; dz < 2; ++dz) {
-                    const size_t vi = ((size_t)(cz + dz) * a.ny + (cy + dy)) * a.nx + (cx + dx);
-                    v[rec_slot(dx, dy, dz)] = field_value(a.d2[vi], a.inv_two_sigma2, a.r_t2);
+                for (int dx = 0; dx < 2; ++dx) {
+                    const size_t vi = ((size_t)iz * ny + (cy + dy)) * nx + (cx + dx);
+                    nzv |= field_value(d2[vi], inv_two_sigma2, r_t2) > 0.f;
                 }
-        float r[8];
-        corners_to_coef(v, r);
-        if (a.dtype == 0) {
-            float4* out = reinterpret_cast<float4*>(a.cells) + 2 * c;
-            out[0] = make_float4(r[0], r[1], r[2], r[3]);
-            out[1] = make_float4(r[4], r[5], r[6], r[7]);
-        } else {
-            reinterpret_cast<uint4*>(a.cells)[c] = encode_rec16(r, a.dtype);
+            // cell iz - 1 (vertex layers iz - 1, iz) and cell iz (layers iz, iz + 1)
+            if (nzv) {
+                const int c0 = iz > 0 ? iz - 1 : 0, c1 = iz < ncz ? iz : ncz - 1;
+                if (lo < 0) lo = c0;
+                hi = c1;
+            }
+            prev = nzv;
         }
+        (void)prev;
+        out[col] = lo < 0 ? 0u : ((uint32_t)lo | ((uint32_t)(hi - lo + 1) << 16));
+    }
+}
+
+// The coefficients (record order) of cell (cx, cy, cz) as stored; zeros for a cell
+// a column-sparse table does not store.
+__device__ __forceinline__ void read_cell(const void* __restrict__ cells, const uint2* __restrict__ dir, int dtype,
+                                          int ncx, int ncy, int cx, int cy, int cz, float* r) {
+    size_t c;
+    if (dir) {
+        uint32_t idx;
+        if (!col_cell(dir, (uint32_t)ncx, (uint32_t)ncy, cx, cy, cz, idx)) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = 0.f;
+            return;
+        }
+        c = idx;
+    } else {
+        c = ((size_t)cz * ncy + cy) * ncx + cx;
+    }
+    if (dtype == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = reinterpret_cast<const float*>(cells)[8 * c + k];
+    } else if (dtype == 1) {
+        decode_rec16<1>(reinterpret_cast<const uint4*>(cells)[c], r);
+    } else {
+        decode_rec16<2>(reinterpret_cast<const uint4*>(cells)[c], r);
     }
 }
 
 // Vertex values read back from the cell records (vertex i lives in cell
 // min(i, nc-1), at its corner; the sum of the stored coefficients).
-__global__ void k_unpack(const void* __restrict__ cells, int dtype, int nx, int ny, int nz, float* __restrict__ out) {
+__global__ void k_unpack(const void* __restrict__ cells, const uint2* __restrict__ dir, int dtype, int nx, int ny,
+                         int nz, float* __restrict__ out) {
     const size_t nv = (size_t)nx * ny * nz;
     const int ncx = nx - 1, ncy = ny - 1, ncz = nz - 1;
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
         const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((size_t)nx * ny));
         const int cx = min(ix, ncx - 1), cy = min(iy, ncy - 1), cz = min(iz, ncz - 1);
-        const size_t c = ((size_t)cz * ncy + cy) * ncx + cx;
         float r[8];
-        if (dtype == 0) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) r[e] = reinterpret_cast<const float*>(cells)[8 * c + e];
-        } else if (dtype == 1) {
-            decode_rec16<1>(reinterpret_cast<const uint4*>(cells)[c], r);
-        } else {
-            decode_rec16<2>(reinterpret_cast<const uint4*>(cells)[c], r);
-        }
+        read_cell(cells, dir, dtype, ncx, ncy, cx, cy, cz, r);
         out[v] = coef_corner(r, ix - cx, iy - cy, iz - cz);
     }
 }
 
-// Coefficients c0..c7 (natural order) of cells [c0, c0 + n), as stored.
-__global__ void k_records(const void* __restrict__ cells, int dtype, size_t c0, size_t n, float* __restrict__ out) {
+// Coefficients c0..c7 (natural order) of cells [c0, c0 + n) (numbered x fastest),
+// as stored (zeros for cells a column-sparse table does not store).
+__global__ void k_records(const void* __restrict__ cells, const uint2* __restrict__ dir, int dtype, int nx, int ny,
+                          size_t c0, size_t n, float* __restrict__ out) {
+    const int ncx = nx - 1, ncy = ny - 1;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const size_t c = c0 + e;
+        const int cx = (int)(c % ncx), cy = (int)((c / ncx) % ncy), cz = (int)(c / ((size_t)ncx * ncy));
         float r[8];
-        if (dtype == 0) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) r[k] = reinterpret_cast<const float*>(cells)[8 * c + k];
-        } else if (dtype == 1) {
-            decode_rec16<1>(reinterpret_cast<const uint4*>(cells)[c], r);
-        } else {
-            decode_rec16<2>(reinterpret_cast<const uint4*>(cells)[c], r);
-        }
+        read_cell(cells, dir, dtype, ncx, ncy, cx, cy, cz, r);
 #pragma unroll
         for (int k = 0; k < 8; ++k) out[8 * e + k] = r[coef_slot(k)];
     }
@@ -157,16 +221,23 @@ void launch_splat(const SplatArgs& a, cudaStream_t s) {
 }
 
 void launch_pack(const PackArgs& a, cudaStream_t s) {
-    const size_t ncell = (size_t)(a.nx - 1) * (a.ny - 1) * (a.nz - 1);
-    k_pack<<<grid_for(ncell, 256), 256, 0, s>>>(a);
+    const size_t n = a.dir ? (size_t)(a.nx - 1) * (a.ny - 1) : (size_t)(a.nx - 1) * (a.ny - 1) * (a.nz - 1);
+    k_pack<<<grid_for(n, 256), 256, 0, s>>>(a);
 }
 
-void launch_unpack(const void* cells, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s) {
-    k_unpack<<<grid_for((size_t)nx * ny * nz, 256), 256, 0, s>>>(cells, dtype, nx, ny, nz, out);
+void launch_col_range(const unsigned* d2, int nx, int ny, int nz, float inv_two_sigma2, float r_t2, uint32_t* out,
+                      cudaStream_t s) {
+    k_col_range<<<grid_for((size_t)(nx - 1) * (ny - 1), 256), 256, 0, s>>>(d2, nx, ny, nz, inv_two_sigma2, r_t2, out);
 }
 
-void launch_records(const void* cells, int dtype, size_t c0, size_t n, float* out, cudaStream_t s) {
-    if (n > 0) k_records<<<grid_for(n, 256), 256, 0, s>>>(cells, dtype, c0, n, out);
+void launch_unpack(const void* cells, const uint2* dir, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s) {
+    k_unpack<<<grid_for((size_t)nx * ny * nz, 256), 256, 0, s>>>(cells, dir, dtype, nx, ny, nz, out);
+}
+
+void launch_records(const void* cells, const uint2* dir, int dtype, int nx, int ny, int nz, size_t c0, size_t n,
+                    float* out, cudaStream_t s) {
+    (void)nz;
+    if (n > 0) k_records<<<grid_for(n, 256), 256, 0, s>>>(cells, dir, dtype, nx, ny, c0, n, out);
 }
 
 }  // namespace gmcs

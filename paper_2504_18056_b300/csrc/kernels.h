@@ -39,13 +39,18 @@ struct PackArgs {
     float r_t2;
     void* cells;
     int dtype;
+    const uint2* dir;       // column-sparse: the column directory (dense: null)
 };
 
 void launch_fill_u32(unsigned* p, size_t n, unsigned v, cudaStream_t s);
 void launch_splat(const SplatArgs& a, cudaStream_t s);
 void launch_pack(const PackArgs& a, cudaStream_t s);
-void launch_unpack(const void* cells, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s);
-void launch_records(const void* cells, int dtype, size_t c0, size_t n, float* out, cudaStream_t s);
+void launch_unpack(const void* cells, const uint2* dir, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s);
+void launch_records(const void* cells, const uint2* dir, int dtype, int nx, int ny, int nz, size_t c0, size_t n,
+                    float* out, cudaStream_t s);
+// column-sparse tables: per column (zlo | count << 16) of its nonzero run, from the squared distances
+void launch_col_range(const unsigned* d2, int nx, int ny, int nz, float inv_two_sigma2, float r_t2, uint32_t* out,
+                      cudaStream_t s);
 
 // ------------------------------------------------------------------ filter
 struct ScanPackArgs {
@@ -90,6 +95,7 @@ struct PassArgs {
     int ntiles, groups, chunk_len;   // groups: chunk groups (kPassCW chunks each)
     float eps;
     int want_ll;            // gradient pass: also accumulate the log-likelihood (the moves do not need it)
+    int sparse;             // the context's tables are column-sparse (TableDesc::dir)
 };
 
 struct FinishArgs {
@@ -313,7 +319,7 @@ struct BatchList {
 void launch_scan_pack_b(const BatchList<ScanPackArgs>* L, cudaStream_t s);
 void launch_predict_b(const BatchList<PredictArgs>* L, cudaStream_t s);
 void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s);
-void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, cudaStream_t s);
+void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, bool sparse, cudaStream_t s);
 void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, bool gicp, cudaStream_t s);
 void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s);
 void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s);

@@ -164,11 +164,11 @@ int capture_graph(gmcs_server* s, TickSet& t) {
     launch_select_b(&d->sel, st);
     for (int k = 0; k < s->cfg.steps; ++k) {
         if (gicp) launch_gicp_b(&d->pgrad, true, st);
-        else launch_pass3_b(&d->pgrad, s->cfg.table_dtype, true, st);
+        else launch_pass3_b(&d->pgrad, s->cfg.table_dtype, true, s->cfg.table_layout == GMCS_LAYOUT_COLUMNS, st);
         launch_finish_b(&d->fgrad, true, gicp, st);
     }
     if (gicp) launch_gicp_b(&d->pval, false, st);
-    else launch_pass3_b(&d->pval, s->cfg.table_dtype, false, st);
+    else launch_pass3_b(&d->pval, s->cfg.table_dtype, false, s->cfg.table_layout == GMCS_LAYOUT_COLUMNS, st);
     launch_finish_b(&d->fval, false, gicp, st);
     launch_weigh_b(&d->weigh, st);
     if (s->cfg.resample == GMCS_RESAMPLE_PRUNE) {

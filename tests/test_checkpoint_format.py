@@ -22,7 +22,7 @@ class Header(C.Structure):
 
 
 class TableHead(C.Structure):
-    _fields_ = [("dtype", C.c_int32), ("grid", g.Grid), ("bytes", C.c_uint64)]
+    _fields_ = [("dtype", C.c_int32), ("layout", C.c_int32), ("grid", g.Grid), ("bytes", C.c_uint64)]
 
 
 def grid(origin, h, n):
@@ -55,13 +55,26 @@ def write(path, P=5, tables=((0, (4, 3, 2)),), cfg=None, frame=7, tweak=None):
     for dt, n in tables:
         th = TableHead()
         th.dtype = dt
+        th.layout = cfg.table_layout if dt != 3 else 0
         th.grid = grid((0.0, 0.0, 0.0), 0.2, n)
         rec = 48 if dt == 3 else (32 if dt == 0 else 16)
-        cells = int(np.prod(n)) if dt == 3 else int(np.prod([v - 1 for v in n]))
-        th.bytes = cells * rec
+        if th.layout == g.LAYOUT_COLUMNS:
+            # column directory (one run of two cells in every column), then the records
+            ncol = (n[0] - 1) * (n[1] - 1)
+            dirb = (ncol * 8 + 255) // 256 * 256
+            d = np.zeros(dirb // 4, np.uint32)
+            d[0:2 * ncol:2] = np.arange(ncol) * 2          # first record of the column
+            d[1:2 * ncol:2] = 0 | (2 << 16)                # zlo 0, two cells
+            if tweak:
+                tweak("dir", d)
+            body = d.tobytes() + bytes(2 * ncol * rec)
+        else:
+            cells = int(np.prod(n)) if dt == 3 else int(np.prod([v - 1 for v in n]))
+            body = bytes(cells * rec)
+        th.bytes = len(body)
         if tweak:
             tweak("table", th)
-        out += bytes(th) + bytes(cells * rec)
+        out += bytes(th) + body
         og = grid((-1.0, -1.0, -1.0), 1.0, (3, 3, 2))
         occ = 3 * 3 * 2
         if tweak:
@@ -91,11 +104,14 @@ def test_well_formed_file_passes(tmp_path):
         assert g.checkpoint_info(p)[2] == 1
     p = write(tmp_path / "gicp.ckpt", cfg=g.default_config(model=g.MODEL_GICP), tables=((3, (2, 2, 1)),))
     assert g.checkpoint_info(p)[2] == 1
+    p = write(tmp_path / "cols.ckpt", cfg=g.default_config(table_layout=g.LAYOUT_COLUMNS), tables=((0, (5, 4, 6)),))
+    assert g.checkpoint_info(p)[2] == 1
 
 
 @pytest.mark.parametrize("case", ["truncated", "extra_byte", "table_bytes", "table_dims", "huge_bytes",
                                   "dtype_vs_config", "unknown_dtype", "bad_config", "occ_bytes", "bad_grid_h",
-                                  "version", "magic", "negative_K"])
+                                  "version", "magic", "negative_K", "layout_vs_config", "cols_short_records",
+                                  "cols_run_past_lattice", "cols_run_past_records"])
 def test_corrupted_files_are_refused(tmp_path, case):
     p = tmp_path / f"{case}.ckpt"
     tweaks = {
@@ -113,6 +129,22 @@ def test_corrupted_files_are_refused(tmp_path, case):
         write(p, tweak=tweaks[case])
     elif case == "dtype_vs_config":
         write(p, cfg=g.default_config(table_dtype=1), tables=((0, (4, 3, 2)),))
+    elif case == "layout_vs_config":
+        cfg = g.default_config(table_layout=g.LAYOUT_COLUMNS)
+        write(p, cfg=cfg, tables=((0, (5, 4, 6)),), tweak=lambda n, o: setattr(o, "layout", 0) if n == "table" else None)
+    elif case == "cols_short_records":
+        cfg = g.default_config(table_layout=g.LAYOUT_COLUMNS)
+        write(p, cfg=cfg, tables=((0, (5, 4, 6)),), tweak=lambda n, o: setattr(o, "bytes", o.bytes - 16) if n == "table" else None)
+    elif case in ("cols_run_past_lattice", "cols_run_past_records"):
+        cfg = g.default_config(table_layout=g.LAYOUT_COLUMNS)
+
+        def bad_dir(n, o):
+            if n == "dir":
+                if case == "cols_run_past_lattice":
+                    o[1] = 4 | (2 << 16)          # zlo 4 + 2 cells > 5 cells per column
+                else:
+                    o[2 * 11] = 10 ** 6           # a run starting past the last record
+        write(p, cfg=cfg, tables=((0, (5, 4, 6)),), tweak=bad_dir)
     elif case == "bad_config":
         write(p, cfg=g.default_config(k_nb=g.MAX_NB + 1))
     else:

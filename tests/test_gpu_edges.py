@@ -13,14 +13,16 @@ pytestmark = pytest.mark.gpu
 # with K >= 3 the three-neighbour pass runs; P, N chosen so that its warps get point
 # chunks of 1 (N = 1, 3), 9 (N = 97) and 10 points with a last chunk of 1 (N = 301):
 # odd and even chunks end the software-pipelined loop at either of its two exits
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("dtype", [0, 1, 2])
 @pytest.mark.parametrize("P,N,K", [(1, 1, 1), (1, 512, 4), (33, 7, 2), (65, 300, 3), (40, 1, 4), (40, 3, 4),
                                    (65, 301, 4), (130, 97, 4)])
-def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K, dtype):
-    """FP32, BF16 and FP16 coefficient records through the software-pipelined
-    passes, against the oracle on the same stored values."""
+def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K, dtype, layout):
+    """FP32, BF16 and FP16 coefficient records, dense and column-sparse tables,
+    through the software-pipelined passes, against the oracle on the same stored
+    values."""
     kfs = box_room["keyframes"][:K]
-    f = make_filter(box_room, P, dtype=dtype, keyframes=kfs)
+    f = make_filter(box_room, P, dtype=dtype, keyframes=kfs, table_layout=layout)
     tables = [oracle.stored_table(t, dtype) for t in box_room_tables[:K]]
     scan = box_room["scans"][2][:N]
     nbr = gpu_nbr(f, P, min(3, K))

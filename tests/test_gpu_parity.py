@@ -21,9 +21,13 @@ def quantised_tables(box_room_tables):
 
 
 # --------------------------------------------------------------------------- tables
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("dtype", [0, 1, 2])
-def test_tables_match_oracle(box_room, box_room_tables, quantised_tables, dtype):
-    f = make_filter(box_room, 64, dtype)
+def test_tables_match_oracle(box_room, box_room_tables, quantised_tables, dtype, layout):
+    """The stored tables read back (vertex values and cell coefficients) against
+    the oracle's, for the dense and the column-sparse layout (which reads as zero
+    every cell it does not store)."""
+    f = make_filter(box_room, 64, dtype, table_layout=layout)
     ulp = {1: 2.0 ** -7, 2: 2.0 ** -10}
     for k, kf in enumerate(box_room["keyframes"]):
         nx, ny, nz = kf["grid"]["dims"]
@@ -111,10 +115,11 @@ def _check_eval(ll, g, mom, o, scan, label):
     assert strict.mean() >= 0.8, (label, strict.mean())
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("dtype", [0, 1, 2])
-def test_eval_matches_oracle(box_room, box_room_tables, quantised_tables, dtype):
+def test_eval_matches_oracle(box_room, box_room_tables, quantised_tables, dtype, layout):
     P = P_SMALL
-    f = make_filter(box_room, P, dtype)
+    f = make_filter(box_room, P, dtype, table_layout=layout)
     scan = box_room["scans"][0]
     nbr = gpu_nbr(f, P, 3)
     ref_nbr = oracle_nbr(box_room["particles"][:P], box_room["kf_particle_poses"])
