@@ -1359,14 +1359,35 @@ void launch_select(const SelectArgs& a, cudaStream_t s) {
     if (a.P > 0) k_select<<<(a.P + 127) / 128, 128, 0, s>>>(a);
 }
 
+// Shared-memory carveout of the lookup passes, as a percentage of the unified
+// L1/shared storage (-1: the driver's choice). The passes need ~9 KB of shared
+// memory per CTA; the rest of the storage can serve as L1 for the cell records.
+#ifndef GMCS_CARVEOUT
+#define GMCS_CARVEOUT -1
+#endif
+template <typename K>
+static void set_carveout(K kernel) {
+    if (GMCS_CARVEOUT >= 0) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, GMCS_CARVEOUT);
+        cudaGetLastError();
+    }
+}
+
+template <int DT, bool G, int U, bool LL, bool SP>
+static void launch_k_pass3(const PassArgs& a, int grid, cudaStream_t s) {
+    static const bool once = (set_carveout(k_pass3<DT, G, U, LL, SP>), true);
+    (void)once;
+    k_pass3<DT, G, U, LL, SP><<<grid, kPassThreads, 0, s>>>(a);
+}
+
 void launch_pass(const PassArgs& a, int dtype, bool grad, cudaStream_t s) {
     const int grid = grid_pass(a);
     if (grid <= 0) return;
     // three neighbours (every particle then has all three slots filled): the fused kernel
     const bool three = GMCS_PASS3 && a.k_nb == 3;
 #define GMCS_PASS3(DT, G, SP)                                                                                   \
-    ((G && !a.want_ll) ? k_pass3<DT, G, pass3_unroll<DT, G>(), false, SP><<<grid, kPassThreads, 0, s>>>(a)     \
-                       : k_pass3<DT, G, pass3_unroll<DT, G>(), true, SP><<<grid, kPassThreads, 0, s>>>(a))
+    ((G && !a.want_ll) ? launch_k_pass3<DT, G, pass3_unroll<DT, G>(), false, SP>(a, grid, s)                  \
+                       : launch_k_pass3<DT, G, pass3_unroll<DT, G>(), true, SP>(a, grid, s))
 #define GMCS_PASS(DT, G)                                                                                        \
     (three ? (a.sparse ? GMCS_PASS3(DT, G, true) : GMCS_PASS3(DT, G, false))                                   \
            : k_pass<DT, G><<<grid, kPassThreads, 0, s>>>(a))

@@ -70,3 +70,7 @@ def test_precision_at_scale(big):
                                "ll_rel_diff_vs_f32_max_all_particles": float(e_vs32.max()),
                                "estimate_vs_f32_m": float(d_est)}
     print("\nPRECISION_AT_SCALE " + json.dumps(report))
+    out = os.environ.get("GMCS_REPORT_DIR")
+    if out:
+        with open(os.path.join(out, "precision_at_scale.json"), "w") as fh:
+            json.dump(report, fh, indent=1)
