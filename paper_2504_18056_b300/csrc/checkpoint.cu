@@ -74,7 +74,8 @@ bool finite_grid(const gmcs_grid& g) {
 }
 
 // Directory bytes of a column-sparse table (the records start 256-byte aligned).
-uint64_t dir_bytes_of(const gmcs_grid& g) { return ((uint64_t)(g.n[0] - 1) * (g.n[1] - 1) * 8 + 255) / 256 * 256; }
+uint64_t dir_tiles_of(const gmcs_grid& g) { return (uint64_t)col_tiles(g.n[0] - 1) * col_tiles(g.n[1] - 1); }
+uint64_t dir_bytes_of(const gmcs_grid& g) { return (dir_tiles_of(g) * 8 + 255) / 256 * 256; }
 
 // Whether a keyframe's table size fits its storage type, layout and lattice as
 // the library writes them: GICP voxel maps 48 bytes per voxel; dense field tables
@@ -104,20 +105,21 @@ bool table_bytes_ok(const TableHead& t, const gmcs_config& cfg) {
     if (t.layout == GMCS_LAYOUT_DENSE) return t.bytes == nc * rec;
     if (t.layout != GMCS_LAYOUT_COLUMNS || t.grid.n[2] > 65536) return false;
     const uint64_t db = dir_bytes_of(t.grid);
-    return t.bytes >= db + rec && (t.bytes - db) % rec == 0 && t.bytes - db <= std::max<uint64_t>(nc, 1) * rec;
+    const uint64_t most = dir_tiles_of(t.grid) * kColTile * kColTile * (uint64_t)(t.grid.n[2] - 1);
+    return t.bytes >= db + rec && (t.bytes - db) % rec == 0 && t.bytes - db <= std::max<uint64_t>(most, 1) * rec;
 }
 
 // A column directory read from a file: every run inside the lattice's z range
 // and inside the records that follow.
 bool directory_ok(const unsigned char* buf, const TableHead& t) {
-    const uint64_t ncol = (uint64_t)(t.grid.n[0] - 1) * (t.grid.n[1] - 1);
+    const uint64_t ncol = dir_tiles_of(t.grid);
     const uint64_t nrec = (t.bytes - dir_bytes_of(t.grid)) / (t.dtype == 0 ? 32 : 16);
     const uint32_t ncz = (uint32_t)(t.grid.n[2] - 1);
     for (uint64_t k = 0; k < ncol; ++k) {
         uint2 d;
         std::memcpy(&d, buf + 8 * k, sizeof(d));
         const uint32_t zlo = d.y & 0xFFFFu, cnt = d.y >> 16;
-        if ((uint64_t)zlo + cnt > ncz || (uint64_t)d.x + cnt > nrec) return false;
+        if ((uint64_t)zlo + cnt > ncz || (uint64_t)d.x + (uint64_t)cnt * kColTile * kColTile > nrec) return false;
     }
     return true;
 }

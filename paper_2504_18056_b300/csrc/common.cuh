@@ -321,18 +321,30 @@ __device__ __forceinline__ void ld_record32(const float4* p, float4& a, float4& 
         : "l"(p));
 }
 
-// Column-sparse tables store, for every (x, y) column of cells, only the cells
-// from the lowest to the highest one whose polynomial is not zero (the field is
-// zero farther than r_t from every keyframe point, so a column holds one short
-// run of cells near the surfaces it crosses); dir[cy * ncx + cx] = (index of the
-// run's first record, zlo | count << 16). A cell outside the run reads as zero.
-// Returns whether (cx, cy, cz) is stored, and its record index.
+// Column-sparse tables store, for every tile of kColTile x kColTile (x, y) columns
+// of cells, only the cells from the lowest to the highest z layer in which any of
+// the tile's cells has a nonzero polynomial (the field is zero farther than r_t
+// from every keyframe point, so a tile holds one short run of layers near the
+// surfaces it crosses). dir[(cy / T) * ntx + cx / T] = (index of the run's first
+// record, zlo | layers << 16), ntx = ceil(ncx / T); within the run the records go
+// layer by layer, each layer's T x T cells x fastest. A cell outside the run reads
+// as zero. Returns whether (cx, cy, cz) is stored, and its record index.
+#ifndef GMCS_COL_TILE_LOG2
+#define GMCS_COL_TILE_LOG2 0
+#endif
+constexpr int kColTileLog2 = GMCS_COL_TILE_LOG2;
+constexpr int kColTile = 1 << kColTileLog2;
+
+__host__ __device__ inline uint32_t col_tiles(uint32_t n) { return (n + kColTile - 1) >> kColTileLog2; }
+
 __device__ __forceinline__ bool col_cell(const uint2* __restrict__ dir, uint32_t ncx, uint32_t ncy, int cx, int cy,
                                          int cz, uint32_t& idx) {
     if (!(((uint32_t)cx < ncx) & ((uint32_t)cy < ncy))) return false;
-    const uint2 d = __ldg(dir + ((uint32_t)cy * ncx + (uint32_t)cx));
+    const uint32_t tx = (uint32_t)cx >> kColTileLog2, ty = (uint32_t)cy >> kColTileLog2;
+    const uint2 d = __ldg(dir + (ty * col_tiles(ncx) + tx));
     const uint32_t rel = (uint32_t)cz - (d.y & 0xFFFFu);
-    idx = d.x + rel;
+    idx = d.x + ((rel << (2 * kColTileLog2)) | (((uint32_t)cy & (kColTile - 1)) << kColTileLog2) |
+                 ((uint32_t)cx & (kColTile - 1)));
     return rel < (d.y >> 16);
 }
 

@@ -956,7 +956,7 @@ namespace {
 // per-column runs (device), read back to build the directory of first-record
 // offsets on the host; allocates the table (directory, then the records) into t.
 int build_columns(gmcs_ctx* c, HostTable& t, int nx, int ny, int nz, float inv_two_sigma2, float r_t2, size_t rec) {
-    const size_t ncol = (size_t)(nx - 1) * (ny - 1);
+    const size_t ncol = (size_t)col_tiles(nx - 1) * col_tiles(ny - 1);   // tiles of columns
     uint32_t* d_run = nullptr;
     if (cudaMalloc((void**)&d_run, ncol * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -983,7 +983,7 @@ int build_columns(gmcs_ctx* c, HostTable& t, int nx, int ny, int nz, float inv_t
     uint64_t total = 0;
     for (size_t k = 0; k < ncol; ++k) {
         dir[k] = make_uint2((uint32_t)total, run[k]);
-        total += run[k] >> 16;
+        total += (uint64_t)(run[k] >> 16) * kColTile * kColTile;
     }
     if (total >= ((uint64_t)1 << 31)) return GMCS_E_INVALID;
     t.dir_bytes = (ncol * sizeof(uint2) + 255) / 256 * 256;   // records start 256-byte aligned

@@ -94,17 +94,26 @@ __device__ __forceinline__ void pack_cell(const PackArgs& a, int cx, int cy, int
     }
 }
 
-// Dense tables: one thread per cell. Column-sparse tables: one thread per (x, y)
-// column, packing the cells of its run.
+// Dense tables: one thread per cell. Column-sparse tables: one thread per tile of
+// columns, packing the cells of its run (cells past the lattice's edge in x or y,
+// which no lookup reads, stay unwritten).
 __global__ void k_pack(PackArgs a) {
     const int ncx = a.nx - 1, ncy = a.ny - 1, ncz = a.nz - 1;
     if (a.dir) {
-        const size_t ncol = (size_t)ncx * ncy;
-        for (size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x; col < ncol; col += (size_t)gridDim.x * blockDim.x) {
-            const uint2 d = a.dir[col];
-            const int cx = (int)(col % ncx), cy = (int)(col / ncx);
+        const uint32_t ntx = col_tiles(ncx), nty = col_tiles(ncy);
+        const size_t ntile = (size_t)ntx * nty;
+        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < ntile; t += (size_t)gridDim.x * blockDim.x) {
+            const uint2 d = a.dir[t];
+            const int tx = (int)(t % ntx), ty = (int)(t / ntx);
             const int zlo = (int)(d.y & 0xFFFFu), cnt = (int)(d.y >> 16);
-            for (int k = 0; k < cnt; ++k) pack_cell(a, cx, cy, zlo + k, (size_t)d.x + k);
+            for (int k = 0; k < cnt; ++k)
+                for (int ly = 0; ly < kColTile; ++ly)
+                    for (int lx = 0; lx < kColTile; ++lx) {
+                        const int cx = tx * kColTile + lx, cy = ty * kColTile + ly;
+                        if (cx < ncx && cy < ncy)
+                            pack_cell(a, cx, cy, zlo + k,
+                                      (size_t)d.x + (((size_t)k * kColTile + ly) * kColTile + lx));
+                    }
         }
         return;
     }
@@ -117,36 +126,31 @@ __global__ void k_pack(PackArgs a) {
     }
 }
 
-// Column-sparse tables: per (x, y) column, the run from its lowest to its highest
-// cell with a nonzero corner value, as zlo | count << 16 (count 0: empty column).
+// Column-sparse tables: per tile of columns, the run from its lowest to its
+// highest cell layer with a nonzero corner value, as zlo | layers << 16 (0: empty).
 __global__ void k_col_range(const unsigned* __restrict__ d2, int nx, int ny, int nz, float inv_two_sigma2,
                             float r_t2, uint32_t* __restrict__ out) {
     const int ncx = nx - 1, ncy = ny - 1, ncz = nz - 1;
-    const size_t ncol = (size_t)ncx * ncy;
-    for (size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x; col < ncol; col += (size_t)gridDim.x * blockDim.x) {
-        const int cx = (int)(col % ncx), cy = (int)(col / ncx);
-        // vertex layer iz of the column is nonzero if any of its 4 vertices is
+    const uint32_t ntx = col_tiles(ncx), nty = col_tiles(ncy);
+    const size_t ntile = (size_t)ntx * nty;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < ntile; t += (size_t)gridDim.x * blockDim.x) {
+        const int x0 = (int)(t % ntx) * kColTile, y0 = (int)(t / ntx) * kColTile;
+        const int x1 = min(x0 + kColTile, ncx), y1 = min(y0 + kColTile, ncy);   // cells [x0, x1) x [y0, y1)
         int lo = -1, hi = -2;
-        bool prev = false;
         for (int iz = 0; iz < nz; ++iz) {
+            // vertex layer iz of the tile (vertices x0..x1, y0..y1) holds a nonzero value:
+            // cell layers iz - 1 and iz are nonzero
             bool nzv = false;
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const size_t vi = ((size_t)iz * ny + (cy + dy)) * nx + (cx + dx);
-                    nzv |= field_value(d2[vi], inv_two_sigma2, r_t2) > 0.f;
-                }
-            // cell iz - 1 (vertex layers iz - 1, iz) and cell iz (layers iz, iz + 1)
+            for (int iy = y0; iy <= y1 && !nzv; ++iy)
+                for (int ix = x0; ix <= x1 && !nzv; ++ix)
+                    nzv = field_value(d2[((size_t)iz * ny + iy) * nx + ix], inv_two_sigma2, r_t2) > 0.f;
             if (nzv) {
                 const int c0 = iz > 0 ? iz - 1 : 0, c1 = iz < ncz ? iz : ncz - 1;
                 if (lo < 0) lo = c0;
                 hi = c1;
             }
-            prev = nzv;
         }
-        (void)prev;
-        out[col] = lo < 0 ? 0u : ((uint32_t)lo | ((uint32_t)(hi - lo + 1) << 16));
+        out[t] = lo < 0 ? 0u : ((uint32_t)lo | ((uint32_t)(hi - lo + 1) << 16));
     }
 }
 
@@ -221,13 +225,14 @@ void launch_splat(const SplatArgs& a, cudaStream_t s) {
 }
 
 void launch_pack(const PackArgs& a, cudaStream_t s) {
-    const size_t n = a.dir ? (size_t)(a.nx - 1) * (a.ny - 1) : (size_t)(a.nx - 1) * (a.ny - 1) * (a.nz - 1);
+    const size_t n = a.dir ? (size_t)col_tiles(a.nx - 1) * col_tiles(a.ny - 1) : (size_t)(a.nx - 1) * (a.ny - 1) * (a.nz - 1);
     k_pack<<<grid_for(n, 256), 256, 0, s>>>(a);
 }
 
 void launch_col_range(const unsigned* d2, int nx, int ny, int nz, float inv_two_sigma2, float r_t2, uint32_t* out,
                       cudaStream_t s) {
-    k_col_range<<<grid_for((size_t)(nx - 1) * (ny - 1), 256), 256, 0, s>>>(d2, nx, ny, nz, inv_two_sigma2, r_t2, out);
+    k_col_range<<<grid_for((size_t)col_tiles(nx - 1) * col_tiles(ny - 1), 256), 256, 0, s>>>(d2, nx, ny, nz,
+                                                                                            inv_two_sigma2, r_t2, out);
 }
 
 void launch_unpack(const void* cells, const uint2* dir, int dtype, int nx, int ny, int nz, float* out, cudaStream_t s) {
