@@ -45,6 +45,9 @@ struct gmcs_ctx {
     int P = 0, K = 0;
     uint32_t frame = 0;
     uint64_t version = 0;            // bumped by every call that changes poses, neighbours or keyframes
+    int* perm = nullptr;             // locality order of the particles (differentiable log-likelihood)
+    uint32_t* order_scratch = nullptr;
+    uint64_t perm_version = ~0ull;   // state version the order was computed for
     bool have_particles = false;
     int cur = 0;
     float* pose[2] = {nullptr, nullptr};

@@ -230,6 +230,7 @@ void pass_args(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* o
     pa.eps = c->cfg.eps;
     pa.want_ll = (!grad || out_ll) ? 1 : 0;
     pa.sparse = c->cfg.table_layout == GMCS_LAYOUT_COLUMNS ? 1 : 0;
+    pa.perm = nullptr;
     FinishArgs fa;
     fa.part = c->part;
     fa.pose = c->pose[c->cur];
@@ -371,10 +372,11 @@ GatherArgs gather_args(gmcs_ctx* c, const WeighResult* res) {
 namespace {
 
 int run_pass(gmcs_ctx* c, int N, bool grad, bool move, float* out_ll, float* out_g, float* out_mom, double* logw,
-             const float* pose_override = nullptr) {
+             const float* pose_override = nullptr, const int* perm = nullptr) {
     PassArgs pa;
     FinishArgs fa;
     pass_args(c, N, grad, move, out_ll, out_g, out_mom, logw, pose_override, &pa, &fa);
+    pa.perm = perm;
     {
         Launch L(c, grad ? K_PASS_GRAD : K_PASS_VALUE);
         if (pa.model == GMCS_MODEL_GICP) launch_gicp_pass(pa, grad, c->stream);
@@ -656,7 +658,7 @@ int gmcs_destroy(gmcs_ctx* c) {
     }
     void* ptrs[] = {c->pose[0], c->pose[1], c->kf[0], c->kf[1], c->logw, c->w, c->gbuf, c->ll, c->nbr, c->part, c->scan,
                     c->stage, c->wpart, c->counter, c->d_res, c->cl, c->btot, c->dtot, c->anc, c->d_tables, c->d2, c->scov, c->d_mm, c->d_ovl,
-                    c->d_kf_path};
+                    c->d_kf_path, c->perm, c->order_scratch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -1353,6 +1355,34 @@ int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float*
 }
 
 // Poses T0 exp(xi) into the alternate pose buffer (xi staged when on the host).
+// The particles in a locality order (k_order.cu) for the passes of the
+// differentiable log-likelihood, whose poses need not be clustered; computed
+// from the current poses once per state version.
+static int locality_order(gmcs_ctx* c, const int** perm) {
+    *perm = nullptr;
+    if (!c->perm) {
+        if (cudaMalloc((void**)&c->perm, sizeof(int) * c->ld) != cudaSuccess ||
+            cudaMalloc((void**)&c->order_scratch, sizeof(uint32_t) * order_scratch_words((int)c->ld)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->perm);
+            c->perm = nullptr;
+            return GMCS_E_OOM;
+        }
+        c->dev_bytes += sizeof(int) * c->ld + sizeof(uint32_t) * order_scratch_words((int)c->ld);
+    }
+    if (c->perm_version != c->version) {
+        {
+            Launch L(c, K_MISC);
+            launch_locality_order(c->pose[c->cur], c->ld, c->P, c->order_scratch, c->perm, c->stream);
+        }
+        const int rc = check_launch();
+        if (rc) return rc;
+        c->perm_version = c->version;
+    }
+    *perm = c->perm;
+    return GMCS_OK;
+}
+
 static int perturbed_poses(gmcs_ctx* c, const float* xi, const float** pose_out) {
     const float* dxi = xi;
     if (!is_device_ptr(xi)) {
@@ -1374,9 +1404,11 @@ int gmcs_loglik(gmcs_ctx* c, const float* xi, const float* scan, int N, float* l
     int rc = upload_scan(c, scan, N);
     if (rc) return rc;
     const float* T = nullptr;
+    const int* perm = nullptr;
     if ((rc = perturbed_poses(c, xi, &T))) return rc;
+    if ((rc = locality_order(c, &perm))) return rc;
     const bool dev = is_device_ptr(ll);
-    if ((rc = run_pass(c, N, false, false, dev ? ll : c->ll, nullptr, nullptr, nullptr, T))) return rc;
+    if ((rc = run_pass(c, N, false, false, dev ? ll : c->ll, nullptr, nullptr, nullptr, T, perm))) return rc;
     if (!dev) return copy_out(c, ll, c->ll, sizeof(float) * c->P);
     return GMCS_OK;
 }
@@ -1387,8 +1419,10 @@ int gmcs_loglik_backward(gmcs_ctx* c, const float* xi, const float* scan, int N,
     int rc = upload_scan(c, scan, N);
     if (rc) return rc;
     const float* T = nullptr;
+    const int* perm = nullptr;
     if ((rc = perturbed_poses(c, xi, &T))) return rc;
-    if ((rc = run_pass(c, N, true, false, nullptr, c->gbuf, nullptr, nullptr, T))) return rc;
+    if ((rc = locality_order(c, &perm))) return rc;
+    if ((rc = run_pass(c, N, true, false, nullptr, c->gbuf, nullptr, nullptr, T, perm))) return rc;
     const float* dxi = is_device_ptr(xi) ? xi : c->stage;
     const float* dgl = grad_ll;
     if (!is_device_ptr(grad_ll)) {

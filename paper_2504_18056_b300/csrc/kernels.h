@@ -96,6 +96,7 @@ struct PassArgs {
     float eps;
     int want_ll;            // gradient pass: also accumulate the log-likelihood (the moves do not need it)
     int sparse;             // the context's tables are column-sparse (TableDesc::dir)
+    const int* perm;        // optional order of the particles over the lanes (null: lane tile*32 + l is particle tile*32 + l)
 };
 
 struct FinishArgs {
@@ -320,6 +321,9 @@ void launch_scan_pack_b(const BatchList<ScanPackArgs>* L, cudaStream_t s);
 void launch_predict_b(const BatchList<PredictArgs>* L, cudaStream_t s);
 void launch_select_b(const BatchList<SelectArgs>* L, cudaStream_t s);
 void launch_pass3_b(const BatchList<PassArgs>* L, int dtype, bool grad, bool sparse, cudaStream_t s);
+// a locality order of P particles (k_order.cu): Morton buckets of their translations
+size_t order_scratch_words(int P);
+void launch_locality_order(const float* pose, size_t ld, int P, uint32_t* scratch, int* perm, cudaStream_t s);
 void launch_finish_b(const BatchList<FinishArgs>* L, bool grad, bool gicp, cudaStream_t s);
 void launch_weigh_b(const BatchList<WeighArgs>* L, cudaStream_t s);
 void launch_resample_scan_b(const BatchList<ScanArgs>* L, cudaStream_t s);

@@ -21,6 +21,7 @@ __device__ __forceinline__ WarpWork warp_work(const PassArgs& a, int vb) {
     const int tile = w.tg * kPassTW + warp % kPassTW;
     const int chunk = w.cg * kPassCW + warp / kPassTW;
     w.i = tile * 32 + lane;
+    if (a.perm && w.i < a.P) w.i = a.perm[w.i];   // the lanes' particles in the given order
     w.j0 = min(chunk * a.chunk_len, a.N);
     w.j1 = min(w.j0 + a.chunk_len, a.N);
     return w;
@@ -47,7 +48,7 @@ __device__ __forceinline__ void store_partials(const PassArgs& a, const float* a
             float s = 0.f;
 #pragma unroll
             for (int c = 0; c < kPassCW; ++c) s += red[c][e][l];
-            if (base + l < a.P) a.part[((size_t)ww.cg * NACC + e) * a.ld + base + l] = s;
+            if (base + l < a.P) a.part[((size_t)ww.cg * NACC + e) * a.ld + (a.perm ? a.perm[base + l] : base + l)] = s;
         }
     }
 }
