@@ -1359,24 +1359,8 @@ void launch_select(const SelectArgs& a, cudaStream_t s) {
     if (a.P > 0) k_select<<<(a.P + 127) / 128, 128, 0, s>>>(a);
 }
 
-// Shared-memory carveout of the lookup passes, as a percentage of the unified
-// L1/shared storage (-1: the driver's choice). The passes need ~9 KB of shared
-// memory per CTA; the rest of the storage can serve as L1 for the cell records.
-#ifndef GMCS_CARVEOUT
-#define GMCS_CARVEOUT -1
-#endif
-template <typename K>
-static void set_carveout(K kernel) {
-    if (GMCS_CARVEOUT >= 0) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, GMCS_CARVEOUT);
-        cudaGetLastError();
-    }
-}
-
 template <int DT, bool G, int U, bool LL, bool SP>
 static void launch_k_pass3(const PassArgs& a, int grid, cudaStream_t s) {
-    static const bool once = (set_carveout(k_pass3<DT, G, U, LL, SP>), true);
-    (void)once;
     k_pass3<DT, G, U, LL, SP><<<grid, kPassThreads, 0, s>>>(a);
 }
 
