@@ -651,6 +651,30 @@ __device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, const 
     }
 }
 
+// Column-sparse tables: the record of cell layer cz from its column's directory
+// entry d (already loaded; (0, 0) outside the lattice, an empty run).
+template <int DT>
+__device__ __forceinline__ void fetch_dir(const void* __restrict__ cells, uint2 d, int cz, bool live, RawRec<DT>& r) {
+    const uint32_t rel = (uint32_t)cz - (d.y & 0xFFFFu);
+    const bool valid = live & (rel < (d.y >> 16));
+    const uint32_t idx = d.x + rel;
+    if constexpr (DT == 0) {
+        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.b = r.a;
+        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
+    } else {
+        r.q = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+    }
+}
+
+// column-sparse tables: directory entries loaded one issue ahead (1), or on the
+// record load's address chain (0)
+#ifndef GMCS_DIR_AHEAD
+#define GMCS_DIR_AHEAD 0
+#endif
+constexpr bool kDirAhead = GMCS_DIR_AHEAD;
+
 template <int DT>
 __device__ __forceinline__ void unpack_raw(const RawRec<DT>& r, float* v) {
     if constexpr (DT == 0) {
@@ -744,15 +768,40 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
         Moments mom;
         moments_zero(mom);
 
-        auto issue = [&](Stage<DT>& st, int j, bool live) {
-            st.p = __ldg(a.scan + j);
+        // column-sparse tables: the directory entries of the next point to issue are
+        // loaded one issue ahead (the columns from its (x, y) transform, recomputed when
+        // it is issued), so the record loads do not wait on them
+        float4 pd = make_float4(0.f, 0.f, 0.f, 1.f);
+        uint2 dd[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
+        auto ahead = [&](int j, bool live) {
+            if constexpr (SP && kDirAhead) {
+                pd = __ldg(a.scan + j);
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    const float2 uxy = p2_fma(make_float2(xf[s].q0.x, xf[s].q0.y), make_float2(pd.x, pd.x),
+                                              p2_fma(make_float2(xf[s].q0.z, xf[s].q0.w), make_float2(pd.y, pd.y),
+                                                     p2_fma(make_float2(xf[s].q1.x, xf[s].q1.y),
+                                                            make_float2(pd.z, pd.z),
+                                                            make_float2(xf[s].q1.z, xf[s].q1.w))));
+                    const float2 t2 = p2_add_rm(uxy, make_float2(12582912.0f, 12582912.0f));
+                    const uint32_t cx = (uint32_t)(__float_as_int(t2.x) - 0x4B400000);
+                    const uint32_t cy = (uint32_t)(__float_as_int(t2.y) - 0x4B400000);
+                    dd[s] = make_uint2(0u, 0u);
+                    if (live && cx < ncx[s] && cy < ncy[s]) dd[s] = __ldg(dirs[s] + (cy * ncx[s] + cx));
+                }
+            }
+        };
+        auto issue = [&](Stage<DT>& st, int j, bool live, int jn, bool live_n) {
+            st.p = (SP && kDirAhead) ? pd : __ldg(a.scan + j);
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 int cx, cy, cz;
                 slot_point<DT, true>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0],
                                       st.f[s][1], st.f[s][2]);
-                fetch_raw<DT, SP>(cells[s], dirs[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
+                if constexpr (SP && kDirAhead) fetch_dir<DT>(cells[s], dd[s], cz, live, st.r[s]);
+                else fetch_raw<DT, SP>(cells[s], dirs[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
             }
+            ahead(jn, live_n);
         };
         auto use = [&](const Stage<DT>& st) {
             // one log2 per point of the product of its three L + eps (each in [eps, 1 + eps]),
@@ -789,14 +838,14 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
             if constexpr (kLL) lsum += __log2f(lprod);
         };
         Stage<DT> SA, SB;
-        issue(SA, j0, true);
+        ahead(j0, true);
+        issue(SA, j0, true, j0 + 1 < j1 ? j0 + 1 : j0, j0 + 1 < j1);
         for (int j = j0;; j += 2) {   // j1 and the exits are uniform across the warp
-            const bool m1 = j + 1 < j1;
-            issue(SB, m1 ? j + 1 : j, m1);
+            const bool m1 = j + 1 < j1, m2 = j + 2 < j1, m3 = j + 3 < j1;
+            issue(SB, m1 ? j + 1 : j, m1, m2 ? j + 2 : j, m2);
             use(SA);
             if (!m1) break;
-            const bool m2 = j + 2 < j1;
-            issue(SA, m2 ? j + 2 : j + 1, m2);
+            issue(SA, m2 ? j + 2 : j + 1, m2, m3 ? j + 3 : j, m3);
             use(SB);
             if (!m2) break;
         }
@@ -1036,7 +1085,8 @@ constexpr int pass3_minblocks() {
 template <int DT, bool GRAD, int UNROLL, bool LL = true, bool SP = false>
 __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
     if constexpr (!GRAD && value3<DT>()) pass3v_body<DT, SP>(a, vb);
-    else if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>()) pass3q_body<DT, GRAD, LL, SP>(a, vb);
+    else if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>() && !(SP && kDirAhead))
+        pass3q_body<DT, GRAD, LL, SP>(a, vb);
     else if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL, SP>(a, vb);
     else pass3_body<DT, GRAD, UNROLL>(a, vb);
 }
