@@ -984,81 +984,6 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
     store_partials<NACC>(a, acc, ww);
 }
 
-// ---- value pass with three stages in turn: two points' records in flight while
-// a third point is interpolated (the value pass keeps no gradient sums, so a
-// third stage fits where the gradient pass has none to spare).
-#ifndef GMCS_V3_32
-#define GMCS_V3_32 0
-#endif
-#ifndef GMCS_V3_16
-#define GMCS_V3_16 0
-#endif
-template <int DT>
-constexpr bool value3() { return DT == 0 ? GMCS_V3_32 : GMCS_V3_16; }
-
-template <int DT, bool SP = false>
-__device__ __forceinline__ void pass3v_body(const PassArgs& a, int vb) {
-    const WarpWork ww = warp_work(a, vb);
-    const int i = ww.i, j0 = ww.j0, j1 = ww.j1;
-    float acc[1] = {0.f};
-    if (i < a.P && j0 < j1) {
-        Xf xf[3];
-        const void* cells[3];
-        const uint2* dirs[3];
-        uint32_t ncx[3], ncy[3], ncz[3];
-        {
-            float Tt[12];
-            load_pose(a.pose, a.ld, i, Tt);
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                const Slot sl = make_slot(a, i, a.nbr[(size_t)s * a.ld + i], Tt);
-                xf[s] = slot_xf(sl);
-                cells[s] = sl.cells;
-                dirs[s] = sl.dir;
-                ncx[s] = sl.ncx; ncy[s] = sl.ncy; ncz[s] = sl.ncz;
-            }
-        }
-        const float eps = a.eps;
-        float lsum = 0.f;
-        auto issue = [&](Stage<DT>& st, int j, bool live) {
-            const float4 p = __ldg(a.scan + (live ? j : j0));
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                int cx, cy, cz;
-                float ux, uy, uz;
-                slot_point<DT, true>(xf[s], p, ux, uy, uz, cx, cy, cz, st.f[s][0], st.f[s][1], st.f[s][2]);
-                fetch_raw<DT, SP>(cells[s], dirs[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
-            }
-        };
-        auto use = [&](const Stage<DT>& st) {
-            float lprod = 1.f, w, gx, gy, gz;
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                float v[8];
-                unpack_raw<DT>(st.r[s], v);
-                coef_interp<false, true>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
-            }
-            lsum += __log2f(lprod);
-        };
-        Stage<DT> S0, S1, S2;
-        issue(S0, j0, true);
-        issue(S1, j0 + 1, j0 + 1 < j1);
-        for (int j = j0;; j += 3) {   // j1 and the exits are uniform across the warp
-            issue(S2, j + 2, j + 2 < j1);
-            use(S0);
-            if (!(j + 1 < j1)) break;
-            issue(S0, j + 3, j + 3 < j1);
-            use(S1);
-            if (!(j + 2 < j1)) break;
-            issue(S1, j + 4, j + 4 < j1);
-            use(S2);
-            if (!(j + 3 < j1)) break;
-        }
-        acc[0] = lsum * 0.69314718055994531f;
-    }
-    store_partials<1>(a, acc, ww);
-}
-
 // CTAs per SM the register allocation is sized for: the pipelined gradient
 // pass fits 168 registers at 3 CTAs per SM; the unpipelined one uses ~150 and
 // capping it at 128 costs 4 %; the value passes fit 128 at 4 CTAs per SM
@@ -1084,8 +1009,7 @@ constexpr int pass3_minblocks() {
 
 template <int DT, bool GRAD, int UNROLL, bool LL = true, bool SP = false>
 __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
-    if constexpr (!GRAD && value3<DT>()) pass3v_body<DT, SP>(a, vb);
-    else if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>() && !(SP && kDirAhead))
+    if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>() && !(SP && kDirAhead))
         pass3q_body<DT, GRAD, LL, SP>(a, vb);
     else if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL, SP>(a, vb);
     else pass3_body<DT, GRAD, UNROLL>(a, vb);
