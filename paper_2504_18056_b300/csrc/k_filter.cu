@@ -622,6 +622,22 @@ struct RawRec<0> {
     float4 a, b;
 };
 
+// Load record idx of a table into r if valid, else zero r. (Leaving r as it was
+// under the predicate and masking the lookup where it is used keeps both stages'
+// records live through the loop: 168 registers with spills, FP32 gradient pass
+// 1.57 -> 2.17 ms.)
+template <int DT>
+__device__ __forceinline__ void rec_load(const void* __restrict__ cells, uint32_t idx, bool valid, RawRec<DT>& r) {
+    if constexpr (DT == 0) {
+        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.b = r.a;
+        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
+    } else {
+        r.q = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+    }
+}
+
 // Issue the load of cell c of a slot's table; a cell outside the table, or a
 // stage with no point (live = false), reads as zeros: the lane's load is
 // predicated off and its record registers are zeroed. (Loading a zero record
@@ -641,14 +657,7 @@ __device__ __forceinline__ void fetch_raw(const void* __restrict__ cells, const 
         valid = live & ((uint32_t)cx < ncx) & ((uint32_t)cy < ncy) & ((uint32_t)cz < ncz);
         idx = ((uint32_t)cz * ncy + (uint32_t)cy) * ncx + (uint32_t)cx;   // used only when valid
     }
-    if constexpr (DT == 0) {
-        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.b = r.a;
-        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
-    } else {
-        r.q = make_uint4(0u, 0u, 0u, 0u);
-        if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
-    }
+    rec_load<DT>(cells, idx, valid, r);
 }
 
 // Column-sparse tables: the record of cell layer cz from its column's directory
@@ -657,15 +666,7 @@ template <int DT>
 __device__ __forceinline__ void fetch_dir(const void* __restrict__ cells, uint2 d, int cz, bool live, RawRec<DT>& r) {
     const uint32_t rel = (uint32_t)cz - (d.y & 0xFFFFu);
     const bool valid = live & (rel < (d.y >> 16));
-    const uint32_t idx = d.x + rel;
-    if constexpr (DT == 0) {
-        r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.b = r.a;
-        if (valid) ld_record32(reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx, r.a, r.b);
-    } else {
-        r.q = make_uint4(0u, 0u, 0u, 0u);
-        if (valid) r.q = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
-    }
+    rec_load<DT>(cells, d.x + rel, valid, r);
 }
 
 // column-sparse tables: directory entries loaded one issue ahead (1), or on the
@@ -675,6 +676,12 @@ __device__ __forceinline__ void fetch_dir(const void* __restrict__ cells, uint2 
 #define GMCS_DIR_AHEAD 1
 #endif
 constexpr bool kDirAhead = GMCS_DIR_AHEAD;
+// dense tables: the next point to issue loaded one issue ahead (1: FP32 gradient /
+// value pass 1.570 / 1.035 -> 1.530 / 1.010 ms, BF16 value pass 0.986 -> 0.970 ms),
+// or when it is issued (0)
+#ifndef GMCS_P_AHEAD
+#define GMCS_P_AHEAD 1
+#endif
 
 template <int DT>
 __device__ __forceinline__ void unpack_raw(const RawRec<DT>& r, float* v) {
@@ -774,9 +781,10 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
         // it is issued), so the record loads do not wait on them
         float4 pd = make_float4(0.f, 0.f, 0.f, 1.f);
         uint2 dd[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
+        constexpr bool kPd = (SP && kDirAhead) || GMCS_P_AHEAD;
         auto ahead = [&](int j, bool live) {
+            if constexpr (kPd) pd = __ldg(a.scan + j);
             if constexpr (SP && kDirAhead) {
-                pd = __ldg(a.scan + j);
 #pragma unroll
                 for (int s = 0; s < 3; ++s) {
                     const float2 uxy = p2_fma(make_float2(xf[s].q0.x, xf[s].q0.y), make_float2(pd.x, pd.x),
@@ -793,7 +801,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
             }
         };
         auto issue = [&](Stage<DT>& st, int j, bool live, int jn, bool live_n) {
-            st.p = (SP && kDirAhead) ? pd : __ldg(a.scan + j);
+            st.p = kPd ? pd : __ldg(a.scan + j);
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 int cx, cy, cz;
@@ -960,15 +968,31 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
             if constexpr (GRAD) moments_add(mom, wsum, pc);
             if constexpr (kLL) lsum += __log2f(lprod);
         };
-        for (int j = j0;; j += 2) {   // j1 and the exits are uniform across the warp
-            const bool m1 = j + 1 < j1;
-            const float4 pB = __ldg(a.scan + (m1 ? j + 1 : j));
-            step(A, pA, B, pB, m1);
-            if (!m1) break;
-            const bool m2 = j + 2 < j1;
-            pA = __ldg(a.scan + (m2 ? j + 2 : j + 1));
-            step(B, pB, A, pA, m2);
-            if (!m2) break;
+        if constexpr (GMCS_P_AHEAD) {
+            // each point loaded one step before the step that issues it
+            float4 pB = __ldg(a.scan + (j0 + 1 < j1 ? j0 + 1 : j0));
+            for (int j = j0;; j += 2) {   // j1 and the exits are uniform across the warp
+                const bool m1 = j + 1 < j1, m2 = j + 2 < j1, m3 = j + 3 < j1;
+                const float4 pN = __ldg(a.scan + (m2 ? j + 2 : j));
+                step(A, pA, B, pB, m1);
+                if (!m1) break;
+                pA = pN;
+                const float4 pM = __ldg(a.scan + (m3 ? j + 3 : j));
+                step(B, pB, A, pA, m2);
+                if (!m2) break;
+                pB = pM;
+            }
+        } else {
+            for (int j = j0;; j += 2) {   // j1 and the exits are uniform across the warp
+                const bool m1 = j + 1 < j1;
+                const float4 pB = __ldg(a.scan + (m1 ? j + 1 : j));
+                step(A, pA, B, pB, m1);
+                if (!m1) break;
+                const bool m2 = j + 2 < j1;
+                pA = __ldg(a.scan + (m2 ? j + 2 : j + 1));
+                step(B, pB, A, pA, m2);
+                if (!m2) break;
+            }
         }
         if constexpr (GRAD) {
 #pragma unroll

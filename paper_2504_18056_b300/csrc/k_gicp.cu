@@ -272,6 +272,17 @@ __device__ __forceinline__ void rot_gen(const float* R, float* A) {
         for (int c = 0; c < 3; ++c) A[r * 3 + c] = fmaf(R[r], M[c], fmaf(R[3 + r], M[3 + c], R[6 + r] * M[6 + c]));
 }
 
+// the gradient pass loads each point and normal one point ahead (1)
+#ifndef GMCS_GICP_PAHEAD
+#define GMCS_GICP_PAHEAD 1
+#endif
+// CTAs per SM the register allocation is sized for (1: no bound; the gradient pass
+// takes 124 registers, 4 CTAs per SM; bounded to 5 CTAs it fits 96 registers but is
+// slower with the look-ahead, 3.93 -> 4.05 ms)
+#ifndef GMCS_GICP_MINBLOCKS
+#define GMCS_GICP_MINBLOCKS 1
+#endif
+
 template <bool GRAD>
 __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
     constexpr int NACC = GRAD ? kAccGicp : 1;
@@ -309,11 +320,28 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
 #pragma unroll
             for (int e = 0; e < 21; ++e) hk[e] = 0.f;
             float nin = 0.f;
+            // the point's normal is loaded with the point, not after the voxel test, off
+            // the record load's dependency chain (4.69 -> 4.61 ms); the gradient pass loads
+            // both one point ahead (gradient pass 4.50 -> 3.93 ms; the value pass loses,
+            // 2.49 -> 2.60 ms)
+            constexpr bool kAhead = GMCS_GICP_PAHEAD && GRAD;
+            float4 pn = make_float4(0.f, 0.f, 0.f, 0.f), nn = pn;
+            if constexpr (kAhead) {
+                pn = __ldg(a.scan + j0);
+                nn = __ldg(a.scov + j0);
+            }
             for (int j = j0; j < j1; ++j) {
-                const float4 p = __ldg(a.scan + j);
-                // the point's normal is loaded with the point, not after the voxel
-                // test, off the record load's dependency chain (4.69 -> 4.61 ms)
-                const float4 nj = __ldg(a.scov + j);
+                float4 p, nj;
+                if constexpr (kAhead) {
+                    p = pn;
+                    nj = nn;
+                    const int jn = j + 1 < j1 ? j + 1 : j;
+                    pn = __ldg(a.scan + jn);
+                    nn = __ldg(a.scov + jn);
+                } else {
+                    p = __ldg(a.scan + j);
+                    nj = __ldg(a.scov + j);
+                }
                 const float r0 = fmaf(R00, p.x, fmaf(R01, p.y, R02 * p.z));
                 const float r1 = fmaf(R10, p.x, fmaf(R11, p.y, R12 * p.z));
                 const float r2 = fmaf(R20, p.x, fmaf(R21, p.y, R22 * p.z));
@@ -443,12 +471,12 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kPassThreads) k_gicp(PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, GMCS_GICP_MINBLOCKS) k_gicp(PassArgs a) {
     gicp_body<GRAD>(a, blockIdx.x);
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kPassThreads) k_gicp_b(const BatchList<PassArgs>* L) {
+__global__ void __launch_bounds__(kPassThreads, GMCS_GICP_MINBLOCKS) k_gicp_b(const BatchList<PassArgs>* L) {
     GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; gicp_body<GRAD>(a, vb));
 }
 
