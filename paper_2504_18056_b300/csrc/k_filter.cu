@@ -1022,14 +1022,17 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
 #ifndef GMCS_PIPE_GRAD_MINBLOCKS16
 #define GMCS_PIPE_GRAD_MINBLOCKS16 3
 #endif
+// The 16-bit value pass on dense tables (slot-interleaved body) fits 96 registers
+// at 5 CTAs per SM (BF16 0.991 -> 0.941 ms; FP32 at 5 CTAs loses, 1.011 -> 1.091
+// ms); on column-sparse tables (two whole stages) it would spill there.
 #ifndef GMCS_VALUE_MINBLOCKS16
-#define GMCS_VALUE_MINBLOCKS16 4
+#define GMCS_VALUE_MINBLOCKS16 5
 #endif
-template <int DT, bool GRAD>
+template <int DT, bool GRAD, bool SP = false>
 constexpr int pass3_minblocks() {
     return GRAD ? (pass3_pipelined<DT, GRAD>() ? (DT == 0 ? GMCS_PIPE_GRAD_MINBLOCKS : GMCS_PIPE_GRAD_MINBLOCKS16)
                                                : GMCS_PASS3_MINBLOCKS)
-                : (DT == 0 ? GMCS_VALUE_MINBLOCKS : GMCS_VALUE_MINBLOCKS16);
+                : (DT == 0 || SP ? GMCS_VALUE_MINBLOCKS : GMCS_VALUE_MINBLOCKS16);
 }
 
 template <int DT, bool GRAD, int UNROLL, bool LL = true, bool SP = false>
@@ -1041,7 +1044,7 @@ __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
 }
 
 template <int DT, bool GRAD, int UNROLL, bool LL = true, bool SP = false>
-__global__ void __launch_bounds__(kPassThreads, pass3_minblocks<DT, GRAD>()) k_pass3(PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, pass3_minblocks<DT, GRAD, SP>()) k_pass3(PassArgs a) {
     pass3_any<DT, GRAD, UNROLL, LL, SP>(a, blockIdx.x);
 }
 
@@ -1278,15 +1281,16 @@ __global__ void __launch_bounds__(128) k_select_b(const BatchList<SelectArgs>* L
 }
 
 // The persistent loop costs the 16-bit gradient pass registers: bounded at 3
-// CTAs per SM like the pipelined one (unbounded it takes 180, i.e. 2 per SM).
-template <int DT, bool GRAD>
+// CTAs per SM like the pipelined one (unbounded it takes 180, i.e. 2 per SM); the
+// value passes at 4 (the 16-bit one spills at 5).
+template <int DT, bool GRAD, bool SP>
 constexpr int pass3_b_minblocks() {
-    return pass3_minblocks<DT, GRAD>() < 3 ? 3 : pass3_minblocks<DT, GRAD>();
+    return !GRAD ? GMCS_VALUE_MINBLOCKS : pass3_minblocks<DT, GRAD, SP>() < 3 ? 3 : pass3_minblocks<DT, GRAD, SP>();
 }
 
 // served frames never ask the gradient passes for the log-likelihood
 template <int DT, bool GRAD, int UNROLL, bool SP = false>
-__global__ void __launch_bounds__(kPassThreads, pass3_b_minblocks<DT, GRAD>()) k_pass3_b(const BatchList<PassArgs>* L) {
+__global__ void __launch_bounds__(kPassThreads, pass3_b_minblocks<DT, GRAD, SP>()) k_pass3_b(const BatchList<PassArgs>* L) {
     GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; (pass3_any<DT, GRAD, UNROLL, !GRAD, SP>(a, vb)));
 }
 

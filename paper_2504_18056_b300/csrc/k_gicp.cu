@@ -282,6 +282,29 @@ __device__ __forceinline__ void rot_gen(const float* R, float* A) {
 #ifndef GMCS_GICP_MINBLOCKS
 #define GMCS_GICP_MINBLOCKS 1
 #endif
+// the value pass: the point loaded when it is used (0); one point ahead it takes
+// 2.49 -> 2.60 ms at 5 CTAs per SM, 2.54 / 2.48 ms bounded to 6 / 7)
+#ifndef GMCS_GICP_PAHEAD_V
+#define GMCS_GICP_PAHEAD_V 0
+#endif
+// value pass CTAs per SM: 8 fits 63 registers (2.49 -> 2.37 ms against 76
+// registers and 6 CTAs unbounded; 9 spills)
+#ifndef GMCS_GICP_MINBLOCKS_V
+#define GMCS_GICP_MINBLOCKS_V 8
+#endif
+template <bool GRAD>
+constexpr int gicp_minblocks() { return GRAD ? GMCS_GICP_MINBLOCKS : GMCS_GICP_MINBLOCKS_V; }
+// the persistent (served) passes: their batch loop costs registers; the gradient
+// pass takes 167 unbounded (3 CTAs per SM), 127 at 4; the value pass 94 (5 CTAs
+// per SM), and spills if bounded to 6
+#ifndef GMCS_GICP_B_MINBLOCKS
+#define GMCS_GICP_B_MINBLOCKS 4
+#endif
+#ifndef GMCS_GICP_B_MINBLOCKS_V
+#define GMCS_GICP_B_MINBLOCKS_V 1
+#endif
+template <bool GRAD>
+constexpr int gicp_b_minblocks() { return GRAD ? GMCS_GICP_B_MINBLOCKS : GMCS_GICP_B_MINBLOCKS_V; }
 
 template <bool GRAD>
 __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
@@ -324,7 +347,7 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
             // the record load's dependency chain (4.69 -> 4.61 ms); the gradient pass loads
             // both one point ahead (gradient pass 4.50 -> 3.93 ms; the value pass loses,
             // 2.49 -> 2.60 ms)
-            constexpr bool kAhead = GMCS_GICP_PAHEAD && GRAD;
+            constexpr bool kAhead = GRAD ? GMCS_GICP_PAHEAD : GMCS_GICP_PAHEAD_V;
             float4 pn = make_float4(0.f, 0.f, 0.f, 0.f), nn = pn;
             if constexpr (kAhead) {
                 pn = __ldg(a.scan + j0);
@@ -471,12 +494,12 @@ __device__ __forceinline__ void gicp_body(const PassArgs& a, int vb) {
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kPassThreads, GMCS_GICP_MINBLOCKS) k_gicp(PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, gicp_minblocks<GRAD>()) k_gicp(PassArgs a) {
     gicp_body<GRAD>(a, blockIdx.x);
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kPassThreads, GMCS_GICP_MINBLOCKS) k_gicp_b(const BatchList<PassArgs>* L) {
+__global__ void __launch_bounds__(kPassThreads, gicp_b_minblocks<GRAD>()) k_gicp_b(const BatchList<PassArgs>* L) {
     GMCS_BATCH_LOOP(L, const PassArgs a = L->args[s]; gicp_body<GRAD>(a, vb));
 }
 
