@@ -49,7 +49,7 @@ GICP_VOXEL = 1.0                # m, voxel edge of the GICP keyframe maps
 FP32_LANES_PER_SM = 128         # FP32 FMA lanes per SM (4 schedulers x 32)
 # DRAM bytes read + written per gradient-pass launch, from one ncu capture of the
 # current kernel at the same particle and point counts (profiles/); None when stale
-TRAFFIC_PER_LAUNCH = {"f32": 32.56e6, "bf16": None, "f16": None}
+TRAFFIC_PER_LAUNCH = {"f32": 32.57e6, "bf16": None, "f16": None}
 
 
 def max_sm_mhz(index):
