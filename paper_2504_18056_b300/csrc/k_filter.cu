@@ -886,8 +886,16 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 #ifndef GMCS_QPIPE16
 #define GMCS_QPIPE16 1
 #endif
-template <int DT>
-constexpr bool qpipe() { return DT == 0 ? GMCS_QPIPE32 : GMCS_QPIPE16; }
+// the value passes likewise (FP32 interleaved: 1.011 -> 1.027 ms at 4 CTAs per SM,
+// 1.070 ms at 5)
+#ifndef GMCS_QPIPE32V
+#define GMCS_QPIPE32V GMCS_QPIPE32
+#endif
+#ifndef GMCS_QPIPE16V
+#define GMCS_QPIPE16V GMCS_QPIPE16
+#endif
+template <int DT, bool GRAD>
+constexpr bool qpipe() { return GRAD ? (DT == 0 ? GMCS_QPIPE32 : GMCS_QPIPE16) : (DT == 0 ? GMCS_QPIPE32V : GMCS_QPIPE16V); }
 
 template <int DT>
 struct SlotStage {
@@ -1028,16 +1036,19 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
 #ifndef GMCS_VALUE_MINBLOCKS16
 #define GMCS_VALUE_MINBLOCKS16 5
 #endif
+#ifndef GMCS_VALUE_MINBLOCKS32
+#define GMCS_VALUE_MINBLOCKS32 GMCS_VALUE_MINBLOCKS
+#endif
 template <int DT, bool GRAD, bool SP = false>
 constexpr int pass3_minblocks() {
     return GRAD ? (pass3_pipelined<DT, GRAD>() ? (DT == 0 ? GMCS_PIPE_GRAD_MINBLOCKS : GMCS_PIPE_GRAD_MINBLOCKS16)
                                                : GMCS_PASS3_MINBLOCKS)
-                : (DT == 0 || SP ? GMCS_VALUE_MINBLOCKS : GMCS_VALUE_MINBLOCKS16);
+                : (SP ? GMCS_VALUE_MINBLOCKS : DT == 0 ? GMCS_VALUE_MINBLOCKS32 : GMCS_VALUE_MINBLOCKS16);
 }
 
 template <int DT, bool GRAD, int UNROLL, bool LL = true, bool SP = false>
 __device__ __forceinline__ void pass3_any(const PassArgs& a, int vb) {
-    if constexpr (qpipe<DT>() && pass3_pipelined<DT, GRAD>() && !(SP && kDirAhead))
+    if constexpr (qpipe<DT, GRAD>() && pass3_pipelined<DT, GRAD>() && !(SP && kDirAhead))
         pass3q_body<DT, GRAD, LL, SP>(a, vb);
     else if constexpr (pass3_pipelined<DT, GRAD>()) pass3p_body<DT, GRAD, LL, SP>(a, vb);
     else pass3_body<DT, GRAD, UNROLL>(a, vb);
