@@ -271,6 +271,10 @@ int gmcs_select(gmcs_ctx* ctx, int* nbr_out);
  * Any output may be NULL; outputs are host or device (host: synchronises).
  */
 int gmcs_eval(gmcs_ctx* ctx, const float* scan, int N, float* ll, float* g, float* mom);
+/* gmcs_eval, gmcs_move, gmcs_loglik and gmcs_loglik_backward return GMCS_E_STATE
+ * until the neighbour sets have been selected (gmcs_select or gmcs_step) since the
+ * context was created or loaded, and while the context has no particles or no
+ * keyframes. */
 
 /* One gradient-guided move of every particle (eval with gradient, then Eq. 5-7
  * with H = sigma^-2 sum w B^T B assembled from the moments). */

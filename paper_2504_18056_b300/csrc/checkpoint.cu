@@ -262,6 +262,7 @@ void unload(gmcs_ctx* c) {
     c->kf_path.clear();
     c->K = 0;
     c->P = 0;
+    c->nbr_K = 0;
     c->have_particles = false;
     c->last_valid = false;
     cudaGetLastError();

@@ -48,6 +48,7 @@ struct gmcs_ctx {
     int* perm = nullptr;             // locality order of the particles (differentiable log-likelihood)
     uint32_t* order_scratch = nullptr;
     uint64_t perm_version = ~0ull;   // state version the order was computed for
+    int nbr_K = 0;                    // keyframes when the neighbours were last selected (0: never)
     bool have_particles = false;
     int cur = 0;
     float* pose[2] = {nullptr, nullptr};

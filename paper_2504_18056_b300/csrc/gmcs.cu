@@ -397,7 +397,18 @@ int run_select(gmcs_ctx* c, int* nbr_out_dev) {
         Launch L(c, K_SELECT);
         launch_select(sa, c->stream);
     }
+    c->nbr_K = c->K;
     return check_launch();
+}
+
+// The passes read the neighbour sets: they must have been selected since the
+// context was created or loaded (before, the sets hold -1 or another session's
+// keyframe indices).
+bool nbr_ready(const gmcs_ctx* c) { return c->nbr_K > 0 && c->nbr_K <= c->K; }
+
+int check_pass_state(const gmcs_ctx* c) {
+    if (!c->have_particles || c->K == 0 || !nbr_ready(c)) return GMCS_E_STATE;
+    return GMCS_OK;
 }
 
 int run_predict(gmcs_ctx* c, const double dT[12], const double cov[36], const float* z_dev, uint32_t frame) {
@@ -638,6 +649,8 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
     }
     if (!rc && cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
     if (!rc && cudaMemsetAsync(c->nbr, 0xff, sizeof(int) * GMCS_MAX_NB * ld, c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
+    if (!rc && cudaMemsetAsync(c->d_tables, 0, sizeof(TableDesc) * (size_t)max_keyframes, c->stream) != cudaSuccess)
+        rc = GMCS_E_CUDA;
     if (!rc && cudaMemsetAsync(c->d_res, 0, sizeof(WeighResult), c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
     if (rc) {
         gmcs_destroy(c);
@@ -1324,8 +1337,9 @@ int gmcs_select(gmcs_ctx* c, int* nbr_out) {
 
 int gmcs_eval(gmcs_ctx* c, const float* scan, int N, float* ll, float* g, float* mom) {
     if (!c) return GMCS_E_INVALID;
-    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
-    int rc = upload_scan(c, scan, N);
+    int rc = check_pass_state(c);
+    if (rc) return rc;
+    rc = upload_scan(c, scan, N);
     if (rc) return rc;
     // outputs go to device staging (ll: c->ll; g and mom: the stage buffer) unless device pointers were given
     const bool gd = g && is_device_ptr(g), md = mom && is_device_ptr(mom), ld_ = ll && is_device_ptr(ll);
@@ -1400,8 +1414,9 @@ static int perturbed_poses(gmcs_ctx* c, const float* xi, const float** pose_out)
 
 int gmcs_loglik(gmcs_ctx* c, const float* xi, const float* scan, int N, float* ll) {
     if (!c || !xi || !ll) return GMCS_E_INVALID;
-    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
-    int rc = upload_scan(c, scan, N);
+    int rc = check_pass_state(c);
+    if (rc) return rc;
+    rc = upload_scan(c, scan, N);
     if (rc) return rc;
     const float* T = nullptr;
     const int* perm = nullptr;
@@ -1415,8 +1430,9 @@ int gmcs_loglik(gmcs_ctx* c, const float* xi, const float* scan, int N, float* l
 
 int gmcs_loglik_backward(gmcs_ctx* c, const float* xi, const float* scan, int N, const float* grad_ll, float* grad_xi) {
     if (!c || !xi || !grad_ll || !grad_xi) return GMCS_E_INVALID;
-    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
-    int rc = upload_scan(c, scan, N);
+    int rc = check_pass_state(c);
+    if (rc) return rc;
+    rc = upload_scan(c, scan, N);
     if (rc) return rc;
     const float* T = nullptr;
     const int* perm = nullptr;
@@ -1442,8 +1458,9 @@ int gmcs_loglik_backward(gmcs_ctx* c, const float* xi, const float* scan, int N,
 
 int gmcs_move(gmcs_ctx* c, const float* scan, int N) {
     if (!c) return GMCS_E_INVALID;
-    if (!c->have_particles || c->K == 0) return GMCS_E_STATE;
-    int rc = upload_scan(c, scan, N);
+    int rc = check_pass_state(c);
+    if (rc) return rc;
+    rc = upload_scan(c, scan, N);
     if (rc) return rc;
     c->version++;
     return run_pass(c, N, true, true, nullptr, nullptr, nullptr, nullptr);

@@ -347,8 +347,25 @@ struct Slot {
     uint32_t ncx, ncy, ncz;
 };
 
+// The table of neighbour slot k; k < 0 (a neighbour set never selected: the sets
+// start as -1, and the entry points refuse to run a pass before a selection) reads
+// as an empty table with no cells, so that every lookup in it misses and nothing
+// is read.
+__device__ __forceinline__ TableDesc slot_table(const PassArgs& a, int k) {
+    if (k >= 0) return a.tables[k];
+    TableDesc td;
+    td.cells = nullptr;
+    td.dir = nullptr;
+    td.ox = td.oy = td.oz = 0.f;
+    td.inv_h = td.h = 0.f;
+    td.ncx = td.ncy = td.ncz = 0;
+    td.dtype = 0;
+    td.pad = 0;
+    return td;
+}
+
 __device__ __forceinline__ Slot make_slot(const PassArgs& a, int i, int k, const float* Tt) {
-    const TableDesc td = a.tables[k];
+    const TableDesc td = slot_table(a, k);
     float Tk[12], rel[12];
     load_pose(a.kf + (size_t)k * kPoseC * a.ld, a.ld, i, Tk);
     pose_rel(Tk, Tt, rel);
@@ -520,7 +537,7 @@ __device__ __forceinline__ void pass3_body(const PassArgs& a, int vb) {
         if constexpr (GRAD) {
 #pragma unroll
             for (int s = 0; s < 3; ++s)
-                fold_slot(sl[s], a.tables[ks[s]].h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
+                fold_slot(sl[s], slot_table(a, ks[s]).h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
         }
         acc[0] = lsum * 0.69314718055994531f;
     }
@@ -863,7 +880,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
             for (int s = 0; s < 3; ++s) {
                 Slot sl;
                 xf_slot(xf[s], sl);
-                fold_slot(sl, a.tables[ks[s]].h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
+                fold_slot(sl, slot_table(a, ks[s]).h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
             }
 #if GMCS_PMOM
             moments_store(mom, acc);
@@ -1008,7 +1025,7 @@ __device__ __forceinline__ void pass3q_body(const PassArgs& a, int vb) {
                 Slot sl;
                 xf_slot(xf[s], sl);
                 const int k = a.nbr[(size_t)s * a.ld + i];
-                fold_slot(sl, a.tables[k].h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
+                fold_slot(sl, slot_table(a, k).h, G[s][0], G[s][1], G[s][2], C[s][0], C[s][1], C[s][2], acc);
             }
             moments_store(mom, acc);
         }

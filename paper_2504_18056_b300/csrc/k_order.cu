@@ -17,6 +17,39 @@ namespace {
 
 constexpr int kOrderBits = 16;
 constexpr uint32_t kOrderBuckets = 1u << kOrderBits;
+constexpr int kMm = 16;   // scratch words of the feature bounds (min 0..5, max 8..13)
+
+// Features of a pose: its translation (1), or its translation and the skew part of
+// its rotation scaled by a typical point range (2: a point at range r moves by
+// about r times the rotation's change, so the six features are displacements in
+// metres and share one quantisation scale).
+#ifndef GMCS_ORDER_MODE
+#define GMCS_ORDER_MODE 1
+#endif
+constexpr int kOrderDims = GMCS_ORDER_MODE == 2 ? 6 : 3;
+#ifndef GMCS_ORDER_RANGE
+#define GMCS_ORDER_RANGE 10.0f
+#endif
+
+__device__ __forceinline__ void pose_features(const float* __restrict__ pose, size_t ld, int i, float* f) {
+    f[0] = pose[3 * ld + i];
+    f[1] = pose[7 * ld + i];
+    f[2] = pose[11 * ld + i];
+    if constexpr (kOrderDims == 6) {
+        const float h = 0.5f * GMCS_ORDER_RANGE;
+        f[3] = h * (pose[9 * ld + i] - pose[6 * ld + i]);    // R21 - R12
+        f[4] = h * (pose[2 * ld + i] - pose[8 * ld + i]);    // R02 - R20
+        f[5] = h * (pose[4 * ld + i] - pose[1 * ld + i]);    // R10 - R01
+    }
+}
+
+// Spread the low 5 bits of x to every sixth bit.
+__device__ __forceinline__ uint32_t spread6(uint32_t x) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) m |= ((x >> b) & 1u) << (6 * b);
+    return m;
+}
 
 // An int whose signed order is the float order (for atomic min / max).
 __device__ __forceinline__ int ordered(float f) {
@@ -37,20 +70,18 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x) {
 
 __global__ void k_order_init(int* mm, uint32_t* cnt) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < kOrderBuckets; k += gridDim.x * blockDim.x) cnt[k] = 0;
-    if (blockIdx.x == 0 && threadIdx.x < 6) mm[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+    if (blockIdx.x == 0 && threadIdx.x < kMm) mm[threadIdx.x] = threadIdx.x < 8 ? 0x7fffffff : (int)0x80000000;
 }
 
 __global__ void k_order_bbox(const float* __restrict__ pose, size_t ld, int P, int* mm) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    float t[3] = {0.f, 0.f, 0.f};
-    const bool in = i < P;
-    if (in) {
-        t[0] = pose[3 * ld + i];
-        t[1] = pose[7 * ld + i];
-        t[2] = pose[11 * ld + i];
-    }
+    float t[kOrderDims];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < kOrderDims; ++a) t[a] = 0.f;
+    const bool in = i < P;
+    if (in) pose_features(pose, ld, i, t);
+#pragma unroll
+    for (int a = 0; a < kOrderDims; ++a) {
         int lo = in && isfinite(t[a]) ? ordered(t[a]) : 0x7fffffff;
         int hi = in && isfinite(t[a]) ? ordered(t[a]) : (int)0x80000000;
 #pragma unroll
@@ -60,7 +91,7 @@ __global__ void k_order_bbox(const float* __restrict__ pose, size_t ld, int P, i
         }
         if ((threadIdx.x & 31) == 0) {
             atomicMin(mm + a, lo);
-            atomicMax(mm + 3 + a, hi);
+            atomicMax(mm + 8 + a, hi);
         }
     }
 }
@@ -70,14 +101,29 @@ __global__ void k_order_count(const float* __restrict__ pose, size_t ld, int P, 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     uint32_t m = 0;
+    if constexpr (kOrderDims == 3) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float lo = unordered(mm[a]), hi = unordered(mm[3 + a]);
-        const float t = pose[(4 * a + 3) * ld + i];
-        const float span = hi - lo;
-        float q = span > 0.f ? (t - lo) / span * 1023.f : 0.f;
-        q = isfinite(q) ? fminf(fmaxf(q, 0.f), 1023.f) : 0.f;
-        m |= spread3((uint32_t)q) << a;
+        for (int a = 0; a < 3; ++a) {
+            const float lo = unordered(mm[a]), hi = unordered(mm[8 + a]);
+            const float t = pose[(4 * a + 3) * ld + i];
+            const float span = hi - lo;
+            float q = span > 0.f ? (t - lo) / span * 1023.f : 0.f;
+            q = isfinite(q) ? fminf(fmaxf(q, 0.f), 1023.f) : 0.f;
+            m |= spread3((uint32_t)q) << a;
+        }
+    } else {
+        // six features on one scale: the widest span gets 32 steps
+        float f[6], wmax = 0.f;
+        pose_features(pose, ld, i, f);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) wmax = fmaxf(wmax, unordered(mm[8 + a]) - unordered(mm[a]));
+        const float sc = wmax > 0.f ? 31.f / wmax : 0.f;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            float q = (f[a] - unordered(mm[a])) * sc;
+            q = isfinite(q) ? fminf(fmaxf(q, 0.f), 31.f) : 0.f;
+            m |= spread6((uint32_t)q) << (5 - a);
+        }
     }
     const uint32_t k = m >> (30 - kOrderBits);
     key[i] = k;
@@ -116,13 +162,13 @@ __global__ void k_order_scatter(const uint32_t* __restrict__ key, int P, uint32_
 
 }  // namespace
 
-size_t order_scratch_words(int P) { return (size_t)kOrderBuckets + (size_t)P + 8; }
+size_t order_scratch_words(int P) { return (size_t)kOrderBuckets + (size_t)P + kMm; }
 
 void launch_locality_order(const float* pose, size_t ld, int P, uint32_t* scratch, int* perm, cudaStream_t s) {
     if (P <= 0) return;
     uint32_t* cnt = scratch;
     int* mm = reinterpret_cast<int*>(scratch + kOrderBuckets);
-    uint32_t* key = scratch + kOrderBuckets + 8;
+    uint32_t* key = scratch + kOrderBuckets + kMm;
     const int blocks = (P + 255) / 256;
     k_order_init<<<64, 256, 0, s>>>(mm, cnt);
     k_order_bbox<<<blocks, 256, 0, s>>>(pose, ld, P, mm);

@@ -38,6 +38,29 @@ def test_small_shapes_match_oracle(box_room, box_room_tables, P, N, K, dtype, la
     f.close()
 
 
+def test_passes_refuse_before_neighbour_selection(box_room):
+    """The neighbour sets start empty (-1): evaluation, a move and the
+    differentiable log-likelihood refuse to run (GMCS_E_STATE) until a selection or
+    a step has filled them, and run once one has."""
+    import paper_2504_18056_b300 as g
+    P = 64
+    f = make_filter(box_room, P)
+    scan = np.ascontiguousarray(box_room["scans"][0])
+    xi = np.zeros((P, 6), np.float32)
+    ll = np.zeros(P, np.float32)
+    calls = [lambda: gpu_eval(f, scan, P), lambda: f.move(scan), lambda: f.loglik(xi, scan, ll),
+             lambda: f.loglik_backward(xi, scan, np.ones(P, np.float32), np.zeros((P, 6), np.float32))]
+    for call in calls:
+        with pytest.raises(g.GmcsError) as e:
+            call()
+        assert e.value.code == g.E_STATE
+    f.select()
+    ll1, _, _ = gpu_eval(f, scan, P)
+    f.loglik(xi, scan, ll)
+    np.testing.assert_allclose(ll, ll1, rtol=1e-6)
+    f.close()
+
+
 def test_particles_outside_every_table(box_room):
     P = 64
     w = dict(box_room)

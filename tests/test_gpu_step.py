@@ -154,6 +154,7 @@ def test_full_size_column_sparse_equals_dense(forest, dtype):
     out = {}
     for layout in (g.LAYOUT_DENSE, g.LAYOUT_COLUMNS):
         f = make_filter(forest, P, dtype=dtype, max_points=2048, table_layout=layout)
+        f.select()
         ev = gpu_eval(f, scan, P)
         frames = [f.step(forest["scans"][fr], forest["odometry"][fr], forest["cov"]) for fr in range(2)]
         poses, logw = f.particles()
