@@ -293,11 +293,12 @@ int gmcs_move(gmcs_ctx* ctx, const float* scan, int N);
  * field is continuous but its gradient jumps across cell faces; the value is the
  * derivative of the cell polynomials that contain the points at T_i.
  * Both calls run their lookup pass with the particles in a locality order (a
- * counting sort of their current translations into Morton buckets, kept until the
- * state changes; gmcs_state_version): a set the caller spread or perturbed reads
+ * counting sort of their current poses -- translation and rotation -- into Morton
+ * buckets, kept until the state changes; gmcs_state_version): a set the caller
+ * spread or perturbed reads
  * more of the same cells per warp. Each particle is still computed alone, so the
  * results do not depend on the order. The first call allocates the order's
- * scratch (about 0.3 MB plus 8 bytes per particle).
+ * scratch (about 4 MB plus 8 bytes per particle).
  */
 int gmcs_loglik(gmcs_ctx* ctx, const float* xi, const float* scan, int N, float* ll);
 int gmcs_loglik_backward(gmcs_ctx* ctx, const float* xi, const float* scan, int N, const float* grad_ll,

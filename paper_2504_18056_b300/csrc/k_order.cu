@@ -5,17 +5,25 @@
 // filter's particles are close after resampling (copies of one parent sit side by
 // side), but a set the caller perturbs or spreads (the differentiable
 // log-likelihood of gmcs_loglik) is not. This order sorts the particles by a
-// Morton code of their translation: a counting sort into 65,536 buckets (the top
-// 16 bits of a 30-bit Morton code over the set's bounding box) with atomic
-// scatter. The order within a bucket is arbitrary; results do not depend on it,
-// since every particle is computed in one lane from its own data.
+// Morton code of six pose features -- the translation and the rotation's skew part
+// times a typical point range of 5 m, all in metres on one scale, 5 bits each over
+// the set's bounding box -- as a counting sort into 2^20 buckets (the code's top
+// 20 bits) with atomic scatter. (On 100,000 poses spread 0.3 m / 5 deg, 4,096
+// points, 50 tables: forward / backward 13.0 / 13.4 ms with a translation-only
+// order into 2^16 buckets, 11.4 / 11.3 ms with the six features into 2^16, 10.7 /
+// 10.3 ms into 2^20; a range of 2, 3, 10 or 20 m orders worse than 5.) The order
+// within a bucket is arbitrary; results do not depend on it, since every particle
+// is computed in one lane from its own data.
 #include "kernels.h"
 
 namespace gmcs {
 
 namespace {
 
-constexpr int kOrderBits = 16;
+#ifndef GMCS_ORDER_BITS
+#define GMCS_ORDER_BITS 20
+#endif
+constexpr int kOrderBits = GMCS_ORDER_BITS;
 constexpr uint32_t kOrderBuckets = 1u << kOrderBits;
 constexpr int kMm = 16;   // scratch words of the feature bounds (min 0..5, max 8..13)
 
@@ -24,11 +32,11 @@ constexpr int kMm = 16;   // scratch words of the feature bounds (min 0..5, max 
 // about r times the rotation's change, so the six features are displacements in
 // metres and share one quantisation scale).
 #ifndef GMCS_ORDER_MODE
-#define GMCS_ORDER_MODE 1
+#define GMCS_ORDER_MODE 2
 #endif
 constexpr int kOrderDims = GMCS_ORDER_MODE == 2 ? 6 : 3;
 #ifndef GMCS_ORDER_RANGE
-#define GMCS_ORDER_RANGE 10.0f
+#define GMCS_ORDER_RANGE 5.0f
 #endif
 
 __device__ __forceinline__ void pose_features(const float* __restrict__ pose, size_t ld, int i, float* f) {
@@ -130,27 +138,51 @@ __global__ void k_order_count(const float* __restrict__ pose, size_t ld, int P, 
     atomicAdd(cnt + k, 1u);
 }
 
-// Exclusive scan of the bucket counts, in place: one CTA of 1024 threads, 64 each.
-__global__ void __launch_bounds__(1024) k_order_scan(uint32_t* cnt) {
-    constexpr int kPer = kOrderBuckets / 1024;
-    __shared__ uint32_t part[1024];
-    uint32_t* mine = cnt + threadIdx.x * kPer;
-    uint32_t s = 0;
-    for (int k = 0; k < kPer; ++k) s += mine[k];
-    part[threadIdx.x] = s;
+// Exclusive scan of v over a CTA of 1024 threads; total: the CTA's sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total) {
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;   // inclusive within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan of the per-thread sums
-        const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;   // inclusive over the warps
     }
-    uint32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0u;
-    for (int k = 0; k < kPer; ++k) {
-        const uint32_t c = mine[k];
-        mine[k] = run;
-        run += c;
-    }
+    __syncthreads();
+    total = wsum[31];
+    return (warp > 0 ? wsum[warp - 1] : 0u) + x - v;
+}
+
+// Exclusive scan of the bucket counts in place, in three launches: each CTA scans
+// 1,024 counts and leaves its total, one CTA scans the totals, each CTA adds its
+// offset.
+__global__ void __launch_bounds__(1024) k_order_scan_tiles(uint32_t* cnt, uint32_t* tot) {
+    const uint32_t k = blockIdx.x * 1024u + threadIdx.x;
+    uint32_t t;
+    cnt[k] = block_exclusive_scan(cnt[k], t);
+    if (threadIdx.x == 0) tot[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan_totals(uint32_t* tot, int n) {
+    uint32_t t;
+    const uint32_t v = (int)threadIdx.x < n ? tot[threadIdx.x] : 0u;
+    const uint32_t e = block_exclusive_scan(v, t);
+    if ((int)threadIdx.x < n) tot[threadIdx.x] = e;
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan_add(uint32_t* cnt, const uint32_t* tot) {
+    cnt[blockIdx.x * 1024u + threadIdx.x] += tot[blockIdx.x];
 }
 
 __global__ void k_order_scatter(const uint32_t* __restrict__ key, int P, uint32_t* __restrict__ cnt,
@@ -162,18 +194,24 @@ __global__ void k_order_scatter(const uint32_t* __restrict__ key, int P, uint32_
 
 }  // namespace
 
-size_t order_scratch_words(int P) { return (size_t)kOrderBuckets + (size_t)P + kMm; }
+constexpr uint32_t kOrderTiles = kOrderBuckets / 1024;
+static_assert(kOrderBuckets % 1024 == 0 && kOrderTiles <= 1024, "bucket tiles of the scan");
+
+size_t order_scratch_words(int P) { return (size_t)kOrderBuckets + kMm + kOrderTiles + (size_t)P; }
 
 void launch_locality_order(const float* pose, size_t ld, int P, uint32_t* scratch, int* perm, cudaStream_t s) {
     if (P <= 0) return;
     uint32_t* cnt = scratch;
     int* mm = reinterpret_cast<int*>(scratch + kOrderBuckets);
-    uint32_t* key = scratch + kOrderBuckets + kMm;
+    uint32_t* tot = scratch + kOrderBuckets + kMm;
+    uint32_t* key = tot + kOrderTiles;
     const int blocks = (P + 255) / 256;
     k_order_init<<<64, 256, 0, s>>>(mm, cnt);
     k_order_bbox<<<blocks, 256, 0, s>>>(pose, ld, P, mm);
     k_order_count<<<blocks, 256, 0, s>>>(pose, ld, P, mm, key, cnt);
-    k_order_scan<<<1, 1024, 0, s>>>(cnt);
+    k_order_scan_tiles<<<kOrderTiles, 1024, 0, s>>>(cnt, tot);
+    k_order_scan_totals<<<1, 1024, 0, s>>>(tot, (int)kOrderTiles);
+    k_order_scan_add<<<kOrderTiles, 1024, 0, s>>>(cnt, tot);
     k_order_scatter<<<blocks, 256, 0, s>>>(key, P, cnt, perm);
 }
 
