@@ -1217,6 +1217,17 @@ int insert_scan_keyframe(gmcs_ctx* c, const float* scan, int N) {
 
 }  // namespace
 
+static int locality_order(gmcs_ctx* c, const int** perm);
+
+// The frame's lookup passes with the particles in the locality order (1), or in
+// their own order (0): after resampling, copies of one parent sit side by side
+// and a warp reads fewer distinct cells than the pose-space order gives it (FP32
+// gradient / value pass 1.534 / 1.015 -> 1.565 / 1.048 ms ordered; GICP value
+// pass 2.37 -> 2.44 ms).
+#ifndef GMCS_STEP_ORDER
+#define GMCS_STEP_ORDER 0
+#endif
+
 int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], const double cov[36],
               const double* u_override, gmcs_step_out* out) {
     if (!c || !delta_T || !cov) return GMCS_E_INVALID;
@@ -1238,9 +1249,11 @@ int gmcs_step(gmcs_ctx* c, const float* scan, int N, const double delta_T[12], c
     if (c->ovl_valid && (rc = enqueue_overlap(c, N, c->odo))) return rc;
     if ((rc = run_predict(c, delta_T, cov, nullptr, frame))) return rc;
     if ((rc = run_select(c, nullptr))) return rc;
+    const int* perm = nullptr;
+    if (GMCS_STEP_ORDER && (rc = locality_order(c, &perm))) return rc;
     for (int s = 0; s < c->cfg.steps; ++s)
-        if ((rc = run_pass(c, N, true, true, nullptr, nullptr, nullptr, nullptr))) return rc;
-    if ((rc = run_pass(c, N, false, false, c->ll, nullptr, nullptr, c->logw))) return rc;
+        if ((rc = run_pass(c, N, true, true, nullptr, nullptr, nullptr, nullptr, nullptr, perm))) return rc;
+    if ((rc = run_pass(c, N, false, false, c->ll, nullptr, nullptr, c->logw, nullptr, perm))) return rc;
     if ((rc = run_weigh(c, nullptr))) return rc;
     if (c->cfg.resample == GMCS_RESAMPLE_NEVER) {
         {
