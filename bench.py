@@ -48,8 +48,11 @@ FLOPS_GICP_MISS = 24
 GICP_VOXEL = 1.0                # m, voxel edge of the GICP keyframe maps
 FP32_LANES_PER_SM = 128         # FP32 FMA lanes per SM (4 schedulers x 32)
 # DRAM bytes read + written per gradient-pass launch, from one ncu capture of the
-# current kernel at the same particle and point counts (profiles/); None when stale
-TRAFFIC_PER_LAUNCH = {"f32": 32.57e6, "bf16": None, "f16": None}
+# current kernel on dense tables at 100,000 particles x 2,048 points (profiles/);
+# reported only for that workload (elsewhere the tables' share of L2 differs, so the
+# traffic does not scale with the lookups)
+TRAFFIC_PER_LAUNCH = {"f32": 32.57e6, "bf16": 30.52e6, "f16": 30.51e6}
+TRAFFIC_WORKLOAD = (100_000, 2048, "dense")
 
 
 def max_sm_mhz(index):
@@ -462,7 +465,8 @@ def run_native(a, world, rank, local):
                      "frac": achieved_tflops / peak_tflops,
                      "frac_of_measured_ffma": achieved_tflops / ffma_tflops, "measured_ffma_tflops": ffma_tflops,
                      "sm_count": sm_count,
-                     "traffic": None if gicp else TRAFFIC_PER_LAUNCH.get(a.dtype), "gicp_inlier_frac": inlier_frac,
+                     "traffic": None if gicp or (a.particles, a.points, a.layout) != TRAFFIC_WORKLOAD
+                     else TRAFFIC_PER_LAUNCH.get(a.dtype), "gicp_inlier_frac": inlier_frac,
                      "peak_source": peak_src_fp32,
                      "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms},
         "gather": {"algorithmic_bytes_per_launch": lookups_per_launch * rec_bytes, "achieved_gbs": gather_gbs,
