@@ -628,6 +628,51 @@ __device__ __forceinline__ void slot_point(const Xf& x, float4 p, float& ux, flo
     }
 }
 
+// slot_point with uz given, and (ZF) its floor too (cz, fz given).
+template <bool ZF>
+__device__ __forceinline__ void slot_point_z(const Xf& x, float4 p, float uz_in, int cz_in, float fz_in, float& ux,
+                                             float& uy, float& uz, int& cx, int& cy, int& cz, float& fx, float& fy,
+                                             float& fz) {
+    uz = uz_in;
+    const float2 uxy = p2_fma(make_float2(x.q0.x, x.q0.y), make_float2(p.x, p.x),
+                              p2_fma(make_float2(x.q0.z, x.q0.w), make_float2(p.y, p.y),
+                                     p2_fma(make_float2(x.q1.x, x.q1.y), make_float2(p.z, p.z),
+                                            make_float2(x.q1.z, x.q1.w))));
+    ux = uxy.x;
+    uy = uxy.y;
+    const float2 C2 = make_float2(12582912.0f, 12582912.0f);
+    const float2 t2 = p2_add_rm(uxy, C2);
+    const float2 f2 = p2_sub(uxy, p2_sub(t2, C2));
+    if constexpr (ZF) {
+        cz = cz_in;
+        fz = fz_in;
+    } else {
+        const float flz = floorf(uz);
+        cz = (int)flz;
+        fz = uz - flz;
+    }
+    cx = __float_as_int(t2.x) - 0x4B400000;
+    cy = __float_as_int(t2.y) - 0x4B400000;
+    fx = f2.x;
+    fy = f2.y;
+}
+
+// FP32 passes: the z rows of neighbour slots 0 and 1 on one packed pair, and their
+// floor on the pair as well (2: gradient pass 1.534 -> 1.511 ms), the z rows only (1:
+// 1.527 ms), or per slot (0); ZPAIR_SP: on column-sparse tables too (gradient pass
+// 1.917 -> 2.089 ms, so off)
+#ifndef GMCS_ZPAIR
+#define GMCS_ZPAIR 2
+#endif
+#ifndef GMCS_ZPAIR_SP
+#define GMCS_ZPAIR_SP 0
+#endif
+// with the pair, slot 2's z floor by the round-down add (1: 1.512 -> 1.547 ms) or on
+// the conversion unit (0)
+#ifndef GMCS_Z2MAGIC
+#define GMCS_Z2MAGIC 0
+#endif
+
 // A cell record as loaded: two float4 (FP32) or one uint4 of 16-bit
 // coefficients; widened to floats only when it is interpolated.
 template <int DT>
@@ -817,13 +862,40 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 }
             }
         };
+        constexpr int kZp = (DT == 0 && (!SP || GMCS_ZPAIR_SP)) ? GMCS_ZPAIR : 0;
         auto issue = [&](Stage<DT>& st, int j, bool live, int jn, bool live_n) {
             st.p = kPd ? pd : __ldg(a.scan + j);
+            float2 z01 = make_float2(0.f, 0.f), fz01 = z01;
+            int cz0 = 0, cz1 = 0;
+            if constexpr (kZp > 0) {
+                const float4 p = st.p;
+                z01 = p2_fma(make_float2(xf[0].q2.x, xf[1].q2.x), make_float2(p.x, p.x),
+                             p2_fma(make_float2(xf[0].q2.y, xf[1].q2.y), make_float2(p.y, p.y),
+                                    p2_fma(make_float2(xf[0].q2.z, xf[1].q2.z), make_float2(p.z, p.z),
+                                           make_float2(xf[0].q2.w, xf[1].q2.w))));
+                if constexpr (kZp == 2) {
+                    const float2 C2 = make_float2(12582912.0f, 12582912.0f);
+                    const float2 t2 = p2_add_rm(z01, C2);
+                    fz01 = p2_sub(z01, p2_sub(t2, C2));
+                    cz0 = __float_as_int(t2.x) - 0x4B400000;
+                    cz1 = __float_as_int(t2.y) - 0x4B400000;
+                }
+            }
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 int cx, cy, cz;
-                slot_point<DT, true>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0],
-                                      st.f[s][1], st.f[s][2]);
+                if constexpr (kZp > 0) {
+                    if (s < 2)
+                        slot_point_z<kZp == 2>(xf[s], st.p, s == 0 ? z01.x : z01.y, s == 0 ? cz0 : cz1,
+                                               s == 0 ? fz01.x : fz01.y, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy,
+                                               cz, st.f[s][0], st.f[s][1], st.f[s][2]);
+                    else
+                        slot_point<DT, !GMCS_Z2MAGIC>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz,
+                                                      st.f[s][0], st.f[s][1], st.f[s][2]);
+                } else {
+                    slot_point<DT, true>(xf[s], st.p, st.u[s][0], st.u[s][1], st.u[s][2], cx, cy, cz, st.f[s][0],
+                                         st.f[s][1], st.f[s][2]);
+                }
                 if constexpr (SP && kDirAhead) fetch_dir<DT>(cells[s], dd[s], cz, live, st.r[s]);
                 else fetch_raw<DT, SP>(cells[s], dirs[s], ncx[s], ncy[s], ncz[s], cx, cy, cz, live, st.r[s]);
             }
