@@ -300,37 +300,6 @@ __device__ __forceinline__ void coef_interp(const float* r, float fx, float fy, 
     }
 }
 
-// The gradient-pass lookup with its normalisation on packed pairs: (gx, gy) and
-// (gz, w) = (dL/dx, dL/dy) and (dL/dz, L) times 1 / (L + eps). On dense tables it
-// loses (FP32 gradient pass 1.511 -> 1.547 ms, GMCS_GPACK), on column-sparse ones it
-// gains (1.916 -> 1.820 ms, GMCS_GPACK_SP).
-#ifndef GMCS_GPACK
-#define GMCS_GPACK 0
-#endif
-#ifndef GMCS_GPACK_SP
-#define GMCS_GPACK_SP 1
-#endif
-template <bool LL>
-__device__ __forceinline__ void coef_interp2(const float* r, float fx, float fy, float fz, float eps, float& lprod,
-                                             float2& gxy, float2& gzw) {
-    const float2 Q0 = make_float2(r[0], r[1]), Q1 = make_float2(r[2], r[3]);   // (c4, c2), (c7, c6)
-    const float2 Q2 = make_float2(r[4], r[5]), Q3 = make_float2(r[6], r[7]);   // (c1, c0), (c5, c3)
-    const float2 ZZ = make_float2(fz, fz), YY = make_float2(fy, fy);
-    const float2 AD = p2_fma(Q1, ZZ, Q0);
-    const float2 BE = p2_fma(Q3, ZZ, Q2);
-    const float2 XE = p2_fma(YY, AD, BE);
-    const float L = fmaf(fx, XE.x, XE.y);
-    const float den = L + eps;
-    if constexpr (LL) lprod *= den;
-    const float2 TS = p2_fma(Q1, YY, Q3);
-    const float Ly = fmaf(fx, AD.x, AD.y);
-    const float Lz = fmaf(fx, TS.x, TS.y);
-    const float inv = __fdividef(1.f, den);
-    const float2 II = make_float2(inv, inv);
-    gxy = p2_mul(make_float2(XE.x, Ly), II);
-    gzw = p2_mul(make_float2(Lz, L), II);
-}
-
 template <int DT, bool GRAD, bool PROD = false>
 __device__ __forceinline__ void lookup_cell(const void* __restrict__ cells, const uint2* __restrict__ dir,
                                             uint32_t ncx, uint32_t ncy, uint32_t ncz,
@@ -942,17 +911,9 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 for (int s = 0; s < 3; ++s) {
                     float v[8], w, gx, gy, gz;
                     unpack_raw<DT>(st.r[s], v);
+                    coef_interp<true, true, kLL>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
                     const float ux = st.u[s][0], uy = st.u[s][1], uz = st.u[s][2];
-                    if constexpr (SP ? GMCS_GPACK_SP : GMCS_GPACK) {
-                        float2 gxy, gzw;
-                        coef_interp2<kLL>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, gxy, gzw);
-                        const float2 Gxy = p2_add(make_float2(G[s][0], G[s][1]), gxy);
-                        G[s][0] = Gxy.x; G[s][1] = Gxy.y; G[s][2] += gzw.x;
-                        gx = gxy.x; gy = gxy.y; gz = gzw.x; w = gzw.y;
-                    } else {
-                        coef_interp<true, true, kLL>(v, st.f[s][0], st.f[s][1], st.f[s][2], eps, lprod, w, gx, gy, gz);
-                        G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
-                    }
+                    G[s][0] += gx; G[s][1] += gy; G[s][2] += gz;
                     C[s][0] = fmaf(uy, gz, fmaf(-uz, gy, C[s][0]));
                     C[s][1] = fmaf(uz, gx, fmaf(-ux, gz, C[s][1]));
                     C[s][2] = fmaf(ux, gy, fmaf(-uy, gx, C[s][2]));
