@@ -263,6 +263,9 @@ void unload(gmcs_ctx* c) {
     c->K = 0;
     c->P = 0;
     c->nbr_K = 0;
+    cudaMemsetAsync(c->nbr, 0, sizeof(int) * GMCS_MAX_NB * c->ld, c->stream);
+    cudaMemsetAsync(c->d_tables, 0, sizeof(TableDesc) * (size_t)c->Kmax, c->stream);
+    cudaStreamSynchronize(c->stream);
     c->have_particles = false;
     c->last_valid = false;
     cudaGetLastError();

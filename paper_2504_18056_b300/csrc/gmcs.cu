@@ -402,8 +402,8 @@ int run_select(gmcs_ctx* c, int* nbr_out_dev) {
 }
 
 // The passes read the neighbour sets: they must have been selected since the
-// context was created or loaded (before, the sets hold -1 or another session's
-// keyframe indices).
+// context was created or loaded (before, the sets hold zeros or indices of the
+// keyframes the context held before a failed load).
 bool nbr_ready(const gmcs_ctx* c) { return c->nbr_K > 0 && c->nbr_K <= c->K; }
 
 int check_pass_state(const gmcs_ctx* c) {
@@ -648,7 +648,8 @@ int gmcs_create(const gmcs_config* cfg, int max_particles, int max_keyframes, in
         rc = GMCS_E_OOM;
     }
     if (!rc && cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
-    if (!rc && cudaMemsetAsync(c->nbr, 0xff, sizeof(int) * GMCS_MAX_NB * ld, c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
+    // neighbour sets start as table 0 (never a negative index; see nbr_ready)
+    if (!rc && cudaMemsetAsync(c->nbr, 0, sizeof(int) * GMCS_MAX_NB * ld, c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
     if (!rc && cudaMemsetAsync(c->d_tables, 0, sizeof(TableDesc) * (size_t)max_keyframes, c->stream) != cudaSuccess)
         rc = GMCS_E_CUDA;
     if (!rc && cudaMemsetAsync(c->d_res, 0, sizeof(WeighResult), c->stream) != cudaSuccess) rc = GMCS_E_CUDA;
