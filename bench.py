@@ -51,7 +51,7 @@ FP32_LANES_PER_SM = 128         # FP32 FMA lanes per SM (4 schedulers x 32)
 # current kernel on dense tables at 100,000 particles x 2,048 points (profiles/);
 # reported only for that workload (elsewhere the tables' share of L2 differs, so the
 # traffic does not scale with the lookups)
-TRAFFIC_PER_LAUNCH = {"f32": 32.57e6, "bf16": 30.52e6, "f16": 30.51e6}
+TRAFFIC_PER_LAUNCH = {"f32": 32.59e6, "bf16": 30.52e6, "f16": 30.51e6}
 TRAFFIC_WORKLOAD = (100_000, 2048, "dense")
 
 
