@@ -664,10 +664,10 @@ __device__ __forceinline__ void slot_point_z(const Xf& x, float4 p, float uz_in,
     fy = f2.y;
 }
 
-// FP32 passes: the z rows of neighbour slots 0 and 1 on one packed pair, and their
-// floor on the pair as well (2: gradient pass 1.534 -> 1.511 ms), the z rows only (1:
-// 1.527 ms), or per slot (0); ZPAIR_SP: on column-sparse tables too (gradient pass
-// 1.917 -> 2.089 ms, so off)
+// Pipelined passes with two whole stages: the z rows of neighbour slots 0 and 1 on
+// one packed pair, and their floor on the pair as well (2: FP32 gradient pass 1.534
+// -> 1.511 ms), the z rows only (1: 1.527 ms), or per slot (0); ZPAIR_SP: on
+// column-sparse tables too (FP32 gradient pass 1.917 -> 2.089 ms, so off)
 #ifndef GMCS_ZPAIR
 #define GMCS_ZPAIR 2
 #endif
@@ -869,7 +869,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
                 }
             }
         };
-        constexpr int kZp = (DT == 0 && (!SP || GMCS_ZPAIR_SP)) ? GMCS_ZPAIR : 0;
+        constexpr int kZp = (!SP || GMCS_ZPAIR_SP) ? GMCS_ZPAIR : 0;
         auto issue = [&](Stage<DT>& st, int j, bool live, int jn, bool live_n) {
             st.p = kPd ? pd : __ldg(a.scan + j);
             float2 z01 = make_float2(0.f, 0.f), fz01 = z01;
@@ -975,12 +975,15 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 // most four slots' records (instead of six) and two points are in flight at a
 // time -- fewer live registers for the same look-ahead.
 // (BF16 gradient pass 1.542 -> 1.521 ms; FP32 1.566 -> 1.607 ms, so FP32 keeps the
-// two whole stages)
+// two whole stages). Since the two whole stages pair two slots' z rows, the 16-bit
+// gradient passes take them too (BF16 1.526 ms either way; FP16 1.614 -> 1.611 ms;
+// served BF16 at saturation 1.089e11 -> 1.101e11 evals/s); the 16-bit value passes
+// stay interleaved.
 #ifndef GMCS_QPIPE32
 #define GMCS_QPIPE32 0
 #endif
 #ifndef GMCS_QPIPE16
-#define GMCS_QPIPE16 1
+#define GMCS_QPIPE16 0
 #endif
 // the value passes likewise (FP32 interleaved: 1.011 -> 1.027 ms at 4 CTAs per SM,
 // 1.070 ms at 5)
@@ -988,7 +991,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 #define GMCS_QPIPE32V GMCS_QPIPE32
 #endif
 #ifndef GMCS_QPIPE16V
-#define GMCS_QPIPE16V GMCS_QPIPE16
+#define GMCS_QPIPE16V 1
 #endif
 template <int DT, bool GRAD>
 constexpr bool qpipe() { return GRAD ? (DT == 0 ? GMCS_QPIPE32 : GMCS_QPIPE16) : (DT == 0 ? GMCS_QPIPE32V : GMCS_QPIPE16V); }
