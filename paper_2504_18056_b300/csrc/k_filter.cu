@@ -977,8 +977,8 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 // (BF16 gradient pass 1.542 -> 1.521 ms; FP32 1.566 -> 1.607 ms, so FP32 keeps the
 // two whole stages). Since the two whole stages pair two slots' z rows, the 16-bit
 // gradient passes take them too (BF16 1.526 ms either way; FP16 1.614 -> 1.611 ms;
-// served BF16 at saturation 1.089e11 -> 1.101e11 evals/s); the 16-bit value passes
-// stay interleaved.
+// served BF16 at saturation 1.089e11 -> 1.101e11 evals/s), and so do the 16-bit value
+// passes (BF16 0.938 -> 0.921 ms at 5 CTAs per SM; 0.949 ms at 4).
 #ifndef GMCS_QPIPE32
 #define GMCS_QPIPE32 0
 #endif
@@ -991,7 +991,7 @@ __device__ __forceinline__ void pass3p_body(const PassArgs& a, int vb) {
 #define GMCS_QPIPE32V GMCS_QPIPE32
 #endif
 #ifndef GMCS_QPIPE16V
-#define GMCS_QPIPE16V 1
+#define GMCS_QPIPE16V 0
 #endif
 template <int DT, bool GRAD>
 constexpr bool qpipe() { return GRAD ? (DT == 0 ? GMCS_QPIPE32 : GMCS_QPIPE16) : (DT == 0 ? GMCS_QPIPE32V : GMCS_QPIPE16V); }
@@ -1392,10 +1392,11 @@ __global__ void __launch_bounds__(128) k_select_b(const BatchList<SelectArgs>* L
 
 // The persistent loop costs the 16-bit gradient pass registers: bounded at 3
 // CTAs per SM like the pipelined one (unbounded it takes 180, i.e. 2 per SM); the
-// value passes at 4 (the 16-bit one spills at 5).
+// value passes as in the plain launch (the 16-bit dense one fits 96 registers at 5
+// CTAs per SM with the two-stage body; the others would spill there).
 template <int DT, bool GRAD, bool SP>
 constexpr int pass3_b_minblocks() {
-    return !GRAD ? GMCS_VALUE_MINBLOCKS : pass3_minblocks<DT, GRAD, SP>() < 3 ? 3 : pass3_minblocks<DT, GRAD, SP>();
+    return pass3_minblocks<DT, GRAD, SP>() < 3 ? 3 : pass3_minblocks<DT, GRAD, SP>();
 }
 
 // served frames never ask the gradient passes for the log-likelihood
